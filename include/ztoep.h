@@ -1,0 +1,200 @@
+/*
+ * ztoep -- solver for the two-level block-Toeplitz method-of-moments systems
+ * of finite antenna arrays with electrically connected elements (array
+ * decomposition into nine components; Akerstedt, Hultin & Jonsson).
+ *
+ * The system is Z I = V (Sec. II, Eq. MoMMatrixEq) with
+ *
+ *     Z = [[A, B^T],
+ *          [B, C  ]]                                  (Sec. II-C, Eq. matrixForm)
+ *
+ * A couples the element (component 5) parts and is two-level block Toeplitz
+ * (Eq. submatrixAA): its b x b block for element pair ((m,n),(m',n')) is the
+ * generating block T[m-m', n-n'], so it is stored as its (2Nx-1)(2Ny-1)
+ * generating blocks.  B couples the E non-Toeplitz edge/margin unknowns to
+ * the element unknowns and C couples them among themselves (Sec. II-C, the
+ * B and C blocks); both are taken dense here.  Z is symmetric (Sec. II-A), so
+ * T[-p,-q] = T[p,q]^T must hold for the input blocks.
+ *
+ * The product with A is done by embedding the generating blocks in a
+ * block circulant of size Lx x Ly >= (2Nx-1) x (2Ny-1), a 2-D FFT over the
+ * element indices (m, n), a b x b block product per frequency, an inverse
+ * FFT and a crop (the FFT acceleration of Toeplitz products cited in Sec. I);
+ * the edge unknowns are coupled in by a separate product with B, B^T and C.
+ * Solves are batched restarted GMRES (Sec. II-D names GMRES for the
+ * second Toeplitz level) inside an FP64 iterative-refinement loop.
+ *
+ * Conventions for every entry point:
+ *  - Unknown order: Toeplitz unknown (m, n, i), element column m < Nx, row
+ *    n < Ny, local basis i < b, has index (n*Nx + m)*b + i (components
+ *    indexed bottom-left first, x fastest, Sec. II-C); the E edge unknowns
+ *    follow at N_T .. N_T+E-1, N_T = Nx*Ny*b, N = N_T + E.
+ *  - Complex numbers are interleaved (re, im) IEEE doubles (complex128)
+ *    unless stated otherwise.  Vectors are stored one RHS after the other:
+ *    X[r*N + k].
+ *  - Device pointers are caller-owned CUDA global memory on the current
+ *    device; all work is ordered on the caller's stream (a cudaStream_t
+ *    passed as void*, NULL = legacy default stream).  A plan is used by one
+ *    stream at a time.
+ *  - Errors are returned as status codes; nothing is thrown across the ABI.
+ *    ZTOEP_ERR_CUDA means a CUDA call failed (the CUDA error is not
+ *    cleared); ZTOEP_ERR_TIMEOUT means a bounded device-side wait gave up.
+ */
+#ifndef ZTOEP_H
+#define ZTOEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define ZTOEP_API __attribute__((visibility("default")))
+#else
+#define ZTOEP_API
+#endif
+
+typedef struct ztoep_plan_s *ztoep_plan_t;
+
+typedef enum {
+    ZTOEP_OK = 0,
+    ZTOEP_ERR_ARG = 1,          /* invalid argument or descriptor */
+    ZTOEP_ERR_NOMEM = 2,        /* device allocation failed or footprint cap exceeded */
+    ZTOEP_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    ZTOEP_ERR_NOCONV = 4,       /* iteration limit reached before the tolerance */
+    ZTOEP_ERR_TIMEOUT = 5,      /* a bounded device-side wait or the solve timeout expired */
+    ZTOEP_ERR_UNSUPPORTED = 6,  /* valid request outside what this build implements */
+    ZTOEP_ERR_NONFINITE = 7     /* NaN/Inf in a right-hand side or residual */
+} ztoep_status_t;
+
+typedef enum {
+    ZTOEP_FP64 = 0,  /* every step in complex FP64 */
+    ZTOEP_MIXED = 1  /* FFTs and block/edge products in complex FP32 (inner
+                        solves), FP64 residuals, Arnoldi, Givens and updates */
+} ztoep_precision_t;
+
+/* Array descriptor.  nx, ny >= 1, b >= 1 (b <= 128), n_edge >= 0.
+ * active: HOST pointer to ny*nx bytes (row n, column m at [n*nx + m]),
+ *   nonzero = element present; NULL = all present.  An absent element's
+ *   unknowns get identity rows and columns, Z' = M Z M + (I - M), so with a
+ *   zero right-hand side there the solution there is exactly zero.
+ * lx, ly: circulant embedding sizes; 0 = choose automatically (the smallest
+ *   size >= 2n-1 whose prime factors are 2, 3 and 5).  Explicit sizes must be
+ *   >= 2n-1, <= 256 and have only those prime factors. */
+typedef struct {
+    int32_t nx, ny, b, n_edge;
+    const uint8_t *active;
+    int32_t lx, ly;
+} ztoep_desc_t;
+
+typedef struct {
+    double tol;          /* stop when ||v - Z x||_2 <= tol ||v||_2 for every RHS (true FP64 residual) */
+    int32_t restart;     /* GMRES restart length m, 1..128 */
+    int32_t max_iter;    /* cap on inner iterations per RHS, summed over cycles */
+    int32_t max_outer;   /* cap on refinement sweeps (true-residual evaluations) */
+    int32_t prec;        /* ztoep_precision_t */
+    double inner_tol;    /* MIXED: relative reduction asked of each inner solve */
+    int64_t timeout_ns;  /* wall-clock limit for the whole solve, 0 = none */
+    int32_t flags;       /* ZTOEP_FLAG_* bits */
+} ztoep_solve_opts_t;
+
+/* Ignore X on entry and start from x = 0 (saves the first FP64 product). */
+#define ZTOEP_FLAG_ZERO_GUESS 1
+
+typedef struct {
+    int32_t outer;        /* true-residual evaluations (refinement sweeps) */
+    int32_t inner_iters;  /* Krylov iterations (matrix products) used */
+    int32_t status;       /* ztoep_status_t for this RHS */
+    double rel_residual;  /* final ||v - Z x|| / ||v|| in FP64 */
+} ztoep_solve_info_t;
+
+typedef struct {
+    int32_t nx, ny, b, n_edge, lx, ly;
+    int64_t n_toep, n;          /* N_T and N */
+    int64_t n_pairs;            /* stored frequency blocks (f and -f share one, T^(-f) = T^(f)^T) */
+    size_t resident_bytes;      /* device bytes held by the plan */
+    size_t dense_bytes;         /* bytes the dense complex128 Z would need, N^2 * 16 */
+} ztoep_plan_info_t;
+
+/* Defaults: tol 1e-8, restart 30, max_iter 4000, max_outer 100, MIXED,
+ * inner_tol 1e-5, no timeout, no flags. */
+ZTOEP_API ztoep_status_t ztoep_default_opts(ztoep_solve_opts_t *opts);
+
+/* Build a plan: embed the generating blocks in the Lx x Ly block circulant,
+ * FFT them over (m, n) in FP64 (Eq. submatrixAA structure), keep the
+ * transformed blocks of one frequency of each pair {f, -f} resident in FP64
+ * and FP32, and keep B (absent elements' columns zeroed) and C in FP64 and
+ * FP32.
+ *   T: device complex128 [2ny-1][2nx-1][b][b]; T[q+ny-1][p+nx-1] is the
+ *      block of offset (p, q) = (m-m', n-n').
+ *   B: device complex128 [n_edge][N_T] (NULL iff n_edge == 0).
+ *   C: device complex128 [n_edge][n_edge] (NULL iff n_edge == 0).
+ * The inputs are read on `stream` and may be freed once the stream has
+ * passed this call.  *out owns its device memory until ztoep_plan_destroy.
+ * Errors: ARG (bad descriptor/pointers), NOMEM, CUDA. */
+ZTOEP_API ztoep_status_t ztoep_plan(const ztoep_desc_t *desc, const void *T, const void *B, const void *C,
+                          void *stream, ztoep_plan_t *out);
+
+/* Y = Z' X for nrhs right-hand sides (Z' with absent elements masked).
+ *   X, Y: device complex128 [nrhs][N], distinct buffers.
+ *   prec: ZTOEP_FP64 computes in FP64; ZTOEP_MIXED rounds X to FP32 and
+ *   computes the FFTs and products in FP32 (result widened to FP64).
+ * Errors: ARG, NOMEM (workspace), CUDA. */
+ZTOEP_API ztoep_status_t ztoep_matvec(ztoep_plan_t plan, int32_t prec, int32_t nrhs, const void *X, void *Y,
+                            void *stream);
+
+/* Solve Z' X = V for nrhs right-hand sides.
+ *   V: device complex128 [nrhs][N].
+ *   X: device complex128 [nrhs][N]; initial guess on entry, solution on
+ *      exit (on NOCONV/TIMEOUT the best iterate).
+ *   info: HOST array of nrhs entries, may be NULL.
+ * FP64: restarted GMRES(m) entirely in FP64, restarted on the true residual.
+ * MIXED: FP64 refinement x <- x + d, d from a GMRES(m) cycle on Z d = r
+ *   with FP32 products and FP64 Arnoldi/Givens/least squares, r = v - Z x in
+ *   FP64 between cycles.
+ * Returns the worst per-RHS status.  The call returns after the solve has
+ * finished on `stream` (it synchronises the stream between cycles). */
+ZTOEP_API ztoep_status_t ztoep_solve(ztoep_plan_t plan, const ztoep_solve_opts_t *opts, int32_t nrhs,
+                           const void *V, void *X, ztoep_solve_info_t *info, void *stream);
+
+/* ztoep_solve with V and X in HOST memory (pinned or pageable): copies V
+ * and the initial guess to the device, solves, copies X back.  The device
+ * buffers are the plan's own. */
+ZTOEP_API ztoep_status_t ztoep_solve_host(ztoep_plan_t plan, const ztoep_solve_opts_t *opts, int32_t nrhs,
+                                const void *V_host, void *X_host, ztoep_solve_info_t *info,
+                                void *stream);
+
+/* Forward spectrum of the Toeplitz part of X (inspection of the embedding
+ * and FFT stage): Xhat[f][r][i] = sum_{m,n} x[r][(n*nx+m)*b+i] w_Lx^(-kx m)
+ * w_Ly^(-ky n), f = ky*lx + kx, absent elements taken as zero.
+ *   X: device complex128 [nrhs][N]; Xhat: device complex128 [lx*ly][nrhs][b].
+ *   prec as in ztoep_matvec (MIXED computes in FP32, widened on output). */
+ZTOEP_API ztoep_status_t ztoep_forward_spectrum(ztoep_plan_t plan, int32_t prec, int32_t nrhs,
+                                      const void *X, void *Xhat, void *stream);
+
+/* Copy the plan's FP64 transformed blocks of every frequency into
+ * That: device complex128 [ly*lx][b][b] (frequency f = ky*lx + kx), rebuilding
+ * the blocks of -f as transposes of the stored ones. */
+ZTOEP_API ztoep_status_t ztoep_plan_spectrum(ztoep_plan_t plan, void *That, void *stream);
+
+ZTOEP_API ztoep_status_t ztoep_plan_get_info(ztoep_plan_t plan, ztoep_plan_info_t *info);
+
+/* Device bytes a plan for `desc` plus the workspace of a solve with up to
+ * max_nrhs right-hand sides and restart length `restart` would use (for
+ * admission control).  0 if the descriptor is invalid. */
+ZTOEP_API size_t ztoep_footprint(const ztoep_desc_t *desc, int32_t max_nrhs, int32_t restart);
+
+ZTOEP_API void ztoep_plan_destroy(ztoep_plan_t plan);
+
+ZTOEP_API const char *ztoep_status_string(ztoep_status_t status);
+
+/* Library version string, e.g. "ztoep 0.1 sm_103a". */
+ZTOEP_API const char *ztoep_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZTOEP_H */

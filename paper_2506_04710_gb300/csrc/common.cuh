@@ -1,0 +1,185 @@
+// Internal definitions shared by the ztoep CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+#include <mutex>
+
+#include "ztoep.h"
+
+namespace ztoep {
+
+// ---------------------------------------------------------------- complex
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { using T = float2; };
+template <> struct Cplx<double> { using T = double2; };
+template <typename R> using cplx_t = typename Cplx<R>::T;
+
+__host__ __device__ __forceinline__ float2 mkc(float r, float i) { return make_float2(r, i); }
+__host__ __device__ __forceinline__ double2 mkc(double r, double i) { return make_double2(r, i); }
+
+template <typename C> __host__ __device__ __forceinline__ C czero() { C z; z.x = 0; z.y = 0; return z; }
+
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+// a * b
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+__host__ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
+}
+// acc + a * b
+__host__ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
+    acc.x = fmaf(a.x, b.x, acc.x); acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y); acc.y = fmaf(a.y, b.x, acc.y);
+    return acc;
+}
+__host__ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+    return acc;
+}
+// acc + conj(a) * b
+__host__ __device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 acc) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+    return acc;
+}
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// a / b by Smith's algorithm (R. L. Smith, CACM 5(8), 1962).
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, d = b.x + b.y * r;
+        return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    }
+    double r = b.x / b.y, d = b.x * r + b.y;
+    return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+}
+
+template <typename Dst, typename Src> __host__ __device__ __forceinline__ Dst ccast(Src s) {
+    Dst d; d.x = s.x; d.y = s.y; return d;
+}
+
+// ---------------------------------------------------------------- FFT plan
+// Radix decomposition of one transform length (radices 2, 3, 4, 5).
+struct Fft1D {
+    int L;
+    int nst;
+    int rad[12];
+};
+
+Fft1D make_fft1d(int L);
+int smooth_size_at_least(int n);
+bool is_smooth(int n);
+
+// ---------------------------------------------------------------- plan
+struct MatvecWs {  // per-precision matvec workspace, sized for `cap` RHS
+    int cap = 0;
+    void *xin = nullptr;    // [cap][N] input copy in this precision (public matvec / solver)
+    void *yout = nullptr;   // [cap][N] output in this precision
+    void *X1 = nullptr;     // [cap][ny][lx][b] after the x pass (also reused by the inverse y pass)
+    void *Xh = nullptr;     // [F][cap][b] spectrum (block product runs in place)
+    void *ET = nullptr;     // [nsplit][cap][NT] B^T x_E partial sums
+    void *Ep = nullptr;     // [ntile][cap][E]   B x_T partial sums
+    size_t bytes = 0;
+};
+
+struct SolveWs {  // Krylov workspace, sized for `cap` RHS and restart `m`
+    int cap = 0, m = 0;
+    double2 *Vb = nullptr;     // [(m+1)][cap][N] Krylov basis
+    double2 *w = nullptr;      // [cap][N] FP64 work vector
+    double2 *r = nullptr;      // [cap][N] residual / FP64 scratch
+    double2 *H = nullptr;      // [cap][m+1][m] Hessenberg (rotated to R)
+    double2 *cs = nullptr;     // [cap][m]
+    double2 *sn = nullptr;     // [cap][m]
+    double2 *g = nullptr;      // [cap][m+1]
+    double2 *y = nullptr;      // [cap][m] least-squares solution
+    double2 *h1 = nullptr;     // [cap][m+1]
+    double2 *h2 = nullptr;     // [cap][m+1]
+    double2 *part = nullptr;   // [cap][nchunk][m+2] per-CTA partial sums
+    double *nrm = nullptr;     // [cap][4] scalars: ||v||, beta0, target, ||r||
+    int *st = nullptr;         // [cap][8] per-RHS state
+    unsigned *cnt = nullptr;   // [cap] last-CTA counters
+    int *hst = nullptr;        // host pinned mirror of st
+    double *hnrm = nullptr;    // host pinned mirror of nrm
+    size_t bytes = 0;
+};
+
+struct PlanImpl;
+
+}  // namespace ztoep
+
+struct ztoep_plan_s {
+    int nx = 0, ny = 0, b = 0, E = 0, lx = 0, ly = 0, F = 0;
+    int64_t NT = 0, N = 0;
+    int npairs = 0;
+    int device = 0;
+    int nsm = 0;
+    bool masked = false;
+    ztoep::Fft1D fx{}, fy{};
+    int2 *pairs = nullptr;          // [npairs] (f, -f); f == -f for self-paired frequencies
+    int *rep = nullptr;             // [F] pair index of f if f is the stored one, else -1-pair
+    double2 *That64 = nullptr;      // [npairs][b][b]
+    float2 *That32 = nullptr;
+    double2 *B64 = nullptr;         // [E][NT], absent elements' columns zero
+    float2 *B32 = nullptr;
+    double2 *C64 = nullptr;         // [E][E]
+    float2 *C32 = nullptr;
+    uint8_t *active = nullptr;      // [ny*nx] device copy, nullptr if all active
+    double2 *twx64 = nullptr, *twy64 = nullptr;  // exp(-2 pi i t / L)
+    float2 *twx32 = nullptr, *twy32 = nullptr;
+    int *err = nullptr;             // device error word (bounded waits)
+    size_t resident = 0;
+    ztoep::MatvecWs ws32, ws64;
+    ztoep::SolveWs sws;
+    cudaStream_t side = nullptr;    // edge-coupling branch of the matvec
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    std::mutex mu;
+};
+
+namespace ztoep {
+
+#define ZT_CUDA(call)                                      \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return ZTOEP_ERR_CUDA;      \
+    } while (0)
+
+#define ZT_TRY(call)                                       \
+    do {                                                   \
+        ztoep_status_t s_ = (call);                        \
+        if (s_ != ZTOEP_OK) return s_;                     \
+    } while (0)
+
+ztoep_status_t dalloc(void **p, size_t bytes, size_t *acc);
+
+// Matvec in one precision on plan-internal buffers: y = Z' x, x/y [nrhs][N].
+template <typename R>
+ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *y,
+                          cudaStream_t s);
+template <typename R> ztoep_status_t ensure_ws(ztoep_plan_t p, int nrhs);
+template <typename R> MatvecWs &ws_of(ztoep_plan_t p);
+template <typename R>
+ztoep_status_t run_forward_spectrum(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *Xh,
+                                    cudaStream_t s);
+
+// Elementwise helpers (kernels in matvec.cu).
+ztoep_status_t launch_c128_to_c64(const double2 *src, float2 *dst, int64_t n, cudaStream_t s);
+ztoep_status_t launch_c64_to_c128(const float2 *src, double2 *dst, int64_t n, cudaStream_t s);
+
+}  // namespace ztoep

@@ -1,0 +1,492 @@
+// The FFT product with the two-level block-Toeplitz part A and the edge
+// coupling (B, B^T, C) of Z = [[A, B^T], [B, C]] (Sec. II-C, Eq. matrixForm,
+// Eq. submatrixAA).
+//
+// Pipeline for y = Z' x (x, y: [nrhs][N], Toeplitz part [ny][nx][b] per RHS):
+//   1. x pass  : X1[r][n][kx][i]  = FFT_m( x[r][n][m][i], zero-padded to lx )
+//   2. y pass  : Xh[f][r][i]      = FFT_n( X1[r][n][kx][i], zero-padded to ly ), f = ky*lx+kx
+//   3. product : Xh[f] <- T^[f] Xh[f],  Xh[-f] <- T^[f]^T Xh[-f]   (in place, one T^ read per pair)
+//   4. y pass^-1: X1[r][n][kx][i] = IFFT_ky(Xh)[n],  n < ny (crop)
+//   5. x pass^-1: y[r][n][m][i]   = IFFT_kx(X1)[m] / (lx ly) + (B^T x_E)[...],  m < nx (crop),
+//                 absent elements pass x through (identity rows)
+//   side branch (concurrent with 1-4): B x_T and B^T x_E in one pass over B,
+//                 then y_E = sum of partials + C x_E.
+#include <algorithm>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace ztoep {
+
+// ------------------------------------------------------------ FFT functors
+template <typename R> struct LdXFwd {  // x[r][(n*nx+m)*b+i], masked, zero beyond nx
+    const cplx_t<R> *x; const uint8_t *active; int nx, b, ib; int64_t N;
+    __device__ cplx_t<R> operator()(int m, int ch) const {
+        const int n = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
+        if (m >= nx || i >= b) return czero<cplx_t<R>>();
+        const int el = n * nx + m;
+        if (active && !active[el]) return czero<cplx_t<R>>();
+        return x[(int64_t)r * N + (int64_t)el * b + i];
+    }
+};
+template <typename R> struct StX1 {  // X1[r][n][kx][i]
+    cplx_t<R> *X1; int ny, lx, b, ib;
+    __device__ void operator()(int kx, int ch, cplx_t<R> v) const {
+        const int n = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
+        if (i < b) X1[(((int64_t)r * ny + n) * lx + kx) * b + i] = v;
+    }
+};
+template <typename R> struct LdX1 {  // X1[r][n][kx][i], zero beyond ny; grid.y = kx
+    const cplx_t<R> *X1; int ny, lx, b, ib;
+    __device__ cplx_t<R> operator()(int n, int ch) const {
+        const int kx = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
+        if (n >= ny || i >= b) return czero<cplx_t<R>>();
+        return X1[(((int64_t)r * ny + n) * lx + kx) * b + i];
+    }
+};
+template <typename R> struct StXh {  // Xh[f][r][i]
+    cplx_t<R> *Xh; int lx, b, ib, nrhs;
+    __device__ void operator()(int ky, int ch, cplx_t<R> v) const {
+        const int kx = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
+        if (i < b) Xh[(((int64_t)ky * lx + kx) * nrhs + r) * b + i] = v;
+    }
+};
+template <typename R> struct LdXh {
+    const cplx_t<R> *Xh; int lx, b, ib, nrhs;
+    __device__ cplx_t<R> operator()(int ky, int ch) const {
+        const int kx = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
+        if (i >= b) return czero<cplx_t<R>>();
+        return Xh[(((int64_t)ky * lx + kx) * nrhs + r) * b + i];
+    }
+};
+template <typename R> struct StY1 {  // crop n < ny
+    cplx_t<R> *X1; int ny, lx, b, ib;
+    __device__ void operator()(int n, int ch, cplx_t<R> v) const {
+        const int kx = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
+        if (n < ny && i < b) X1[(((int64_t)r * ny + n) * lx + kx) * b + i] = v;
+    }
+};
+template <typename R> struct LdY1 {  // grid.y = n
+    const cplx_t<R> *X1; int ny, lx, b, ib;
+    __device__ cplx_t<R> operator()(int kx, int ch) const {
+        const int n = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
+        if (i >= b) return czero<cplx_t<R>>();
+        return X1[(((int64_t)r * ny + n) * lx + kx) * b + i];
+    }
+};
+template <typename R> struct StYOut {  // crop m < nx, scale, + B^T x_E partials, identity on absent elements
+    cplx_t<R> *y; const cplx_t<R> *xin; const cplx_t<R> *ET; const uint8_t *active;
+    int nx, b, ib, nrhs, nsplit; int64_t N, NT; R scale;
+    __device__ void operator()(int m, int ch, cplx_t<R> v) const {
+        const int n = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
+        if (m >= nx || i >= b) return;
+        const int el = n * nx + m;
+        const int64_t t = (int64_t)el * b + i;
+        cplx_t<R> out;
+        if (active && !active[el]) {
+            out = xin[(int64_t)r * N + t];
+        } else {
+            out = cscale(v, scale);
+            for (int s = 0; s < nsplit; ++s) out = out + ET[((int64_t)s * nrhs + r) * NT + t];
+        }
+        y[(int64_t)r * N + t] = out;
+    }
+};
+
+// ------------------------------------------------------------ block product
+// One CTA per frequency pair {f, -f}: T^[f] (b x b, row-major) is staged in
+// shared memory once and used for both Xh[f] <- T^[f] Xh[f] (row products,
+// each thread walks its row with a skew so that a warp hits distinct banks)
+// and Xh[-f] <- T^[f]^T Xh[-f] (column products, contiguous across threads).
+template <typename R>
+__global__ void __launch_bounds__(256) k_blockprod(const int2 *__restrict__ pairs, int npairs,
+                                                   const cplx_t<R> *__restrict__ That,
+                                                   cplx_t<R> *Xh, int b, int nrhs, int rch) {
+    using C = cplx_t<R>;
+    extern __shared__ __align__(16) unsigned char zt_smem[];
+    C *sT = reinterpret_cast<C *>(zt_smem);
+    C *sf = sT + (size_t)b * b;
+    C *sg = sf + (size_t)rch * b;
+    const int rb = nrhs * b;
+    for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
+        const int f = pairs[p].x, g = pairs[p].y;
+        const C *Tb = That + (size_t)p * b * b;
+        for (int t = threadIdx.x; t < b * b; t += blockDim.x) sT[t] = Tb[t];
+        for (int r0 = 0; r0 < nrhs; r0 += rch) {
+            const int rc = min(rch, nrhs - r0);
+            const int cb = rc * b;
+            C *xf = Xh + (size_t)f * rb + (size_t)r0 * b;
+            C *xg = Xh + (size_t)g * rb + (size_t)r0 * b;
+            for (int t = threadIdx.x; t < cb; t += blockDim.x) {
+                sf[t] = xf[t];
+                if (g != f) sg[t] = xg[t];
+            }
+            __syncthreads();
+            const int nout = (g != f ? 2 : 1) * cb;
+            for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+                C acc = czero<C>();
+                if (o < cb) {
+                    const int rr = o / b, i = o - rr * b;
+                    const C *row = sT + (size_t)i * b;
+                    const C *xv = sf + (size_t)rr * b;
+                    int j = i;
+                    for (int jj = 0; jj < b; ++jj) {
+                        acc = cfma(row[j], xv[j], acc);
+                        if (++j == b) j = 0;
+                    }
+                    xf[o] = acc;
+                } else {
+                    const int o2 = o - cb;
+                    const int rr = o2 / b, j = o2 - rr * b;
+                    const C *xv = sg + (size_t)rr * b;
+                    for (int i = 0; i < b; ++i) acc = cfma(sT[(size_t)i * b + j], xv[i], acc);
+                    xg[o2] = acc;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------ edge coupling
+// One pass over B [E][ldb] (row e = edge unknown, column t = Toeplitz unknown)
+// computing, for RHS r0..r0+RC-1,
+//   ET[split][r][t] = sum_{e in split} B[e][t] x_E[r][e]     (B^T x_E)
+//   Ep[tile][r][e]  = sum_{t in tile} B[e][t] x_T[r][t]       (B x_T partials)
+// Each lane owns U 16-byte units of columns; B rows are read with fully
+// coalesced 16-byte loads.  Row partials are reduced across the warp with
+// shuffles and across warps through shared memory.
+template <typename R> struct EdgeGeom {
+    static constexpr int CPL = 16 / sizeof(cplx_t<R>);  // complex per 16-byte unit
+    static constexpr int U = 2;                          // units per lane
+    static constexpr int WARPS = 8;
+    static constexpr int TILE = WARPS * 32 * U * CPL;    // columns per CTA
+};
+
+template <typename R>
+__device__ __forceinline__ cplx_t<R> warp_sum(cplx_t<R> v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+template <typename R, int RC>
+__global__ void __launch_bounds__(256) k_edge(const cplx_t<R> *__restrict__ x, const cplx_t<R> *__restrict__ B,
+                                              cplx_t<R> *__restrict__ ET, cplx_t<R> *__restrict__ Ep,
+                                              int64_t NT, int64_t ldb, int E, int64_t N, int nrhs, int r0,
+                                              int rc, int e_per_split) {
+    using C = cplx_t<R>;
+    using G = EdgeGeom<R>;
+    constexpr int CPL = G::CPL, U = G::U, W = G::WARPS;
+    constexpr int CHUNK = 32;
+    __shared__ C sxe[CHUNK][RC];
+    __shared__ C red[W][CHUNK][RC];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tile = blockIdx.x, split = blockIdx.y;
+    const int64_t tbase = (int64_t)tile * G::TILE + (int64_t)warp * (32 * U * CPL);
+    const int e0 = split * e_per_split;
+    const int e1 = min(E, e0 + e_per_split);
+
+    C xt[U][CPL][RC];
+    C acc[U][CPL][RC];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int64_t t = tbase + (int64_t)(u * 32 + lane) * CPL + c;
+#pragma unroll
+            for (int q = 0; q < RC; ++q) {
+                acc[u][c][q] = czero<C>();
+                xt[u][c][q] = (t < NT && q < rc) ? x[(int64_t)(r0 + q) * N + t] : czero<C>();
+            }
+        }
+
+    for (int ec = e0; ec < e1; ec += CHUNK) {
+        const int ne = min(CHUNK, e1 - ec);
+        __syncthreads();
+        for (int k = threadIdx.x; k < CHUNK * RC; k += blockDim.x) {
+            const int el = k / RC, q = k - el * RC;
+            sxe[el][q] = (el < ne && q < rc) ? x[(int64_t)(r0 + q) * N + NT + ec + el] : czero<C>();
+        }
+        __syncthreads();
+        for (int el = 0; el < ne; ++el) {
+            const C *brow = B + (int64_t)(ec + el) * ldb + tbase;
+            C bv[U][CPL];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float4 raw = __ldg(reinterpret_cast<const float4 *>(brow + (int64_t)(u * 32 + lane) * CPL));
+                const C *pc = reinterpret_cast<const C *>(&raw);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) bv[u][c] = pc[c];
+            }
+#pragma unroll
+            for (int q = 0; q < RC; ++q) {
+                const C xe = sxe[el][q];
+                C part = czero<C>();
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) {
+                        acc[u][c][q] = cfma(bv[u][c], xe, acc[u][c][q]);
+                        part = cfma(bv[u][c], xt[u][c][q], part);
+                    }
+                part = warp_sum<R>(part);
+                if (lane == 0) red[warp][el][q] = part;
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < ne * RC; k += blockDim.x) {
+            const int el = k / RC, q = k - el * RC;
+            if (q < rc) {
+                C s = czero<C>();
+#pragma unroll
+                for (int w = 0; w < W; ++w) s = s + red[w][el][q];
+                Ep[((int64_t)tile * nrhs + r0 + q) * E + ec + el] = s;
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int64_t t = tbase + (int64_t)(u * 32 + lane) * CPL + c;
+            if (t < NT) {
+#pragma unroll
+                for (int q = 0; q < RC; ++q)
+                    if (q < rc) ET[((int64_t)split * nrhs + r0 + q) * NT + t] = acc[u][c][q];
+            }
+        }
+}
+
+// y_E[r][e] = sum_tile Ep[tile][r][e] + sum_e' C[e][e'] x_E[r][e'].  One warp per (e, r).
+template <typename R>
+__global__ void __launch_bounds__(256) k_edge_finish(const cplx_t<R> *__restrict__ x, const cplx_t<R> *__restrict__ Cm,
+                                                     const cplx_t<R> *__restrict__ Ep, cplx_t<R> *__restrict__ y,
+                                                     int64_t NT, int E, int64_t N, int nrhs, int ntile) {
+    using C = cplx_t<R>;
+    const int lane = threadIdx.x & 31;
+    const int e = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int r = blockIdx.y;
+    if (e >= E) return;
+    C s = czero<C>();
+    for (int t = lane; t < ntile; t += 32) s = s + Ep[((int64_t)t * nrhs + r) * E + e];
+    const C *crow = Cm + (int64_t)e * E;
+    const C *xe = x + (int64_t)r * N + NT;
+    for (int k = lane; k < E; k += 32) s = cfma(crow[k], xe[k], s);
+    s = warp_sum<R>(s);
+    if (lane == 0) y[(int64_t)r * N + NT + e] = s;
+}
+
+// ------------------------------------------------------------ conversions
+__global__ void k_c128_to_c64(const double2 *__restrict__ s, float2 *__restrict__ d, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        d[k] = make_float2((float)s[k].x, (float)s[k].y);
+}
+__global__ void k_c64_to_c128(const float2 *__restrict__ s, double2 *__restrict__ d, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        d[k] = make_double2(s[k].x, s[k].y);
+}
+
+static unsigned grid_for(int64_t n, int threads) {
+    int64_t g = (n + threads - 1) / threads;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
+}
+
+ztoep_status_t launch_c128_to_c64(const double2 *src, float2 *dst, int64_t n, cudaStream_t s) {
+    if (n <= 0) return ZTOEP_OK;
+    k_c128_to_c64<<<grid_for(n, 256), 256, 0, s>>>(src, dst, n);
+    ZT_CUDA(cudaGetLastError());
+    return ZTOEP_OK;
+}
+ztoep_status_t launch_c64_to_c128(const float2 *src, double2 *dst, int64_t n, cudaStream_t s) {
+    if (n <= 0) return ZTOEP_OK;
+    k_c64_to_c128<<<grid_for(n, 256), 256, 0, s>>>(src, dst, n);
+    ZT_CUDA(cudaGetLastError());
+    return ZTOEP_OK;
+}
+
+// ------------------------------------------------------------ workspace
+template <> MatvecWs &ws_of<float>(ztoep_plan_t p) { return p->ws32; }
+template <> MatvecWs &ws_of<double>(ztoep_plan_t p) { return p->ws64; }
+
+static int edge_ntile(ztoep_plan_t p, size_t csize) {
+    int tile = (csize == 8) ? EdgeGeom<float>::TILE : EdgeGeom<double>::TILE;
+    return (int)((p->NT + tile - 1) / tile);
+}
+static int edge_nsplit(ztoep_plan_t p, int ntile) {
+    if (p->E == 0) return 0;
+    int want = (2 * p->nsm + ntile - 1) / ntile;
+    int maxs = std::max(1, p->E / 32);
+    return std::max(1, std::min(want, maxs));
+}
+
+static void free_ws(MatvecWs &w) {
+    cudaFree(w.xin); cudaFree(w.yout); cudaFree(w.X1); cudaFree(w.Xh); cudaFree(w.ET); cudaFree(w.Ep);
+    w = MatvecWs{};
+}
+
+template <typename R> ztoep_status_t ensure_ws(ztoep_plan_t p, int nrhs) {
+    MatvecWs &w = ws_of<R>(p);
+    if (w.cap >= nrhs) return ZTOEP_OK;
+    free_ws(w);
+    const size_t cs = sizeof(cplx_t<R>);
+    const int ntile = edge_ntile(p, cs);
+    const int nsplit = edge_nsplit(p, ntile);
+    size_t acc = 0;
+    ZT_TRY(dalloc(&w.xin, cs * nrhs * p->N, &acc));
+    ZT_TRY(dalloc(&w.yout, cs * nrhs * p->N, &acc));
+    ZT_TRY(dalloc(&w.X1, cs * nrhs * (size_t)p->ny * p->lx * p->b, &acc));
+    ZT_TRY(dalloc(&w.Xh, cs * nrhs * (size_t)p->F * p->b, &acc));
+    if (p->E > 0) {
+        ZT_TRY(dalloc(&w.ET, cs * (size_t)nsplit * nrhs * p->NT, &acc));
+        ZT_TRY(dalloc(&w.Ep, cs * (size_t)ntile * nrhs * p->E, &acc));
+    }
+    w.cap = nrhs;
+    w.bytes = acc;
+    return ZTOEP_OK;
+}
+template ztoep_status_t ensure_ws<float>(ztoep_plan_t, int);
+template ztoep_status_t ensure_ws<double>(ztoep_plan_t, int);
+
+template <typename R> static const cplx_t<R> *that_of(ztoep_plan_t p);
+template <> const float2 *that_of<float>(ztoep_plan_t p) { return p->That32; }
+template <> const double2 *that_of<double>(ztoep_plan_t p) { return p->That64; }
+template <typename R> static const cplx_t<R> *b_of(ztoep_plan_t p);
+template <> const float2 *b_of<float>(ztoep_plan_t p) { return p->B32; }
+template <> const double2 *b_of<double>(ztoep_plan_t p) { return p->B64; }
+template <typename R> static const cplx_t<R> *c_of(ztoep_plan_t p);
+template <> const float2 *c_of<float>(ztoep_plan_t p) { return p->C32; }
+template <> const double2 *c_of<double>(ztoep_plan_t p) { return p->C64; }
+template <typename R> static const cplx_t<R> *twx_of(ztoep_plan_t p);
+template <> const float2 *twx_of<float>(ztoep_plan_t p) { return p->twx32; }
+template <> const double2 *twx_of<double>(ztoep_plan_t p) { return p->twx64; }
+template <typename R> static const cplx_t<R> *twy_of(ztoep_plan_t p);
+template <> const float2 *twy_of<float>(ztoep_plan_t p) { return p->twy32; }
+template <> const double2 *twy_of<double>(ztoep_plan_t p) { return p->twy64; }
+
+static int64_t edge_ldb(int64_t NT) { return (NT + 1023) / 1024 * 1024; }
+
+template <typename R>
+static ztoep_status_t forward_passes(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *X1,
+                                     cplx_t<R> *Xh, cudaStream_t s) {
+    const size_t cs = sizeof(cplx_t<R>);
+    const uint8_t *act = p->masked ? p->active : nullptr;
+    const int libx = pick_lib(p->lx, p->b, cs, 64 * 1024);
+    const int ibx = 1 << libx;
+    dim3 gx((p->b + ibx - 1) / ibx, p->ny, nrhs);
+    ZT_TRY((launch_fft_pass<R>(p->fx, twx_of<R>(p), libx, false, gx,
+                               LdXFwd<R>{x, act, p->nx, p->b, ibx, p->N},
+                               StX1<R>{X1, p->ny, p->lx, p->b, ibx}, s)));
+    const int liby = pick_lib(p->ly, p->b, cs, 64 * 1024);
+    const int iby = 1 << liby;
+    dim3 gy((p->b + iby - 1) / iby, p->lx, nrhs);
+    ZT_TRY((launch_fft_pass<R>(p->fy, twy_of<R>(p), liby, false, gy,
+                               LdX1<R>{X1, p->ny, p->lx, p->b, iby},
+                               StXh<R>{Xh, p->lx, p->b, iby, nrhs}, s)));
+    return ZTOEP_OK;
+}
+
+template <typename R>
+static ztoep_status_t launch_blockprod(ztoep_plan_t p, int nrhs, cplx_t<R> *Xh, cudaStream_t s) {
+    const size_t cs = sizeof(cplx_t<R>);
+    const size_t budget = 200 * 1024;
+    const size_t tbytes = cs * (size_t)p->b * p->b;
+    if (tbytes + 2 * cs * p->b > budget) return ZTOEP_ERR_UNSUPPORTED;
+    const int rch = (int)std::min<size_t>((size_t)nrhs, (budget - tbytes) / (2 * cs * p->b));
+    const size_t smem = tbytes + 2 * cs * (size_t)rch * p->b;
+    static bool attr = false;
+    if (!attr) {
+        ZT_CUDA(cudaFuncSetAttribute(k_blockprod<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr = true;
+    }
+    k_blockprod<R><<<p->npairs, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, p->b, nrhs, rch);
+    ZT_CUDA(cudaGetLastError());
+    return ZTOEP_OK;
+}
+
+template <typename R>
+static ztoep_status_t launch_edge(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *y,
+                                  MatvecWs &w, cudaStream_t s) {
+    const size_t cs = sizeof(cplx_t<R>);
+    const int ntile = edge_ntile(p, cs);
+    const int nsplit = edge_nsplit(p, ntile);
+    const int eps = (p->E + nsplit - 1) / nsplit;
+    cplx_t<R> *ET = reinterpret_cast<cplx_t<R> *>(w.ET);
+    cplx_t<R> *Ep = reinterpret_cast<cplx_t<R> *>(w.Ep);
+    const int64_t ldb = edge_ldb(p->NT);
+    for (int r0 = 0; r0 < nrhs; r0 += 4) {
+        const int rc = std::min(4, nrhs - r0);
+        dim3 g(ntile, nsplit);
+        if (rc == 1)
+            k_edge<R, 1><<<g, 256, 0, s>>>(x, b_of<R>(p), ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc, eps);
+        else if (rc == 2)
+            k_edge<R, 2><<<g, 256, 0, s>>>(x, b_of<R>(p), ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc, eps);
+        else
+            k_edge<R, 4><<<g, 256, 0, s>>>(x, b_of<R>(p), ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc, eps);
+        ZT_CUDA(cudaGetLastError());
+    }
+    dim3 gf((p->E + 7) / 8, nrhs);
+    k_edge_finish<R><<<gf, 256, 0, s>>>(x, c_of<R>(p), Ep, y, p->NT, p->E, p->N, nrhs, ntile);
+    ZT_CUDA(cudaGetLastError());
+    return ZTOEP_OK;
+}
+
+template <typename R>
+ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *y, cudaStream_t s) {
+    ZT_TRY(ensure_ws<R>(p, nrhs));
+    MatvecWs &w = ws_of<R>(p);
+    const size_t cs = sizeof(cplx_t<R>);
+    cplx_t<R> *X1 = reinterpret_cast<cplx_t<R> *>(w.X1);
+    cplx_t<R> *Xh = reinterpret_cast<cplx_t<R> *>(w.Xh);
+    const int ntile = edge_ntile(p, cs);
+    const int nsplit = edge_nsplit(p, ntile);
+    if (p->E > 0) {  // edge branch on the side stream, concurrent with the FFT chain
+        ZT_CUDA(cudaEventRecord(p->ev_fork, s));
+        ZT_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+        ZT_TRY(launch_edge<R>(p, nrhs, x, y, w, p->side));
+        ZT_CUDA(cudaEventRecord(p->ev_join, p->side));
+    }
+    ZT_TRY(forward_passes<R>(p, nrhs, x, X1, Xh, s));
+    ZT_TRY(launch_blockprod<R>(p, nrhs, Xh, s));
+    const int liby = pick_lib(p->ly, p->b, cs, 64 * 1024);
+    const int iby = 1 << liby;
+    dim3 gy((p->b + iby - 1) / iby, p->lx, nrhs);
+    ZT_TRY((launch_fft_pass<R>(p->fy, twy_of<R>(p), liby, true, gy,
+                               LdXh<R>{Xh, p->lx, p->b, iby, nrhs},
+                               StY1<R>{X1, p->ny, p->lx, p->b, iby}, s)));
+    if (p->E > 0) ZT_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
+    const int libx = pick_lib(p->lx, p->b, cs, 64 * 1024);
+    const int ibx = 1 << libx;
+    dim3 gx((p->b + ibx - 1) / ibx, p->ny, nrhs);
+    const R scale = (R)(1.0 / ((double)p->lx * (double)p->ly));
+    ZT_TRY((launch_fft_pass<R>(p->fx, twx_of<R>(p), libx, true, gx,
+                               LdY1<R>{X1, p->ny, p->lx, p->b, ibx},
+                               StYOut<R>{y, x, reinterpret_cast<const cplx_t<R> *>(w.ET),
+                                         p->masked ? p->active : nullptr, p->nx, p->b, ibx, nrhs,
+                                         nsplit, p->N, p->NT, scale}, s)));
+    return ZTOEP_OK;
+}
+template ztoep_status_t run_matvec<float>(ztoep_plan_t, int, const float2 *, float2 *, cudaStream_t);
+template ztoep_status_t run_matvec<double>(ztoep_plan_t, int, const double2 *, double2 *, cudaStream_t);
+
+template <typename R>
+ztoep_status_t run_forward_spectrum(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *Xh,
+                                    cudaStream_t s) {
+    ZT_TRY(ensure_ws<R>(p, nrhs));
+    MatvecWs &w = ws_of<R>(p);
+    return forward_passes<R>(p, nrhs, x, reinterpret_cast<cplx_t<R> *>(w.X1), Xh, s);
+}
+template ztoep_status_t run_forward_spectrum<float>(ztoep_plan_t, int, const float2 *, float2 *, cudaStream_t);
+template ztoep_status_t run_forward_spectrum<double>(ztoep_plan_t, int, const double2 *, double2 *, cudaStream_t);
+
+void free_matvec_ws(ztoep_plan_t p) {
+    free_ws(p->ws32);
+    free_ws(p->ws64);
+}
+
+int64_t edge_row_stride(int64_t NT) { return edge_ldb(NT); }
+
+}  // namespace ztoep

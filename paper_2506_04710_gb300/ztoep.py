@@ -1,0 +1,269 @@
+"""Python binding of the ztoep C-ABI (libztoep.so): argument marshalling only.
+
+The functions carry the C names (`ztoep_plan`, `ztoep_matvec`, `ztoep_solve`,
+...) and take torch tensors (device complex128, or host complex128 for
+`ztoep_solve_host`) plus an optional torch CUDA stream.  Every step of the
+computation runs in the library's CUDA kernels; there is no CPU fallback:
+if the library is missing or fails to load, `lib()` raises.
+
+`Plan` is a small owner object around a plan handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libztoep.so")
+
+ZTOEP_OK = 0
+ZTOEP_ERR_ARG = 1
+ZTOEP_ERR_NOMEM = 2
+ZTOEP_ERR_CUDA = 3
+ZTOEP_ERR_NOCONV = 4
+ZTOEP_ERR_TIMEOUT = 5
+ZTOEP_ERR_UNSUPPORTED = 6
+ZTOEP_ERR_NONFINITE = 7
+ZTOEP_FP64 = 0
+ZTOEP_MIXED = 1
+ZTOEP_FLAG_ZERO_GUESS = 1
+
+
+class ZtoepError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {ztoep_status_string(status)} ({status})")
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("b", ctypes.c_int32),
+                ("n_edge", ctypes.c_int32), ("active", ctypes.c_void_p),
+                ("lx", ctypes.c_int32), ("ly", ctypes.c_int32)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("max_outer", ctypes.c_int32), ("prec", ctypes.c_int32), ("inner_tol", ctypes.c_double),
+                ("timeout_ns", ctypes.c_int64), ("flags", ctypes.c_int32)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("outer", ctypes.c_int32), ("inner_iters", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("b", ctypes.c_int32),
+                ("n_edge", ctypes.c_int32), ("lx", ctypes.c_int32), ("ly", ctypes.c_int32),
+                ("n_toep", ctypes.c_int64), ("n", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
+                ("resident_bytes", ctypes.c_size_t), ("dense_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+c_p = ctypes.c_void_p
+c_i32 = ctypes.c_int32
+
+EXPORTS = ["ztoep_default_opts", "ztoep_plan", "ztoep_matvec", "ztoep_solve", "ztoep_solve_host",
+           "ztoep_forward_spectrum", "ztoep_plan_spectrum", "ztoep_plan_get_info", "ztoep_footprint",
+           "ztoep_plan_destroy", "ztoep_status_string", "ztoep_version"]
+
+
+def lib(path: str | None = None):
+    """Load libztoep.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libztoep.so not built ({p}); run __graft_entry__.build()")
+    L = ctypes.CDLL(p)
+    L.ztoep_default_opts.argtypes = [ctypes.POINTER(SolveOpts)]
+    L.ztoep_default_opts.restype = c_i32
+    L.ztoep_plan.argtypes = [ctypes.POINTER(Desc), c_p, c_p, c_p, c_p, ctypes.POINTER(c_p)]
+    L.ztoep_plan.restype = c_i32
+    L.ztoep_matvec.argtypes = [c_p, c_i32, c_i32, c_p, c_p, c_p]
+    L.ztoep_matvec.restype = c_i32
+    L.ztoep_solve.argtypes = [c_p, ctypes.POINTER(SolveOpts), c_i32, c_p, c_p, ctypes.POINTER(SolveInfo), c_p]
+    L.ztoep_solve.restype = c_i32
+    L.ztoep_solve_host.argtypes = [c_p, ctypes.POINTER(SolveOpts), c_i32, c_p, c_p, ctypes.POINTER(SolveInfo),
+                                   c_p]
+    L.ztoep_solve_host.restype = c_i32
+    L.ztoep_forward_spectrum.argtypes = [c_p, c_i32, c_i32, c_p, c_p, c_p]
+    L.ztoep_forward_spectrum.restype = c_i32
+    L.ztoep_plan_spectrum.argtypes = [c_p, c_p, c_p]
+    L.ztoep_plan_spectrum.restype = c_i32
+    L.ztoep_plan_get_info.argtypes = [c_p, ctypes.POINTER(PlanInfo)]
+    L.ztoep_plan_get_info.restype = c_i32
+    L.ztoep_footprint.argtypes = [ctypes.POINTER(Desc), c_i32, c_i32]
+    L.ztoep_footprint.restype = ctypes.c_size_t
+    L.ztoep_plan_destroy.argtypes = [c_p]
+    L.ztoep_plan_destroy.restype = None
+    L.ztoep_status_string.argtypes = [c_i32]
+    L.ztoep_status_string.restype = ctypes.c_char_p
+    L.ztoep_version.argtypes = []
+    L.ztoep_version.restype = ctypes.c_char_p
+    if path is None:
+        _lib = L
+    return L
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    if t is None:
+        return None
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous(), \
+        "expected a contiguous CUDA complex128 tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    import torch
+    if isinstance(a, torch.Tensor):
+        assert (not a.is_cuda) and a.dtype == torch.complex128 and a.is_contiguous()
+        return ctypes.c_void_p(a.data_ptr())
+    assert a.dtype == np.complex128 and a.flags.c_contiguous
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def make_desc(nx, ny, b, n_edge, active=None, lx=0, ly=0):
+    """Returns (Desc, keepalive) -- keep the second item alive while the Desc is used."""
+    keep = None
+    ap = None
+    if active is not None:
+        keep = np.ascontiguousarray(np.asarray(active, dtype=np.uint8).reshape(-1))
+        assert keep.size == nx * ny
+        ap = keep.ctypes.data
+    return Desc(nx, ny, b, n_edge, ap, lx, ly), keep
+
+
+def _check(st, what):
+    if st != ZTOEP_OK:
+        raise ZtoepError(st, what)
+
+
+def ztoep_version() -> str:
+    return lib().ztoep_version().decode()
+
+
+def ztoep_status_string(status: int) -> str:
+    return lib().ztoep_status_string(status).decode()
+
+
+def ztoep_default_opts() -> SolveOpts:
+    o = SolveOpts()
+    _check(lib().ztoep_default_opts(ctypes.byref(o)), "ztoep_default_opts")
+    return o
+
+
+def ztoep_plan(desc: Desc, T, B, C, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().ztoep_plan(ctypes.byref(desc), _dptr(T), _dptr(B), _dptr(C), _stream_ptr(stream),
+                            ctypes.byref(h)), "ztoep_plan")
+    return h
+
+
+def ztoep_matvec(plan, prec: int, nrhs: int, X, Y, stream=None) -> int:
+    return lib().ztoep_matvec(plan, prec, nrhs, _dptr(X), _dptr(Y), _stream_ptr(stream))
+
+
+def ztoep_solve(plan, opts: SolveOpts, nrhs: int, V, X, info=None, stream=None) -> int:
+    ip = info if info is not None else None
+    return lib().ztoep_solve(plan, ctypes.byref(opts), nrhs, _dptr(V), _dptr(X), ip, _stream_ptr(stream))
+
+
+def ztoep_solve_host(plan, opts: SolveOpts, nrhs: int, V_host, X_host, info=None, stream=None) -> int:
+    ip = info if info is not None else None
+    return lib().ztoep_solve_host(plan, ctypes.byref(opts), nrhs, _hptr(V_host), _hptr(X_host), ip,
+                                  _stream_ptr(stream))
+
+
+def ztoep_forward_spectrum(plan, prec: int, nrhs: int, X, Xhat, stream=None) -> int:
+    return lib().ztoep_forward_spectrum(plan, prec, nrhs, _dptr(X), _dptr(Xhat), _stream_ptr(stream))
+
+
+def ztoep_plan_spectrum(plan, That, stream=None) -> int:
+    return lib().ztoep_plan_spectrum(plan, _dptr(That), _stream_ptr(stream))
+
+
+def ztoep_plan_get_info(plan) -> PlanInfo:
+    info = PlanInfo()
+    _check(lib().ztoep_plan_get_info(plan, ctypes.byref(info)), "ztoep_plan_get_info")
+    return info
+
+
+def ztoep_footprint(desc: Desc, max_nrhs: int, restart: int = 30) -> int:
+    return lib().ztoep_footprint(ctypes.byref(desc), max_nrhs, restart)
+
+
+def ztoep_plan_destroy(plan) -> None:
+    lib().ztoep_plan_destroy(plan)
+
+
+def info_array(nrhs: int):
+    return (SolveInfo * nrhs)()
+
+
+class Plan:
+    """Owns a plan built from a synthetic Problem (or explicit arrays)."""
+
+    def __init__(self, nx, ny, b, n_edge, T, B, C, active=None, lx=0, ly=0, stream=None):
+        self.desc, self._keep = make_desc(nx, ny, b, n_edge, active, lx, ly)
+        self.handle = ztoep_plan(self.desc, T, B, C, stream)
+        self.info = ztoep_plan_get_info(self.handle)
+        self.n = int(self.info.n)
+
+    @classmethod
+    def from_problem(cls, prob, device="cuda", lx=0, ly=0, stream=None):
+        import torch
+        T = torch.from_numpy(np.ascontiguousarray(prob.T)).to(device)
+        B = torch.from_numpy(np.ascontiguousarray(prob.B)).to(device) if prob.n_edge else None
+        C = torch.from_numpy(np.ascontiguousarray(prob.C)).to(device) if prob.n_edge else None
+        act = prob.active if not prob.active.all() else None
+        p = cls(prob.nx, prob.ny, prob.b, prob.n_edge, T, B, C, act, lx, ly, stream)
+        if stream is None:
+            torch.cuda.current_stream().synchronize()
+        else:
+            stream.synchronize()
+        return p
+
+    def matvec(self, X, prec=ZTOEP_FP64, stream=None):
+        import torch
+        Y = torch.empty_like(X)
+        _check(ztoep_matvec(self.handle, prec, X.shape[0], X, Y, stream), "ztoep_matvec")
+        return Y
+
+    def solve(self, V, X=None, opts: SolveOpts | None = None, stream=None, check=True):
+        import torch
+        o = opts or ztoep_default_opts()
+        nrhs = V.shape[0]
+        if X is None:
+            X = torch.zeros_like(V)
+            o.flags |= ZTOEP_FLAG_ZERO_GUESS
+        info = info_array(nrhs)
+        st = ztoep_solve(self.handle, o, nrhs, V, X, info, stream)
+        if check and st not in (ZTOEP_OK,):
+            raise ZtoepError(st, "ztoep_solve")
+        return X, [dict(outer=i.outer, inner_iters=i.inner_iters, status=i.status,
+                        rel_residual=i.rel_residual) for i in info], st
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ztoep_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

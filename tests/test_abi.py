@@ -1,0 +1,69 @@
+"""The C-ABI library builds, loads and exports every symbol its header
+declares (no GPU needed; only host-side calls are made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"ZTOEP_API\s+[\w\s\*]+?\b(ztoep_\w+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2506_04710_gb300 import build, ztoep
+    build.build()
+    return ztoep.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ["ztoep_plan", "ztoep_matvec", "ztoep_solve", "ztoep_solve_host", "ztoep_footprint",
+              "ztoep_plan_destroy", "ztoep_status_string"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in declared_symbols():
+        assert hasattr(lib, n), n
+    from paper_2506_04710_gb300 import ztoep
+    assert sorted(ztoep.EXPORTS) == declared_symbols()
+
+
+def test_host_only_calls(lib):
+    from paper_2506_04710_gb300 import ztoep
+    assert "sm_103a" in ztoep.ztoep_version()
+    assert ztoep.ztoep_status_string(0) == "ok"
+    assert ztoep.ztoep_status_string(4) == "not converged"
+    o = ztoep.ztoep_default_opts()
+    assert o.tol == 1e-8 and o.restart == 30 and o.prec == ztoep.ZTOEP_MIXED
+    d, _ = ztoep.make_desc(32, 32, 64, 512)
+    fp = ztoep.ztoep_footprint(d, 1, 30)
+    # resident spectrum (half the frequencies, FP64+FP32) + B (FP64+FP32) dominate
+    assert 24 * 4096 * 64 * 64 // 2 < fp < 4e9
+    bad, _ = ztoep.make_desc(0, 4, 8, 0)
+    assert ztoep.ztoep_footprint(bad, 1, 30) == 0
+    bad2, _ = ztoep.make_desc(4, 4, 8, 0, lx=6)  # 6 < 2*4-1
+    assert ztoep.ztoep_footprint(bad2, 1, 30) == 0
+
+
+def test_structs_match_header_layout():
+    from paper_2506_04710_gb300 import ztoep
+    assert ctypes.sizeof(ztoep.Desc) == 32
+    assert ctypes.sizeof(ztoep.SolveOpts) == 48
+    assert ctypes.sizeof(ztoep.SolveInfo) == 24
+
+
+def test_no_cpu_fallback_when_library_missing(tmp_path):
+    from paper_2506_04710_gb300 import ztoep
+    with pytest.raises(RuntimeError):
+        ztoep.lib(str(tmp_path / "missing.so"))
