@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched block-Toeplitz solve on one GB300 per rank.
+
+Workload (one step): solve Z x = v for the 32 x 32 array, b = 64 basis
+functions per element (65,536 Toeplitz unknowns) and 512 edge unknowns, one
+right-hand side of ones, mixed precision (FP32 FFT products inside GMRES(30),
+FP64 refinement) to relative residual 1e-8.  The plan (the FFT'd generating
+blocks, B and C) is built once and stays resident, as the method intends; its
+build time is reported separately.
+
+Printed (rank 0, one JSON line): solves/s of the mixed path (`value`), the
+same through the host-buffer C-ABI call with the copies inside the timed
+region (`e2e`), the plain FP64 path on the same inputs, the FFT-matvec GB/s,
+p50/p99 solve latency, the roofline of the dominant kernel measured live with
+CUDA events, SM clocks during the timed region, and the CPU oracle timed on a
+bounded sample (`cpu_baseline`).
+
+`--impl reference` times the CPU FP64 oracle instead (direct products of the
+same system on the host cores; each step is a row sample of one product,
+extrapolated to a full solve).
+
+Multi-GPU (`torchrun --nproc-per-node N`): independent replicas, one system
+per rank, no collective on the data path (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "c2_32x32_b64"
+WORKLOAD_DESC = ("32x32 array, b=64 (65,536 Toeplitz + 512 edge unknowns), 1 RHS of ones, "
+                 "mixed FP32/FP64 GMRES(30)-IR to rel. residual 1e-8")
+METRIC = "solves/s & FFT-matvec HBM GB/s, mixed vs FP64 plain at 1e-8 residual; p50/p99"
+# Products of one FP64 GMRES(30) solve of this system to 1e-8 (300 iterations
+# + 11 true-residual products), used to extrapolate the CPU oracle's product
+# time to a solve in the reference arm, which runs no GPU code.
+PRODUCTS_PER_SOLVE_FP64 = 311
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def dist_setup():
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region."""
+
+    def __init__(self, gpu_id: str):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", gpu_id, f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def oracle_product_seconds(prob, fraction: float):
+    """CPU oracle: direct FP64 product on a row sample; returns (sample s, full-product s)."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import numpy as np
+    import oracle
+    step = max(1, int(round(1.0 / fraction)))
+    rows = np.arange(0, prob.n, step)
+    t = time.perf_counter()
+    oracle.matvec_rows(prob, prob.V, rows)
+    dt = time.perf_counter() - t
+    return dt, dt * prob.n / len(rows), len(rows)
+
+
+def omp_threads():
+    return env_int("OMP_NUM_THREADS", os.cpu_count() or 1)
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_2506_04710_gb300 import synth
+    prob, tol = synth.config_problem(WORKLOAD)
+    frac = 1.0 / 16
+    for _ in range(max(0, args.warmup)):
+        oracle_product_seconds(prob, frac / 4)
+    per_solve = []
+    sample_s = 0.0
+    for _ in range(args.steps):
+        dt, full, nrows = oracle_product_seconds(prob, frac)
+        sample_s += dt
+        per_solve.append(full * PRODUCTS_PER_SOLVE_FP64)
+    total = sum(per_solve)
+    value = args.steps / total
+    sample = (f"per step: direct FP64 product (oracle_matvec_rows) on {nrows} of {prob.n} rows (1/16), "
+              f"scaled to a full product and by {PRODUCTS_PER_SOLVE_FP64} products per GMRES(30) solve")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": WORKLOAD_DESC},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": omp_threads(), "kind": "oracle",
+                             "sample": sample, "sample_seconds": sample_s},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2506_04710_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2506_04710_gb300 import synth, ztoep
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob, tol = synth.config_problem(WORKLOAD)
+    stream = torch.cuda.current_stream(dev)
+
+    t0 = time.perf_counter()
+    plan = ztoep.Plan.from_problem(prob, device=dev)
+    torch.cuda.synchronize(dev)
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    V = torch.from_numpy(prob.V.copy()).to(dev)
+    X = torch.zeros_like(V)
+    N, nrhs = prob.n, prob.nrhs
+
+    def opts(prec):
+        o = ztoep.ztoep_default_opts()
+        o.prec, o.tol, o.restart = prec, tol, args.restart
+        o.flags = ztoep.ZTOEP_FLAG_ZERO_GUESS
+        return o
+
+    o_mixed = opts(ztoep.ZTOEP_MIXED)
+    info = ztoep.info_array(nrhs)
+
+    def solve(o):
+        st = ztoep.ztoep_solve(plan.handle, o, nrhs, V, X, info, stream)
+        if st != 0:
+            raise RuntimeError(f"solve failed: {ztoep.ztoep_status_string(st)}")
+
+    for _ in range(max(3, args.warmup)):
+        solve(o_mixed)
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region: mixed solves
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(getattr(props, "uuid", local))
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
+        gpu_id = "GPU-" + gpu_id
+    clocks = Clocks(gpu_id)
+    ztoep.ztoep_timing_reset()
+    ztoep.ztoep_timing_enable(1 << ztoep.K_EDGE | 1 << ztoep.K_BLOCKPROD | 1 << ztoep.K_FFT | 1 << ztoep.K_ARNOLDI)
+    launches0 = ztoep.ztoep_launch_count()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    evs[0].record(stream)
+    for k in range(args.steps):
+        solve(o_mixed)
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    launches = ztoep.ztoep_launch_count() - launches0
+    ztoep.ztoep_timing_enable(0)
+    clk = clocks.stop()
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    total_ms = allmax(world, sum(step_ms))
+    value = world * args.steps * nrhs / (total_ms / 1e3)
+    iters = info[0].inner_iters
+    outer = info[0].outer
+    relres = info[0].rel_residual
+    kt = {}
+    for name, c in (("fft", ztoep.K_FFT), ("blockprod", ztoep.K_BLOCKPROD), ("edge", ztoep.K_EDGE),
+                    ("arnoldi", ztoep.K_ARNOLDI)):
+        n, ms = ztoep.ztoep_timing_read(c)
+        kt[name] = {"launches": n, "ms": ms}
+
+    # ---- roofline of the edge-coupling kernel (one pass over B, FP32), the
+    # largest HBM stream of the product
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    E, NT = prob.n_edge, prob.n_toep
+    edge_bytes = E * NT * 8 + 2 * NT * 8 * nrhs + E * 8 * nrhs
+    e_n, e_ms = kt["edge"]["launches"], kt["edge"]["ms"]
+    edge_gbs = edge_bytes * e_n / (e_ms / 1e3) / 1e9 if e_ms > 0 else None
+    b, F = prob.b, plan.info.lx * plan.info.ly
+    bp_bytes = plan.info.n_pairs * b * b * 8 + 2 * F * b * nrhs * 8
+    bp_n, bp_ms = kt["blockprod"]["launches"], kt["blockprod"]["ms"]
+    bp_gbs = bp_bytes * bp_n / (bp_ms / 1e3) / 1e9 if bp_ms > 0 else None
+    roofline = {"kernel": "k_edge<float> (B x_T and B^T x_E, one pass over B)", "bound": "hbm",
+                "achieved": edge_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": (edge_gbs / hbm) if edge_gbs else None, "traffic": None,
+                "bytes_per_launch": edge_bytes, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+
+    # ---- FFT-matvec GB/s (FP32 product, algorithmic bytes per product)
+    Xm = torch.from_numpy(np.ones((nrhs, N), np.complex128)).to(dev)
+    Ym = torch.empty_like(Xm)
+    ws32 = plan  # noqa: F841  (workspace lives in the plan)
+    for _ in range(3):
+        ztoep.ztoep_matvec(plan.handle, ztoep.ZTOEP_MIXED, nrhs, Xm, Ym, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nmv = 30
+    e0.record(stream)
+    for _ in range(nmv):
+        ztoep.ztoep_matvec(plan.handle, ztoep.ZTOEP_MIXED, nrhs, Xm, Ym, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    mv_ms = e0.elapsed_time(e1) / nmv
+    That_bytes = plan.info.n_pairs * b * b * 8
+    mv_bytes = That_bytes + 2 * NT * nrhs * 8 + 4 * F * b * nrhs * 8 + (E * NT + E * E) * 8 + 4 * E * nrhs * 8
+    mv_gbs = mv_bytes / (mv_ms / 1e3) / 1e9
+
+    # ---- FP64 plain path on the same inputs
+    o64 = opts(ztoep.ZTOEP_FP64)
+    solve(o64)
+    torch.cuda.synchronize(dev)
+    k64 = max(2, args.steps // 3)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(k64):
+        solve(o64)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    fp64_ms = allmax(world, f0.elapsed_time(f1)) / k64
+    fp64_value = world * nrhs / (fp64_ms / 1e3)
+    fp64_iters, fp64_outer = info[0].inner_iters, info[0].outer
+
+    # ---- end to end through the host-buffer C-ABI call (copies in the timed region)
+    Vh = torch.from_numpy(prob.V.copy()).pin_memory()
+    Xh = torch.zeros_like(Vh).pin_memory()
+    for _ in range(2):
+        ztoep.ztoep_solve_host(plan.handle, o_mixed, nrhs, Vh, Xh, info, stream)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st = ztoep.ztoep_solve_host(plan.handle, o_mixed, nrhs, Vh, Xh, info, stream)
+        assert st == 0
+    torch.cuda.synchronize(dev)
+    e2e_s = allmax(world, time.perf_counter() - t0)
+    barrier(world)
+    e2e_value = world * args.steps * nrhs / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, full, nrows = oracle_product_seconds(prob, 1.0)
+        products = fp64_iters + fp64_outer
+        cpu = {"value": 1.0 / (full * products), "unit": "solves/s", "cores": omp_threads(), "kind": "oracle",
+               "sample": (f"one direct FP64 product of the full system (oracle_matvec_rows over all "
+                          f"{nrows} rows, {dt:.1f} s), scaled by the {products} products of the FP64 "
+                          f"GMRES(30) solve")}
+
+    if rank == 0:
+        s_sorted = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64 products + f64 refinement",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "nx": prob.nx, "ny": prob.ny, "b": prob.b, "n_edge": E,
+                       "nrhs": nrhs, "tol": tol, "restart": args.restart, "lx": plan.info.lx,
+                       "ly": plan.info.ly,
+                       "l2": "inputs larger than L2: FP32 working set per product "
+                             f"{(That_bytes + E * NT * 8) / 1e6:.0f} MB > 129 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(nrhs * N * 16),
+                    "d2h_bytes_per_step": int(nrhs * N * 16)},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "latency_ms": {"p50": s_sorted[len(s_sorted) // 2],
+                           "p99": s_sorted[min(len(s_sorted) - 1, int(0.99 * len(s_sorted)))]},
+            "solve": {"iterations": iters, "sweeps": outer, "rel_residual": relres},
+            "fp64_plain": {"value": fp64_value, "ms_per_step": fp64_ms, "iterations": fp64_iters,
+                           "sweeps": fp64_outer},
+            "speedup_vs_fp64": value / fp64_value,
+            "fft_matvec": {"GB/s": mv_gbs, "us": mv_ms * 1e3, "bytes": mv_bytes,
+                           "frac_of_hbm": mv_gbs / hbm},
+            "blockprod": {"GB/s": bp_gbs, "bytes_per_launch": bp_bytes},
+            "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in kt.items()},
+            "plan_ms": plan_ms,
+            "launches_per_step": launches / args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

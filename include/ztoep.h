@@ -190,6 +190,24 @@ ZTOEP_API void ztoep_plan_destroy(ztoep_plan_t plan);
 
 ZTOEP_API const char *ztoep_status_string(ztoep_status_t status);
 
+/* ---- Instrumentation (not part of the method) ----
+ * Kernel classes: 0 FFT passes, 1 per-frequency block products, 2 edge
+ * coupling (one pass over B), 3 Arnoldi/Givens steps, 4 everything else. */
+
+/* Number of CUDA kernels this library has launched in this process. */
+ZTOEP_API uint64_t ztoep_launch_count(void);
+
+/* Time the launches of the classes whose bit is set in `mask` with a CUDA
+ * event pair on the launching stream (0 = off, the default). */
+ZTOEP_API void ztoep_timing_enable(int32_t mask);
+
+/* Forget accumulated timings (waits for pending events). */
+ZTOEP_API void ztoep_timing_reset(void);
+
+/* Timed launches of class `cls` since the last reset and their summed device
+ * time in ms (waits for pending events).  Errors: ARG. */
+ZTOEP_API ztoep_status_t ztoep_timing_read(int32_t cls, uint64_t *timed_launches, double *total_ms);
+
 /* Library version string, e.g. "ztoep 0.1 sm_103a". */
 ZTOEP_API const char *ztoep_version(void);
 

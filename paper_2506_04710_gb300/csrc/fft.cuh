@@ -6,6 +6,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "instrument.cuh"
 
 namespace ztoep {
 
@@ -157,6 +158,7 @@ ztoep_status_t launch_fft_pass(const Fft1D &pl, const cplx_t<R> *tw, int lib, bo
                                      200 * 1024));
         attr_set = true;
     }
+    KScope ks(K_FFT, s);
     k_fft_pass<R, Ld, St><<<grid, 256, smem, s>>>(pl, tw, lib, inv ? 1 : 0, ld, st);
     ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;

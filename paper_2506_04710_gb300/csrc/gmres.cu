@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "instrument.cuh"
 
 namespace ztoep {
 
@@ -440,17 +441,19 @@ static ztoep_status_t ensure_solve_ws(ztoep_plan_t p, int nrhs, int m) {
 }
 
 template <int ELEM> struct Launch {
-    static ztoep_status_t vnorm(const GArgs &a, dim3 g, cudaStream_t s) { k_vnorm<ELEM><<<g, NT_, 0, s>>>(a); return ok(); }
-    static ztoep_status_t residual(const GArgs &a, dim3 g, int zero, cudaStream_t s) { k_residual<ELEM><<<g, NT_, 0, s>>>(a, zero); return ok(); }
-    static ztoep_status_t start(const GArgs &a, dim3 g, cudaStream_t s) { k_start<ELEM><<<g, NT_, 0, s>>>(a); return ok(); }
+    static ztoep_status_t vnorm(const GArgs &a, dim3 g, cudaStream_t s) { KScope ks(K_MISC, s); k_vnorm<ELEM><<<g, NT_, 0, s>>>(a); return ok(); }
+    static ztoep_status_t residual(const GArgs &a, dim3 g, int zero, cudaStream_t s) { KScope ks(K_MISC, s); k_residual<ELEM><<<g, NT_, 0, s>>>(a, zero); return ok(); }
+    static ztoep_status_t start(const GArgs &a, dim3 g, cudaStream_t s) { KScope ks(K_MISC, s); k_start<ELEM><<<g, NT_, 0, s>>>(a); return ok(); }
     static ztoep_status_t arnoldi(const GArgs &a, dim3 g, int j, cudaStream_t s) {
+        KScope ks(K_ARNOLDI, s);
+        ks.add(4);
         k_gs1<ELEM><<<g, NT_, 0, s>>>(a, j);
         k_gs_update<ELEM, true><<<g, NT_, 0, s>>>(a, j);
         k_gs_update<ELEM, false><<<g, NT_, 0, s>>>(a, j);
         k_normalize<ELEM><<<g, NT_, 0, s>>>(a, j);
         return ok();
     }
-    static ztoep_status_t update_x(const GArgs &a, dim3 g, cudaStream_t s) { k_update_x<ELEM><<<g, NT_, 0, s>>>(a); return ok(); }
+    static ztoep_status_t update_x(const GArgs &a, dim3 g, cudaStream_t s) { KScope ks(K_MISC, s); k_update_x<ELEM><<<g, NT_, 0, s>>>(a); return ok(); }
     static ztoep_status_t ok() { ZT_CUDA(cudaGetLastError()); return ZTOEP_OK; }
 };
 

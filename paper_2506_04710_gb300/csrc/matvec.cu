@@ -297,12 +297,14 @@ static unsigned grid_for(int64_t n, int threads) {
 
 ztoep_status_t launch_c128_to_c64(const double2 *src, float2 *dst, int64_t n, cudaStream_t s) {
     if (n <= 0) return ZTOEP_OK;
+    KScope ks(K_MISC, s);
     k_c128_to_c64<<<grid_for(n, 256), 256, 0, s>>>(src, dst, n);
     ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
 }
 ztoep_status_t launch_c64_to_c128(const float2 *src, double2 *dst, int64_t n, cudaStream_t s) {
     if (n <= 0) return ZTOEP_OK;
+    KScope ks(K_MISC, s);
     k_c64_to_c128<<<grid_for(n, 256), 256, 0, s>>>(src, dst, n);
     ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
@@ -402,6 +404,7 @@ static ztoep_status_t launch_blockprod(ztoep_plan_t p, int nrhs, cplx_t<R> *Xh, 
         ZT_CUDA(cudaFuncSetAttribute(k_blockprod<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         attr = true;
     }
+    KScope ks(K_BLOCKPROD, s);
     k_blockprod<R><<<p->npairs, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, p->b, nrhs, rch);
     ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
@@ -420,6 +423,7 @@ static ztoep_status_t launch_edge(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, 
     for (int r0 = 0; r0 < nrhs; r0 += 4) {
         const int rc = std::min(4, nrhs - r0);
         dim3 g(ntile, nsplit);
+        KScope ks(K_EDGE, s);
         if (rc == 1)
             k_edge<R, 1><<<g, 256, 0, s>>>(x, b_of<R>(p), ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc, eps);
         else if (rc == 2)
@@ -429,6 +433,7 @@ static ztoep_status_t launch_edge(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, 
         ZT_CUDA(cudaGetLastError());
     }
     dim3 gf((p->E + 7) / 8, nrhs);
+    KScope ks(K_MISC, s);
     k_edge_finish<R><<<gf, 256, 0, s>>>(x, c_of<R>(p), Ep, y, p->NT, p->E, p->N, nrhs, ntile);
     ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;

@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "instrument.cuh"
 
 namespace ztoep {
 
@@ -313,6 +314,7 @@ static ztoep_status_t plan_build(ztoep_plan_t p, const ztoep_desc_t *d, const do
         ZT_CUDA(cudaMemcpy2DAsync(p->B64, sizeof(double2) * ldb, B, sizeof(double2) * p->NT,
                                   sizeof(double2) * p->NT, p->E, cudaMemcpyDeviceToDevice, s));
         if (p->masked) {
+            KScope ks(K_MISC, s);
             k_zero_columns<<<1024, 256, 0, s>>>(p->B64, ldb, p->E, p->active, p->nx * p->ny, p->b);
             ZT_CUDA(cudaGetLastError());
         }
@@ -399,6 +401,7 @@ ztoep_status_t ztoep_forward_spectrum(ztoep_plan_t p, int32_t prec, int32_t nrhs
 
 ztoep_status_t ztoep_plan_spectrum(ztoep_plan_t p, void *That, void *stream) {
     if (!p || !That) return ZTOEP_ERR_ARG;
+    KScope ks(K_MISC, (cudaStream_t)stream);
     k_expand_spectrum<<<1024, 256, 0, (cudaStream_t)stream>>>(p->That64, p->rep, (double2 *)That, p->F, p->b);
     ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;

@@ -67,7 +67,10 @@ c_i32 = ctypes.c_int32
 
 EXPORTS = ["ztoep_default_opts", "ztoep_plan", "ztoep_matvec", "ztoep_solve", "ztoep_solve_host",
            "ztoep_forward_spectrum", "ztoep_plan_spectrum", "ztoep_plan_get_info", "ztoep_footprint",
-           "ztoep_plan_destroy", "ztoep_status_string", "ztoep_version"]
+           "ztoep_plan_destroy", "ztoep_status_string", "ztoep_version", "ztoep_launch_count",
+           "ztoep_timing_enable", "ztoep_timing_reset", "ztoep_timing_read"]
+
+K_FFT, K_BLOCKPROD, K_EDGE, K_ARNOLDI, K_MISC = range(5)
 
 
 def lib(path: str | None = None):
@@ -104,6 +107,14 @@ def lib(path: str | None = None):
     L.ztoep_status_string.restype = ctypes.c_char_p
     L.ztoep_version.argtypes = []
     L.ztoep_version.restype = ctypes.c_char_p
+    L.ztoep_launch_count.argtypes = []
+    L.ztoep_launch_count.restype = ctypes.c_uint64
+    L.ztoep_timing_enable.argtypes = [c_i32]
+    L.ztoep_timing_enable.restype = None
+    L.ztoep_timing_reset.argtypes = []
+    L.ztoep_timing_reset.restype = None
+    L.ztoep_timing_read.argtypes = [c_i32, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]
+    L.ztoep_timing_read.restype = c_i32
     if path is None:
         _lib = L
     return L
@@ -208,6 +219,25 @@ def ztoep_footprint(desc: Desc, max_nrhs: int, restart: int = 30) -> int:
 
 def ztoep_plan_destroy(plan) -> None:
     lib().ztoep_plan_destroy(plan)
+
+
+def ztoep_launch_count() -> int:
+    return int(lib().ztoep_launch_count())
+
+
+def ztoep_timing_enable(mask: int) -> None:
+    lib().ztoep_timing_enable(mask)
+
+
+def ztoep_timing_reset() -> None:
+    lib().ztoep_timing_reset()
+
+
+def ztoep_timing_read(cls: int) -> tuple[int, float]:
+    n = ctypes.c_uint64()
+    ms = ctypes.c_double()
+    _check(lib().ztoep_timing_read(cls, ctypes.byref(n), ctypes.byref(ms)), "ztoep_timing_read")
+    return int(n.value), float(ms.value)
 
 
 def info_array(nrhs: int):
