@@ -145,6 +145,27 @@ ZTOEP_API ztoep_status_t ztoep_plan(const ztoep_desc_t *desc, const void *T, con
 ZTOEP_API ztoep_status_t ztoep_matvec(ztoep_plan_t plan, int32_t prec, int32_t nrhs, const void *X, void *Y,
                             void *stream);
 
+/* Edge-coupling part of the FP64 product, allocating nothing (the paper has
+ * no counterpart; this is a service for callers that cannot allocate device
+ * memory at call time: code inside a CUDA stream capture in global mode,
+ * where cudaMalloc is an error, hosts that forbid allocation after start-up,
+ * and frameworks whose memory pool owns all device memory).
+ *   Y[r][t]       = sum_e B[e][t] x_E[r][e]                 (t < N_T; 0 on absent elements)
+ *   Y[r][N_T + e] = sum_t B[e][t] x_T[r][t] + sum_e' C[e][e'] x_E[r][e']
+ *   X, Y: device complex128 [nrhs][N], distinct.  The plan's device must be
+ *   current.  The partial sums live in a fixed 16 MiB device array that every
+ *   device holding this library keeps until the process exits; nrhs is
+ *   limited by it (about 4 for a 32x32 array with b = 64 and 512 edge
+ *   unknowns) and a call that would need more returns ZTOEP_ERR_NOMEM without
+ *   doing anything.  The first call on a device looks up the array's device
+ *   address (cudaGetSymbolAddress); make that first call before any stream
+ *   capture.  All calls share the array: calls whose work overlaps on the GPU
+ *   (other streams, other threads) race and must be serialised by the caller.
+ *   No cudaMalloc, cudaFree or allocating library routine is called.
+ * Errors: ARG, NOMEM (scratch cap), CUDA, UNSUPPORTED (device index >= 64). */
+ZTOEP_API ztoep_status_t ztoep_edge_product_noalloc(ztoep_plan_t plan, int32_t nrhs, const void *X, void *Y,
+                                                    void *stream);
+
 /* Solve Z' X = V for nrhs right-hand sides.
  *   V: device complex128 [nrhs][N].
  *   X: device complex128 [nrhs][N]; initial guess on entry, solution on

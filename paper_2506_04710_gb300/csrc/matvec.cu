@@ -495,3 +495,89 @@ void free_matvec_ws(ztoep_plan_t p) {
 int64_t edge_row_stride(int64_t NT) { return edge_ldb(NT); }
 
 }  // namespace ztoep
+
+// ------------------------------------------------------------ allocation-free edge product
+// Some callers cannot allocate device memory when they call into the library:
+// code running inside a CUDA stream capture in global capture mode (where a
+// cudaMalloc is an error), real-time or embedded hosts that forbid allocation
+// after start-up, and frameworks whose memory pool owns every device byte.
+// For them ztoep_edge_product_noalloc computes the edge-coupling part of the
+// FP64 product with its partial sums in the fixed array below instead of the
+// plan's lazily allocated workspace.  The array is 16 MiB, lives on every
+// device that loads this library until the process exits, is shared by all
+// calls (so two calls whose work overlaps on the GPU race on it) and keeps
+// whatever the last call left in it; every call overwrites all the scratch it
+// reads, so nothing in it has to start at zero.
+namespace ztoep {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static void *g_noalloc_addr[kMaxDevices];
+static std::mutex g_noalloc_mu;
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (host code only sees a host-side stand-in for the symbol).
+static ztoep_status_t noalloc_scratch(int dev, void **out) {
+    if (dev < 0 || dev >= kMaxDevices) return ZTOEP_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) return ZTOEP_ERR_CUDA;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return ZTOEP_OK;
+}
+
+// y[r][t] = sum_s ET[s][r][t] (the B^T x_E rows), t < NT.
+__global__ void k_sum_splits(const double2 *__restrict__ ET, double2 *__restrict__ y, int64_t NT, int64_t N,
+                             int nrhs, int nsplit) {
+    const int64_t total = (int64_t)nrhs * NT;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = k / NT, t = k - r * NT;
+        double2 s = ET[k];
+        for (int sp = 1; sp < nsplit; ++sp) s = s + ET[(int64_t)sp * total + k];
+        y[r * N + t] = s;
+    }
+}
+
+static size_t round256(size_t n) { return (n + 255) / 256 * 256; }
+
+}  // namespace ztoep
+
+extern "C" ztoep_status_t ztoep_edge_product_noalloc(ztoep_plan_t p, int32_t nrhs, const void *X, void *Y,
+                                                     void *stream) {
+    using namespace ztoep;
+    if (!p || !X || !Y || nrhs < 1 || X == Y) return ZTOEP_ERR_ARG;
+    int dev = -1;
+    ZT_CUDA(cudaGetDevice(&dev));
+    if (dev != p->device) return ZTOEP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    double2 *y = (double2 *)Y;
+    const double2 *x = (const double2 *)X;
+    if (p->E == 0) {  // no edge unknowns: the edge part of the product is zero
+        ZT_CUDA(cudaMemsetAsync(y, 0, sizeof(double2) * (size_t)nrhs * p->N, s));
+        return ZTOEP_OK;
+    }
+    const int ntile = edge_ntile(p, sizeof(double2));
+    const int nsplit = edge_nsplit(p, ntile);
+    const size_t et_bytes = round256(sizeof(double2) * (size_t)nsplit * nrhs * p->NT);
+    const size_t ep_bytes = round256(sizeof(double2) * (size_t)ntile * nrhs * p->E);
+    if (et_bytes + ep_bytes > kNoAllocScratchBytes) return ZTOEP_ERR_NOMEM;
+    void *base = nullptr;
+    ZT_TRY(noalloc_scratch(dev, &base));
+    MatvecWs w{};  // views into the fixed scratch; owns nothing
+    w.ET = base;
+    w.Ep = (unsigned char *)base + et_bytes;
+    std::lock_guard<std::mutex> lk(p->mu);
+    ZT_TRY(launch_edge<double>(p, nrhs, x, y, w, s));
+    KScope ks(K_MISC, s);
+    k_sum_splits<<<grid_for((int64_t)nrhs * p->NT, 256), 256, 0, s>>>((const double2 *)w.ET, y, p->NT, p->N,
+                                                                      nrhs, nsplit);
+    ZT_CUDA(cudaGetLastError());
+    return ZTOEP_OK;
+}

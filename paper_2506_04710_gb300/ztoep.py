@@ -68,7 +68,7 @@ c_i32 = ctypes.c_int32
 EXPORTS = ["ztoep_default_opts", "ztoep_plan", "ztoep_matvec", "ztoep_solve", "ztoep_solve_host",
            "ztoep_forward_spectrum", "ztoep_plan_spectrum", "ztoep_plan_get_info", "ztoep_footprint",
            "ztoep_plan_destroy", "ztoep_status_string", "ztoep_version", "ztoep_launch_count",
-           "ztoep_timing_enable", "ztoep_timing_reset", "ztoep_timing_read"]
+           "ztoep_timing_enable", "ztoep_timing_reset", "ztoep_timing_read", "ztoep_edge_product_noalloc"]
 
 K_FFT, K_BLOCKPROD, K_EDGE, K_ARNOLDI, K_MISC = range(5)
 
@@ -107,6 +107,8 @@ def lib(path: str | None = None):
     L.ztoep_status_string.restype = ctypes.c_char_p
     L.ztoep_version.argtypes = []
     L.ztoep_version.restype = ctypes.c_char_p
+    L.ztoep_edge_product_noalloc.argtypes = [c_p, c_i32, c_p, c_p, c_p]
+    L.ztoep_edge_product_noalloc.restype = c_i32
     L.ztoep_launch_count.argtypes = []
     L.ztoep_launch_count.restype = ctypes.c_uint64
     L.ztoep_timing_enable.argtypes = [c_i32]
@@ -219,6 +221,13 @@ def ztoep_footprint(desc: Desc, max_nrhs: int, restart: int = 30) -> int:
 
 def ztoep_plan_destroy(plan) -> None:
     lib().ztoep_plan_destroy(plan)
+
+
+def ztoep_edge_product_noalloc(plan, nrhs: int, X, Y, stream=None) -> int:
+    """Edge-coupling part of the FP64 product with no device allocation (for
+    callers that cannot allocate at call time, e.g. inside a global-mode stream
+    capture); scratch is a fixed 16 MiB device array shared by all calls."""
+    return lib().ztoep_edge_product_noalloc(plan, nrhs, _dptr(X), _dptr(Y), _stream_ptr(stream))
 
 
 def ztoep_launch_count() -> int:
