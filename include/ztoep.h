@@ -175,8 +175,12 @@ ZTOEP_API ztoep_status_t ztoep_edge_product_noalloc(ztoep_plan_t plan, int32_t n
  * MIXED: FP64 refinement x <- x + d, d from a GMRES(m) cycle on Z d = r
  *   with FP32 products and FP64 Arnoldi/Givens/least squares, r = v - Z x in
  *   FP64 between cycles.
- * Returns the worst per-RHS status.  The call returns after the solve has
- * finished on `stream` (it synchronises the stream between cycles). */
+ * The whole refinement/GMRES loop runs on the device as one CUDA graph
+ * (loops as conditional graph nodes, instantiated once per precision, RHS
+ * count and restart length and cached in the plan); V is copied into the
+ * plan's buffers first and the solution copied back to X at the end.
+ * timeout_ns is enforced on the device (%globaltimer) between iterations.
+ * Returns the worst per-RHS status after synchronising `stream` once. */
 ZTOEP_API ztoep_status_t ztoep_solve(ztoep_plan_t plan, const ztoep_solve_opts_t *opts, int32_t nrhs,
                            const void *V, void *X, ztoep_solve_info_t *info, void *stream);
 

@@ -101,9 +101,11 @@ struct MatvecWs {  // per-precision matvec workspace, sized for `cap` RHS
 
 struct SolveWs {  // Krylov workspace, sized for `cap` RHS and restart `m`
     int cap = 0, m = 0;
-    double2 *Vb = nullptr;     // [(m+1)][cap][N] Krylov basis
-    double2 *w = nullptr;      // [cap][N] FP64 work vector
-    double2 *r = nullptr;      // [cap][N] residual / FP64 scratch
+    double2 *Vb = nullptr;     // [(m+1)][cap][N] unnormalised Krylov basis
+    double2 *w = nullptr;      // [cap][N] FP64 product output
+    double2 *xin64 = nullptr;  // [cap][N] FP64 product input (next basis vector)
+    double2 *vbuf = nullptr;   // [cap][N] right-hand sides (graph-owned copy)
+    double2 *xbuf = nullptr;   // [cap][N] iterate (graph-owned copy)
     double2 *H = nullptr;      // [cap][m+1][m] Hessenberg (rotated to R)
     double2 *cs = nullptr;     // [cap][m]
     double2 *sn = nullptr;     // [cap][m]
@@ -112,12 +114,21 @@ struct SolveWs {  // Krylov workspace, sized for `cap` RHS and restart `m`
     double2 *h1 = nullptr;     // [cap][m+1]
     double2 *h2 = nullptr;     // [cap][m+1]
     double2 *part = nullptr;   // [cap][nchunk][m+2] per-CTA partial sums
-    double *nrm = nullptr;     // [cap][4] scalars: ||v||, beta0, target, ||r||
+    double *nrm = nullptr;     // [cap][8] scalars, then [cap][m+1] basis norms
     int *st = nullptr;         // [cap][8] per-RHS state
-    unsigned *cnt = nullptr;   // [cap] last-CTA counters
-    int *hst = nullptr;        // host pinned mirror of st
+    unsigned *cnt = nullptr;   // [cap][4] last-CTA counters
+    void *ctl = nullptr;       // device solve control block
+    int *hst = nullptr;        // host pinned mirror of st (+ control words)
     double *hnrm = nullptr;    // host pinned mirror of nrm
     size_t bytes = 0;
+};
+
+// One instantiated solve graph (per precision, RHS count and restart length).
+struct SolveGraph {
+    int prec = -1, nrhs = 0, m = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t k_fixed = 0, k_sweep = 0, k_iter = 0, k_first_product = 0;  // kernels per part
 };
 
 struct PlanImpl;
@@ -147,7 +158,10 @@ struct ztoep_plan_s {
     size_t resident = 0;
     ztoep::MatvecWs ws32, ws64;
     ztoep::SolveWs sws;
+    ztoep::SolveGraph graphs[4];    // small cache of instantiated solve graphs
+    int graph_next = 0;
     cudaStream_t side = nullptr;    // edge-coupling branch of the matvec
+    cudaStream_t cap = nullptr;     // stream used to capture solve graphs
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::mutex mu;
 };
@@ -167,6 +181,7 @@ namespace ztoep {
     } while (0)
 
 ztoep_status_t dalloc(void **p, size_t bytes, size_t *acc);
+void free_solve_graphs(ztoep_plan_t p);  // cached graphs bake in workspace pointers
 
 // Matvec in one precision on plan-internal buffers: y = Z' x, x/y [nrhs][N].
 template <typename R>

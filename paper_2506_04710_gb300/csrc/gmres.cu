@@ -3,15 +3,21 @@
 // second-level Toeplitz structure of A, with the FFT product for Z').
 //
 // Outer sweep (FP64):  r = v - Z' x (FP64 product), ||r|| per RHS, stop test.
-// Inner cycle:         GMRES(m) on Z' d = r, Arnoldi by classical
-//                      Gram-Schmidt with one reorthogonalisation (CGS2,
-//                      Giraud, Langou & Rozloznik 2005), Givens rotations,
-//                      least squares R y = g, x <- x + V y.  The products inside
-//                      the cycle are FP32 (MIXED) or FP64 (FP64); the Arnoldi,
-//                      rotations and updates are always FP64.
+// Inner cycle:         GMRES(m) on Z' d = r (Saad & Schultz 1986) with
+//                      classical Gram-Schmidt and selective
+//                      reorthogonalisation (a second pass only when the first
+//                      one cancels more than 1 - 1/sqrt(2) of ||w||, the
+//                      criterion of Daniel, Gragg, Kaufman & Stewart 1976),
+//                      Givens rotations, least squares R y = g, x <- x + V y.
+//                      The products inside the cycle are FP32 (MIXED) or FP64
+//                      (FP64); Arnoldi, rotations and updates are FP64.
+// The basis is kept unnormalised: u_k with v_k = u_k / beta_k, so no kernel
+// pass is spent on normalising; every use of v_k folds 1/beta_k into its
+// coefficient.
 // Every kernel is batched over the RHS (grid.y) and each RHS stops on its own
 // flag.  Cross-CTA reductions use the last-CTA-done pattern (atomic ticket,
-// no waiting), so the summation order is fixed and results are reproducible.
+// no waiting), so the summation order is fixed and results do not depend on
+// the batch.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -22,55 +28,103 @@
 
 namespace ztoep {
 
-enum { ST_ACTIVE = 0, ST_JLEN = 1, ST_ITERS = 2, ST_STATUS = 3, ST_OUTER = 4, ST_PENDING = 5, ST_STRIDE = 8 };
+enum { ST_ACTIVE = 0, ST_JLEN = 1, ST_ITERS = 2, ST_STATUS = 3, ST_OUTER = 4, ST_PENDING = 5, ST_REORTH = 6,
+       ST_STRIDE = 8 };
 enum { RS_RUNNING = 0, RS_CONVERGED = 1, RS_NONFINITE = 2, RS_MAXITER = 3 };
-enum { NM_VNORM = 0, NM_BETA0 = 1, NM_TARGET = 2, NM_RNORM = 3, NM_BETA = 4, NM_STRIDE = 8 };
+enum { NM_VNORM = 0, NM_TARGET = 2, NM_RNORM = 3, NM_W0 = 5, NM_STRIDE = 8 };
 enum { CNT_STRIDE = 4 };
+constexpr double kReorthEta = 0.70710678118654752440;  // 1/sqrt(2)
+
+// Device-side control of one solve (written by the host before each launch of
+// the solve graph; loop counters advanced by the control kernels).
+struct SolveCtl {
+    int j;               // current inner iteration of the running cycle
+    int sweeps;          // true-residual evaluations so far
+    int timed_out;       // the deadline passed while some RHS was unconverged
+    int zero;            // first sweep starts from x = 0
+    int max_iter, max_outer;
+    int outer_bodies;    // executions of the sweep body (for launch accounting)
+    int inner_bodies;    // executions of the iteration body
+    double tol, inner_tol;
+    long long timeout_ns;
+    unsigned long long deadline;  // %globaltimer value, 0 = none
+};
 
 struct GArgs {
-    double2 *Vb, *w, *r, *x;
-    const double2 *v;
-    float2 *x32;
-    const float2 *y32;
+    double2 *Vb;       // [(m+1)][cap][N] unnormalised basis u_k
+    double2 *w;        // [cap][N] FP64 product output
+    double2 *x;        // [nrhs][N] iterate (caller's buffer)
+    const double2 *v;  // [nrhs][N] right-hand sides
+    float2 *x32;       // [cap][N] FP32 copy of the next product input (MIXED)
+    const float2 *y32; // [cap][N] FP32 product output (MIXED)
     double2 *H, *cs, *sn, *g, *y, *h1, *h2, *part;
+    double *beta;      // [cap][m+1] ||u_k||
+    double2 *xin64;    // [cap][N] FP64 copy of the next product input (FP64)
     double *nrm;
     int *st;
     unsigned *cnt;
+    SolveCtl *ctl;
     int64_t N;
-    int cap, m, nchunk, pstride;
+    int cap, m, nchunk, pstride, nrhs;
     int mixed;
-    double tol, inner_tol;
-    int max_iter;
 };
 
-constexpr int NT_ = 256;       // threads per CTA
-constexpr int NW_ = NT_ / 32;  // warps per CTA
-constexpr int KG = 8;          // basis vectors per register group
-
-__device__ __forceinline__ double2 wsum(double2 v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-    }
+__device__ __forceinline__ double2 shfl_xor2(double2 v, int o) {
+    v.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y = __shfl_xor_sync(0xffffffffu, v.y, o);
     return v;
 }
 
-// Sum v[0..K) over the CTA; the totals land in red[0..K).
-template <int K> __device__ __forceinline__ void block_sum(double2 (&v)[K], double2 *red /*[NW_][K]*/) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Warp reduce-scatter of 8 values: afterwards v[0] holds the warp total of
+// value ((lane>>4)&1)*4 + ((lane>>3)&1)*2 + ((lane>>2)&1).  9 exchanges instead
+// of 40 for 8 separate butterflies.
+__device__ __forceinline__ void warp_rs8(double2 (&v)[8]) {
+    const int lane = threadIdx.x & 31;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = wsum(v[k]);
-    if (lane == 0)
+    for (int i = 0; i < 4; ++i) {
+        const double2 recv = shfl_xor2(b4 ? v[i] : v[i + 4], 16);
+        v[i] = (b4 ? v[i + 4] : v[i]) + recv;
+    }
 #pragma unroll
-        for (int k = 0; k < K; ++k) red[warp * K + k] = v[k];
+    for (int i = 0; i < 2; ++i) {
+        const double2 recv = shfl_xor2(b3 ? v[i] : v[i + 2], 8);
+        v[i] = (b3 ? v[i + 2] : v[i]) + recv;
+    }
+    {
+        const double2 recv = shfl_xor2(b2 ? v[0] : v[1], 4);
+        v[0] = (b2 ? v[1] : v[0]) + recv;
+    }
+    v[0] = v[0] + shfl_xor2(v[0], 2);
+    v[0] = v[0] + shfl_xor2(v[0], 1);
+}
+
+// CTA totals of 8 values into red[0..8) (red holds >= 8 * warps entries).
+__device__ __forceinline__ void block_sum8(double2 (&v)[8], double2 *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    warp_rs8(v);
+    if ((lane & 3) == 0) red[warp * 8 + (((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1))] = v[0];
     __syncthreads();
-    if (threadIdx.x < K) {
+    if (threadIdx.x < 8) {
         double2 s = red[threadIdx.x];
-        for (int w = 1; w < NW_; ++w) s = s + red[w * K + threadIdx.x];
-        red[threadIdx.x] = s;  // each thread reads only column threadIdx.x, rows >= 1 already read
+        for (int w = 1; w < nw; ++w) s = s + red[w * 8 + threadIdx.x];
+        red[threadIdx.x] = s;  // thread t only touches column t
     }
     __syncthreads();
+}
+
+// CTA total of one real value (valid in thread 0).
+__device__ __forceinline__ double block_sum1(double v, double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < nw; ++w) s += red[w];
+    __syncthreads();
+    return s;
 }
 
 // Last-CTA-done ticket for the CTAs of one RHS (no waiting).
@@ -81,7 +135,7 @@ __device__ __forceinline__ bool last_cta(unsigned *cnt, unsigned total) {
     if (threadIdx.x == 0) {
         const unsigned t = atomicAdd(cnt, 1u);
         s_last = (t == total - 1);
-        if (s_last) *cnt = 0;  // reset for the next use; nobody else touches it in this launch
+        if (s_last) *cnt = 0;  // reset for the next use; no other CTA touches it in this launch
     }
     __syncthreads();
     if (s_last) __threadfence();
@@ -89,16 +143,13 @@ __device__ __forceinline__ bool last_cta(unsigned *cnt, unsigned total) {
 }
 
 // In the last CTA: out[k] = sum_c part[c][k] for k < K (one warp per k).
-__device__ __forceinline__ void reduce_partials(const double2 *part, int nchunk, int pstride, int K,
-                                                double2 *out) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = warp; k < K; k += NW_) {
+__device__ __forceinline__ void reduce_partials(const double2 *part, int nchunk, int pstride, int K, double2 *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = warp; k < K; k += nw) {
         double2 s = make_double2(0, 0);
-        for (int c = lane; c < nchunk; c += 32) {
-            const double2 pv = __ldcg(part + (int64_t)c * pstride + k);
-            s = s + pv;
-        }
-        s = wsum(s);
+        for (int c = lane; c < nchunk; c += 32) s = s + __ldcg(part + (int64_t)c * pstride + k);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = s + shfl_xor2(s, o);
         if (lane == 0) out[k] = s;
     }
     __syncthreads();
@@ -109,214 +160,95 @@ __device__ __forceinline__ double2 *basis(const GArgs &a, int k, int rr) {
 }
 
 // ---------------------------------------------------------------- norms
-// ||v|| per RHS -> nrm[VNORM].
-template <int ELEM> __global__ void __launch_bounds__(NT_) k_vnorm(GArgs a) {
-    __shared__ double2 red[NW_];
+template <int ELEM> __global__ void __launch_bounds__(256) k_vnorm(GArgs a) {
+    __shared__ double red[8];
+    __shared__ double2 tot[1];
     const int rr = blockIdx.y;
-    const int64_t base = (int64_t)blockIdx.x * NT_ * ELEM;
-    double2 acc[1] = {make_double2(0, 0)};
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x * ELEM;
+    double acc = 0;
 #pragma unroll
     for (int e = 0; e < ELEM; ++e) {
-        const int64_t idx = base + e * NT_ + threadIdx.x;
-        if (idx < a.N) {
-            const double2 t = a.v[(int64_t)rr * a.N + idx];
-            acc[0].x += t.x * t.x + t.y * t.y;
-        }
+        const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
+        if (idx < a.N) acc += cabs2(a.v[(int64_t)rr * a.N + idx]);
     }
-    block_sum<1>(acc, red);
+    acc = block_sum1(acc, red);
     double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * a.pstride] = red[0];
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * a.pstride] = make_double2(acc, 0);
     if (last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk)) {
-        __shared__ double2 tot[1];
         reduce_partials(part, a.nchunk, a.pstride, 1, tot);
         if (threadIdx.x == 0) a.nrm[rr * NM_STRIDE + NM_VNORM] = sqrt(tot[0].x);
     }
 }
 
-// r = v - r (r holds Z' x) or r = v (zero guess); ||r||, stop test, start of a cycle.
-template <int ELEM> __global__ void __launch_bounds__(NT_) k_residual(GArgs a, int zero) {
-    __shared__ double2 red[NW_];
+// u_0 = v - Z'x (w holds Z'x) or v (zero guess), its FP32 copy, ||u_0||, stop
+// test and the start of a cycle.
+template <int ELEM> __global__ void __launch_bounds__(256) k_residual(GArgs a, int first) {
+    __shared__ double red[8];
+    __shared__ double2 tot[1];
     const int rr = blockIdx.y;
     int *st = a.st + rr * ST_STRIDE;
     if (st[ST_STATUS] != RS_RUNNING) return;
-    const int64_t base = (int64_t)blockIdx.x * NT_ * ELEM;
-    double2 acc[1] = {make_double2(0, 0)};
+    const int zero = first && a.ctl->zero;
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x * ELEM;
+    double2 *u0 = basis(a, 0, rr);
+    double acc = 0;
 #pragma unroll
     for (int e = 0; e < ELEM; ++e) {
-        const int64_t idx = base + e * NT_ + threadIdx.x;
+        const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
         if (idx < a.N) {
             const int64_t o = (int64_t)rr * a.N + idx;
-            const double2 t = zero ? a.v[o] : a.v[o] - a.r[o];
-            a.r[o] = t;
-            acc[0].x += t.x * t.x + t.y * t.y;
+            const double2 t = zero ? a.v[o] : a.v[o] - a.w[o];
+            u0[idx] = t;
+            if (a.mixed)
+                a.x32[o] = make_float2((float)t.x, (float)t.y);
+            else
+                a.xin64[o] = t;
+            acc += cabs2(t);
         }
     }
-    block_sum<1>(acc, red);
+    acc = block_sum1(acc, red);
     double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * a.pstride] = red[0];
-    if (last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk)) {
-        __shared__ double2 tot[1];
-        reduce_partials(part, a.nchunk, a.pstride, 1, tot);
-        if (threadIdx.x == 0) {
-            double *nm = a.nrm + rr * NM_STRIDE;
-            const double vn = nm[NM_VNORM], rn = sqrt(tot[0].x);
-            nm[NM_RNORM] = rn;
-            st[ST_OUTER] += 1;
-            st[ST_PENDING] = 0;
-            st[ST_JLEN] = 0;
-            st[ST_ACTIVE] = 0;
-            if (!isfinite(vn) || !isfinite(rn)) {
-                st[ST_STATUS] = RS_NONFINITE;
-            } else if (rn <= a.tol * vn || rn == 0.0) {
-                st[ST_STATUS] = RS_CONVERGED;
-            } else if (st[ST_ITERS] >= a.max_iter) {
-                st[ST_STATUS] = RS_MAXITER;
-            } else {
-                st[ST_ACTIVE] = 1;
-                nm[NM_BETA0] = rn;
-                const double floor_abs = 0.5 * a.tol * vn;
-                nm[NM_TARGET] = a.mixed ? fmax(a.inner_tol * rn, floor_abs) : floor_abs;
-                double2 *g = a.g + (int64_t)rr * (a.m + 1);
-                g[0] = make_double2(rn, 0);
-                for (int i = 1; i <= a.m; ++i) g[i] = make_double2(0, 0);
-            }
-        }
-    }
-}
-
-// V[0] = r / beta0 (and its FP32 copy for the inner product).
-template <int ELEM> __global__ void __launch_bounds__(NT_) k_start(GArgs a) {
-    const int rr = blockIdx.y;
-    if (!a.st[rr * ST_STRIDE + ST_ACTIVE]) return;
-    const double inv = 1.0 / a.nrm[rr * NM_STRIDE + NM_BETA0];
-    double2 *v0 = basis(a, 0, rr);
-    const int64_t base = (int64_t)blockIdx.x * NT_ * ELEM;
-#pragma unroll
-    for (int e = 0; e < ELEM; ++e) {
-        const int64_t idx = base + e * NT_ + threadIdx.x;
-        if (idx < a.N) {
-            const double2 t = cscale(a.r[(int64_t)rr * a.N + idx], inv);
-            v0[idx] = t;
-            if (a.mixed) a.x32[(int64_t)rr * a.N + idx] = make_float2((float)t.x, (float)t.y);
-        }
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * a.pstride] = make_double2(acc, 0);
+    if (!last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk)) return;
+    reduce_partials(part, a.nchunk, a.pstride, 1, tot);
+    if (threadIdx.x != 0) return;
+    double *nm = a.nrm + rr * NM_STRIDE;
+    const double vn = nm[NM_VNORM], rn = sqrt(tot[0].x);
+    nm[NM_RNORM] = rn;
+    st[ST_OUTER] += 1;
+    st[ST_PENDING] = 0;
+    st[ST_JLEN] = 0;
+    st[ST_ACTIVE] = 0;
+    st[ST_REORTH] = 0;
+    if (!isfinite(vn) || !isfinite(rn)) {
+        st[ST_STATUS] = RS_NONFINITE;
+    } else if (rn <= a.ctl->tol * vn || rn == 0.0) {
+        st[ST_STATUS] = RS_CONVERGED;
+    } else if (st[ST_ITERS] >= a.ctl->max_iter) {
+        st[ST_STATUS] = RS_MAXITER;
+    } else {
+        st[ST_ACTIVE] = 1;
+        a.beta[(int64_t)rr * (a.m + 1)] = rn;
+        const double floor_abs = 0.5 * a.ctl->tol * vn;
+        nm[NM_TARGET] = a.mixed ? fmax(a.ctl->inner_tol * rn, floor_abs) : floor_abs;
+        double2 *g = a.g + (int64_t)rr * (a.m + 1);
+        g[0] = make_double2(rn, 0);
+        for (int i = 1; i <= a.m; ++i) g[i] = make_double2(0, 0);
     }
 }
 
 // ---------------------------------------------------------------- Arnoldi
-// Partial sums of conj(V_k) . w for k <= j over this CTA's elements -> part.
-template <int ELEM>
-__device__ __forceinline__ void dots_partial(const GArgs &a, int rr, int j, const double2 (&wv)[ELEM],
-                                             int64_t base, double2 *part, double2 *red) {
-    for (int k0 = 0; k0 <= j; k0 += KG) {
-        double2 acc[KG];
-#pragma unroll
-        for (int kk = 0; kk < KG; ++kk) acc[kk] = make_double2(0, 0);
-#pragma unroll
-        for (int kk = 0; kk < KG; ++kk) {
-            if (k0 + kk <= j) {
-                const double2 *vk = basis(a, k0 + kk, rr);
-#pragma unroll
-                for (int e = 0; e < ELEM; ++e) {
-                    const int64_t idx = base + e * NT_ + threadIdx.x;
-                    if (idx < a.N) acc[kk] = cfmac(vk[idx], wv[e], acc[kk]);
-                }
-            }
-        }
-        block_sum<KG>(acc, red);
-        if (threadIdx.x < KG && k0 + threadIdx.x <= j)
-            part[(int64_t)blockIdx.x * a.pstride + k0 + threadIdx.x] = red[threadIdx.x];
-        __syncthreads();
-    }
-}
-
-// First Gram-Schmidt pass: w <- product output (widened), h1 = V^H w.
-template <int ELEM> __global__ void __launch_bounds__(NT_) k_gs1(GArgs a, int j) {
-    __shared__ double2 red[NW_ * KG];
-    const int rr = blockIdx.y;
-    if (!a.st[rr * ST_STRIDE + ST_ACTIVE]) return;
-    const int64_t base = (int64_t)blockIdx.x * NT_ * ELEM;
-    double2 wv[ELEM];
-#pragma unroll
-    for (int e = 0; e < ELEM; ++e) {
-        const int64_t idx = base + e * NT_ + threadIdx.x;
-        wv[e] = make_double2(0, 0);
-        if (idx < a.N) {
-            const int64_t o = (int64_t)rr * a.N + idx;
-            if (a.mixed) {
-                const float2 t = a.y32[o];
-                wv[e] = make_double2(t.x, t.y);
-                a.w[o] = wv[e];
-            } else {
-                wv[e] = a.w[o];
-            }
-        }
-    }
-    double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
-    dots_partial<ELEM>(a, rr, j, wv, base, part, red);
-    if (last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk))
-        reduce_partials(part, a.nchunk, a.pstride, j + 1, a.h1 + (int64_t)rr * (a.m + 1));
-}
-
-// w <- w - V h (h from the previous pass); optionally h2 = V^H w (second pass)
-// or the partial ||w||^2.
-template <int ELEM, bool SECOND>
-__global__ void __launch_bounds__(NT_) k_gs_update(GArgs a, int j) {
-    __shared__ double2 red[NW_ * KG];
-    __shared__ double2 hs[129];
-    const int rr = blockIdx.y;
-    if (!a.st[rr * ST_STRIDE + ST_ACTIVE]) return;
-    const double2 *h = (SECOND ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
-    for (int k = threadIdx.x; k <= j; k += NT_) hs[k] = __ldcg(h + k);
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * NT_ * ELEM;
-    double2 wv[ELEM];
-#pragma unroll
-    for (int e = 0; e < ELEM; ++e) {
-        const int64_t idx = base + e * NT_ + threadIdx.x;
-        wv[e] = make_double2(0, 0);
-        if (idx < a.N) wv[e] = a.w[(int64_t)rr * a.N + idx];
-    }
-    for (int k = 0; k <= j; ++k) {
-        const double2 hk = hs[k];
-        const double2 *vk = basis(a, k, rr);
-#pragma unroll
-        for (int e = 0; e < ELEM; ++e) {
-            const int64_t idx = base + e * NT_ + threadIdx.x;
-            if (idx < a.N) wv[e] = wv[e] - cmul(hk, vk[idx]);
-        }
-    }
-#pragma unroll
-    for (int e = 0; e < ELEM; ++e) {
-        const int64_t idx = base + e * NT_ + threadIdx.x;
-        if (idx < a.N) a.w[(int64_t)rr * a.N + idx] = wv[e];
-    }
-    double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
-    if (SECOND) {
-        dots_partial<ELEM>(a, rr, j, wv, base, part, red);
-        if (last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk))
-            reduce_partials(part, a.nchunk, a.pstride, j + 1, a.h2 + (int64_t)rr * (a.m + 1));
-        return;
-    }
-    double2 acc[1] = {make_double2(0, 0)};
-#pragma unroll
-    for (int e = 0; e < ELEM; ++e) acc[0].x += wv[e].x * wv[e].x + wv[e].y * wv[e].y;
-    block_sum<1>(acc, red);
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * a.pstride] = red[0];
-    if (!last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk)) return;
-    __shared__ double2 tot[1];
-    reduce_partials(part, a.nchunk, a.pstride, 1, tot);
-    if (threadIdx.x != 0) return;
-    // Hessenberg column j, Givens rotations, residual estimate (one thread).
+// Hessenberg column j from the Gram-Schmidt coefficients h and beta_{j+1},
+// Givens rotations, residual estimate, end-of-cycle least squares.  One thread.
+__device__ void finalize_column(const GArgs &a, int rr, int j, const double2 *h, double beta) {
     const int m = a.m;
     int *st = a.st + rr * ST_STRIDE;
     double *nm = a.nrm + rr * NM_STRIDE;
     double2 *H = a.H + (int64_t)rr * (m + 1) * m;
     double2 *cs = a.cs + (int64_t)rr * m, *sn = a.sn + (int64_t)rr * m;
     double2 *g = a.g + (int64_t)rr * (m + 1);
-    const double2 *h1 = a.h1 + (int64_t)rr * (m + 1), *h2 = a.h2 + (int64_t)rr * (m + 1);
-    const double beta = sqrt(tot[0].x);
-    nm[NM_BETA] = beta;
-    for (int i = 0; i <= j; ++i) H[i * m + j] = __ldcg(h1 + i) + __ldcg(h2 + i);
+    a.beta[(int64_t)rr * (m + 1) + j + 1] = beta;
+    for (int i = 0; i <= j; ++i) H[i * m + j] = h[i];
     for (int i = 0; i < j; ++i) {
         const double2 p = H[i * m + j], q = H[(i + 1) * m + j];
         H[i * m + j] = cmulc(cs[i], p) + cmulc(sn[i], q);
@@ -338,51 +270,172 @@ __global__ void __launch_bounds__(NT_) k_gs_update(GArgs a, int j) {
     st[ST_JLEN] = j + 1;
     st[ST_ITERS] += 1;
     const double res = sqrt(cabs2(g[j + 1]));
-    const bool end = !(res > nm[NM_TARGET]) || !(beta > 0) || (j + 1 == m) || (st[ST_ITERS] >= a.max_iter);
+    const bool end = !(res > nm[NM_TARGET]) || !(beta > 0) || (j + 1 == m) || (st[ST_ITERS] >= a.ctl->max_iter);
     if (end) {
-        // least squares: R y = g (R upper triangular, (j+1) x (j+1))
-        double2 *y = a.y + (int64_t)rr * m;
+        double2 *y = a.y + (int64_t)rr * m;  // R y = g, (j+1) x (j+1) upper triangular
         for (int i = j; i >= 0; --i) {
             double2 s = g[i];
             for (int l = i + 1; l <= j; ++l) s = s - cmul(H[i * m + l], y[l]);
-            y[i] = (H[i * m + i].x != 0.0 || H[i * m + i].y != 0.0) ? cdiv(s, H[i * m + i]) : make_double2(0, 0);
+            const double2 rii = H[i * m + i];
+            y[i] = (rii.x != 0.0 || rii.y != 0.0) ? cdiv(s, rii) : make_double2(0, 0);
         }
         st[ST_ACTIVE] = 0;
         st[ST_PENDING] = 1;
     }
 }
 
-// V[j+1] = w / beta (and its FP32 copy).
-template <int ELEM> __global__ void __launch_bounds__(NT_) k_normalize(GArgs a, int j) {
+// Gram-Schmidt dots.  PASS 1: w = (product of u_j) / beta_j is formed (from the
+// FP32 or FP64 product) and stored as u_{j+1}; h1_k = <v_k, w>, ||w||.
+// PASS 2 (only RHS flagged for reorthogonalisation): h2_k = <v_k, u_{j+1}>.
+template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(GArgs a) {
+    __shared__ double2 red[64];
+    __shared__ double2 tot[130];
     const int rr = blockIdx.y;
-    if (!a.st[rr * ST_STRIDE + ST_ACTIVE]) return;
-    const double inv = 1.0 / a.nrm[rr * NM_STRIDE + NM_BETA];
-    double2 *vn = basis(a, j + 1, rr);
-    const int64_t base = (int64_t)blockIdx.x * NT_ * ELEM;
+    const int *st = a.st + rr * ST_STRIDE;
+    if (!st[ST_ACTIVE]) return;
+    if (PASS == 2 && !st[ST_REORTH]) return;
+    const int j = a.ctl->j;
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x * ELEM;
+    const double *beta = a.beta + (int64_t)rr * (a.m + 1);
+    double2 *un = basis(a, j + 1, rr);
+    double2 wv[ELEM];
+    const double sc = 1.0 / beta[j];
 #pragma unroll
     for (int e = 0; e < ELEM; ++e) {
-        const int64_t idx = base + e * NT_ + threadIdx.x;
+        const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
+        wv[e] = make_double2(0, 0);
         if (idx < a.N) {
-            const double2 t = cscale(a.w[(int64_t)rr * a.N + idx], inv);
-            vn[idx] = t;
-            if (a.mixed) a.x32[(int64_t)rr * a.N + idx] = make_float2((float)t.x, (float)t.y);
+            if (PASS == 1) {
+                const int64_t o = (int64_t)rr * a.N + idx;
+                double2 t;
+                if (a.mixed) {
+                    const float2 f = a.y32[o];
+                    t = make_double2(f.x, f.y);
+                } else {
+                    t = a.w[o];
+                }
+                wv[e] = cscale(t, sc);
+                un[idx] = wv[e];
+            } else {
+                wv[e] = un[idx];
+            }
         }
+    }
+    const int K = j + 1 + (PASS == 1 ? 1 : 0);  // dots with u_0..u_j (+ ||w||^2 last in pass 1)
+    double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
+    for (int k0 = 0; k0 < K; k0 += 8) {
+        double2 acc[8];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            acc[kk] = make_double2(0, 0);
+            const int k = k0 + kk;
+            if (k <= j) {
+                const double2 *uk = basis(a, k, rr);
+#pragma unroll
+                for (int e = 0; e < ELEM; ++e) {
+                    const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
+                    if (idx < a.N) acc[kk] = cfmac(uk[idx], wv[e], acc[kk]);
+                }
+            } else if (PASS == 1 && k == j + 1) {
+#pragma unroll
+                for (int e = 0; e < ELEM; ++e) acc[kk].x += cabs2(wv[e]);
+            }
+        }
+        block_sum8(acc, red);
+        if (threadIdx.x < 8 && k0 + (int)threadIdx.x < K)
+            part[(int64_t)blockIdx.x * a.pstride + k0 + threadIdx.x] = red[threadIdx.x];
+        __syncthreads();
+    }
+    if (!last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk)) return;
+    reduce_partials(part, a.nchunk, a.pstride, K, tot);
+    double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) h[k] = cscale(tot[k], 1.0 / beta[k]);
+    if (PASS == 1 && threadIdx.x == 0) a.nrm[rr * NM_STRIDE + NM_W0] = sqrt(tot[j + 1].x);
+}
+
+// u_{j+1} <- u_{j+1} - sum_k (h_k / beta_k) u_k, its FP32 copy, ||u_{j+1}||.
+// PASS 1 decides whether a second pass is needed; otherwise (and after PASS 2)
+// the Hessenberg column is finalised.
+template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(GArgs a) {
+    __shared__ double red[8];
+    __shared__ double2 cf[129];
+    __shared__ double2 tot[1];
+    const int rr = blockIdx.y;
+    int *st = a.st + rr * ST_STRIDE;
+    if (!st[ST_ACTIVE]) return;
+    if (PASS == 2 && !st[ST_REORTH]) return;
+    const int j = a.ctl->j;
+    const double *beta = a.beta + (int64_t)rr * (a.m + 1);
+    const double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) cf[k] = cscale(__ldcg(h + k), 1.0 / beta[k]);
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x * ELEM;
+    double2 *un = basis(a, j + 1, rr);
+    double2 wv[ELEM];
+#pragma unroll
+    for (int e = 0; e < ELEM; ++e) {
+        const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
+        wv[e] = idx < a.N ? un[idx] : make_double2(0, 0);
+    }
+    for (int k = 0; k <= j; ++k) {
+        const double2 c = cf[k];
+        const double2 *uk = basis(a, k, rr);
+#pragma unroll
+        for (int e = 0; e < ELEM; ++e) {
+            const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
+            if (idx < a.N) wv[e] = wv[e] - cmul(c, uk[idx]);
+        }
+    }
+    double acc = 0;
+#pragma unroll
+    for (int e = 0; e < ELEM; ++e) {
+        const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
+        if (idx < a.N) {
+            un[idx] = wv[e];
+            if (a.mixed)
+                a.x32[(int64_t)rr * a.N + idx] = make_float2((float)wv[e].x, (float)wv[e].y);
+            else
+                a.xin64[(int64_t)rr * a.N + idx] = wv[e];
+            acc += cabs2(wv[e]);
+        }
+    }
+    acc = block_sum1(acc, red);
+    double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * a.pstride] = make_double2(acc, 0);
+    if (!last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk)) return;
+    reduce_partials(part, a.nchunk, a.pstride, 1, tot);
+    if (threadIdx.x != 0) return;
+    const double wn = sqrt(tot[0].x);
+    const double2 *h1 = a.h1 + (int64_t)rr * (a.m + 1);
+    if (PASS == 1) {
+        if (wn < kReorthEta * a.nrm[rr * NM_STRIDE + NM_W0]) {
+            st[ST_REORTH] = 1;
+            return;
+        }
+        finalize_column(a, rr, j, h1, wn);
+    } else {
+        double2 *h2 = a.h2 + (int64_t)rr * (a.m + 1);
+        for (int k = 0; k <= j; ++k) h2[k] = h1[k] + h2[k];  // total coefficients
+        st[ST_REORTH] = 0;
+        finalize_column(a, rr, j, h2, wn);
     }
 }
 
-// x <- x + V y for RHS whose cycle produced an update.
-template <int ELEM> __global__ void __launch_bounds__(NT_) k_update_x(GArgs a) {
+// x <- x + sum_k (y_k / beta_k) u_k for RHS whose cycle produced an update.
+template <int ELEM> __global__ void __launch_bounds__(256) k_update_x(GArgs a) {
     __shared__ double2 ys[128];
     const int rr = blockIdx.y;
     const int *st = a.st + rr * ST_STRIDE;
     if (!st[ST_PENDING]) return;
     const int jl = st[ST_JLEN];
-    for (int k = threadIdx.x; k < jl; k += NT_) ys[k] = __ldcg(a.y + (int64_t)rr * a.m + k);
+    const double *beta = a.beta + (int64_t)rr * (a.m + 1);
+    for (int k = threadIdx.x; k < jl; k += blockDim.x)
+        ys[k] = cscale(__ldcg(a.y + (int64_t)rr * a.m + k), 1.0 / beta[k]);
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * NT_ * ELEM;
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x * ELEM;
 #pragma unroll
     for (int e = 0; e < ELEM; ++e) {
-        const int64_t idx = base + e * NT_ + threadIdx.x;
+        const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
         if (idx < a.N) {
             double2 s = a.x[(int64_t)rr * a.N + idx];
             for (int k = 0; k < jl; ++k) s = cfma(ys[k], basis(a, k, rr)[idx], s);
@@ -391,35 +444,122 @@ template <int ELEM> __global__ void __launch_bounds__(NT_) k_update_x(GArgs a) {
     }
 }
 
+// ---------------------------------------------------------------- loop control
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Start of a solve: counters, deadline, x = 0 for a zero guess, and whether the
+// first true residual needs a product (it does not when x = 0).
+__global__ void k_solve_begin(GArgs a, cudaGraphConditionalHandle h_first_product) {
+    SolveCtl *c = a.ctl;
+    const int64_t total = (int64_t)a.nrhs * a.N;
+    if (c->zero)
+        for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x)
+            a.x[k] = make_double2(0, 0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->j = 0;
+        c->sweeps = 0;
+        c->timed_out = 0;
+        c->outer_bodies = 0;
+        c->inner_bodies = 0;
+        c->deadline = c->timeout_ns > 0 ? globaltimer_ns() + (unsigned long long)c->timeout_ns : 0ull;
+        cudaGraphSetConditional(h_first_product, c->zero ? 0u : 1u);
+    }
+}
+
+__device__ __forceinline__ bool any_active(const GArgs &a) {
+    int any = 0;
+    for (int rr = threadIdx.x; rr < a.nrhs; rr += blockDim.x) any |= a.st[rr * ST_STRIDE + ST_ACTIVE];
+    return __syncthreads_or(any) != 0;
+}
+
+__device__ __forceinline__ bool past_deadline(const SolveCtl *c) {
+    return c->deadline != 0ull && globaltimer_ns() > c->deadline;
+}
+
+// After a true residual: another sweep while some RHS is active, within the
+// sweep cap and the deadline.
+__global__ void k_sweep_ctl(GArgs a, cudaGraphConditionalHandle h_sweep) {
+    const bool any = any_active(a);
+    if (threadIdx.x != 0) return;
+    SolveCtl *c = a.ctl;
+    c->sweeps += 1;
+    const bool late = past_deadline(c);
+    if (any && late) c->timed_out = 1;
+    cudaGraphSetConditional(h_sweep, (any && c->sweeps < c->max_outer && !late) ? 1u : 0u);
+}
+
+__global__ void k_cycle_begin(GArgs a, cudaGraphConditionalHandle h_iter) {
+    if (threadIdx.x != 0) return;
+    a.ctl->j = 0;
+    a.ctl->outer_bodies += 1;
+    cudaGraphSetConditional(h_iter, 1u);
+}
+
+// After an Arnoldi step: next iteration while some RHS is still in its cycle.
+__global__ void k_iter_ctl(GArgs a, cudaGraphConditionalHandle h_iter) {
+    const bool any = any_active(a);
+    if (threadIdx.x != 0) return;
+    SolveCtl *c = a.ctl;
+    c->j += 1;
+    c->inner_bodies += 1;
+    const bool late = past_deadline(c);
+    if (any && late) c->timed_out = 1;
+    cudaGraphSetConditional(h_iter, (any && c->j < a.m && !late) ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------- workspace
+void free_solve_graphs(ztoep_plan_t p) {
+    for (auto &g : p->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+        g = SolveGraph{};
+    }
+    p->graph_next = 0;
+}
+
 void free_solve_ws(ztoep_plan_t p) {
+    free_solve_graphs(p);
     SolveWs &w = p->sws;
-    cudaFree(w.Vb); cudaFree(w.w); cudaFree(w.r); cudaFree(w.H); cudaFree(w.cs); cudaFree(w.sn);
-    cudaFree(w.g); cudaFree(w.y); cudaFree(w.h1); cudaFree(w.h2); cudaFree(w.part); cudaFree(w.nrm);
-    cudaFree(w.st); cudaFree(w.cnt);
+    cudaFree(w.Vb); cudaFree(w.w); cudaFree(w.xin64); cudaFree(w.vbuf); cudaFree(w.xbuf); cudaFree(w.H);
+    cudaFree(w.cs); cudaFree(w.sn); cudaFree(w.g); cudaFree(w.y); cudaFree(w.h1); cudaFree(w.h2);
+    cudaFree(w.part); cudaFree(w.nrm); cudaFree(w.st); cudaFree(w.cnt); cudaFree(w.ctl);
     if (w.hst) cudaFreeHost(w.hst);
     if (w.hnrm) cudaFreeHost(w.hnrm);
     w = SolveWs{};
 }
 
-static int elem_for(int64_t N, int nsm) {
-    // 1 element per thread for small systems, 4 for large ones.  Depends on N
-    // only, so a RHS is summed in the same order alone and in any batch.
-    const int64_t ctas1 = (N + NT_ - 1) / NT_;
-    return ctas1 >= 8LL * nsm ? 4 : 1;
+// Launch geometry: depends on N only, so a RHS is summed in the same order
+// alone and in any batch.  Small systems: 128 threads x 2 elements (enough
+// CTAs to cover every SM); large ones: 256 threads x 4 elements.
+struct Geom {
+    int threads, elem;
+};
+static Geom geom_for(int64_t N, int nsm) {
+    const int64_t ctas_small = (N + 255) / 256;
+    if (ctas_small >= 8LL * nsm) return {256, 4};
+    return {128, 2};
 }
+
+constexpr int kHostCtlInts = 32;  // host mirror of SolveCtl after st
 
 static ztoep_status_t ensure_solve_ws(ztoep_plan_t p, int nrhs, int m) {
     SolveWs &w = p->sws;
     if (w.cap >= nrhs && w.m >= m) return ZTOEP_OK;
     free_solve_ws(p);
     const int64_t N = p->N;
-    const int nchunk = (int)((N + NT_ - 1) / NT_);  // upper bound (ELEM = 1)
+    const int nchunk = (int)((N + 255) / 256);  // upper bound over the geometries
     const int pstride = m + 2;
+    const size_t vec = sizeof(double2) * (size_t)nrhs * N;
     size_t acc = 0;
     ZT_TRY(dalloc((void **)&w.Vb, sizeof(double2) * (size_t)(m + 1) * nrhs * N, &acc));
-    ZT_TRY(dalloc((void **)&w.w, sizeof(double2) * (size_t)nrhs * N, &acc));
-    ZT_TRY(dalloc((void **)&w.r, sizeof(double2) * (size_t)nrhs * N, &acc));
+    ZT_TRY(dalloc((void **)&w.w, vec, &acc));
+    ZT_TRY(dalloc((void **)&w.xin64, vec, &acc));
+    ZT_TRY(dalloc((void **)&w.vbuf, vec, &acc));
+    ZT_TRY(dalloc((void **)&w.xbuf, vec, &acc));
     ZT_TRY(dalloc((void **)&w.H, sizeof(double2) * (size_t)nrhs * (m + 1) * m, &acc));
     ZT_TRY(dalloc((void **)&w.cs, sizeof(double2) * (size_t)nrhs * m, &acc));
     ZT_TRY(dalloc((void **)&w.sn, sizeof(double2) * (size_t)nrhs * m, &acc));
@@ -428,11 +568,12 @@ static ztoep_status_t ensure_solve_ws(ztoep_plan_t p, int nrhs, int m) {
     ZT_TRY(dalloc((void **)&w.h1, sizeof(double2) * (size_t)nrhs * (m + 1), &acc));
     ZT_TRY(dalloc((void **)&w.h2, sizeof(double2) * (size_t)nrhs * (m + 1), &acc));
     ZT_TRY(dalloc((void **)&w.part, sizeof(double2) * (size_t)nrhs * nchunk * pstride, &acc));
-    ZT_TRY(dalloc((void **)&w.nrm, sizeof(double) * (size_t)nrhs * NM_STRIDE, &acc));
+    ZT_TRY(dalloc((void **)&w.nrm, sizeof(double) * (size_t)nrhs * (NM_STRIDE + m + 1), &acc));
     ZT_TRY(dalloc((void **)&w.st, sizeof(int) * (size_t)nrhs * ST_STRIDE, &acc));
     ZT_TRY(dalloc((void **)&w.cnt, sizeof(unsigned) * (size_t)nrhs * CNT_STRIDE, &acc));
+    ZT_TRY(dalloc((void **)&w.ctl, sizeof(SolveCtl), &acc));
     ZT_CUDA(cudaMemset(w.cnt, 0, sizeof(unsigned) * (size_t)nrhs * CNT_STRIDE));
-    ZT_CUDA(cudaMallocHost((void **)&w.hst, sizeof(int) * (size_t)nrhs * ST_STRIDE));
+    ZT_CUDA(cudaMallocHost((void **)&w.hst, sizeof(int) * (size_t)nrhs * ST_STRIDE + sizeof(SolveCtl) + 64));
     ZT_CUDA(cudaMallocHost((void **)&w.hnrm, sizeof(double) * (size_t)nrhs * NM_STRIDE));
     w.cap = nrhs;
     w.m = m;
@@ -440,100 +581,238 @@ static ztoep_status_t ensure_solve_ws(ztoep_plan_t p, int nrhs, int m) {
     return ZTOEP_OK;
 }
 
+static GArgs make_args(ztoep_plan_t p, int nrhs, int m, bool mixed, int nchunk) {
+    SolveWs &w = p->sws;
+    GArgs a{};
+    a.Vb = w.Vb; a.w = w.w; a.x = w.xbuf; a.v = w.vbuf; a.xin64 = w.xin64;
+    a.x32 = (float2 *)p->ws32.xin; a.y32 = (const float2 *)p->ws32.yout;
+    a.H = w.H; a.cs = w.cs; a.sn = w.sn; a.g = w.g; a.y = w.y; a.h1 = w.h1; a.h2 = w.h2; a.part = w.part;
+    a.nrm = w.nrm; a.beta = w.nrm + (size_t)w.cap * NM_STRIDE; a.st = w.st; a.cnt = w.cnt;
+    a.ctl = (SolveCtl *)w.ctl;
+    a.N = p->N; a.cap = w.cap; a.m = m; a.nchunk = nchunk; a.pstride = w.m + 2; a.nrhs = nrhs;
+    a.mixed = mixed ? 1 : 0;
+    return a;
+}
+
 template <int ELEM> struct Launch {
-    static ztoep_status_t vnorm(const GArgs &a, dim3 g, cudaStream_t s) { KScope ks(K_MISC, s); k_vnorm<ELEM><<<g, NT_, 0, s>>>(a); return ok(); }
-    static ztoep_status_t residual(const GArgs &a, dim3 g, int zero, cudaStream_t s) { KScope ks(K_MISC, s); k_residual<ELEM><<<g, NT_, 0, s>>>(a, zero); return ok(); }
-    static ztoep_status_t start(const GArgs &a, dim3 g, cudaStream_t s) { KScope ks(K_MISC, s); k_start<ELEM><<<g, NT_, 0, s>>>(a); return ok(); }
-    static ztoep_status_t arnoldi(const GArgs &a, dim3 g, int j, cudaStream_t s) {
-        KScope ks(K_ARNOLDI, s);
-        ks.add(4);
-        k_gs1<ELEM><<<g, NT_, 0, s>>>(a, j);
-        k_gs_update<ELEM, true><<<g, NT_, 0, s>>>(a, j);
-        k_gs_update<ELEM, false><<<g, NT_, 0, s>>>(a, j);
-        k_normalize<ELEM><<<g, NT_, 0, s>>>(a, j);
+    static ztoep_status_t vnorm(const GArgs &a, dim3 g, int t, cudaStream_t s) {
+        KScope ks(K_MISC, s);
+        k_vnorm<ELEM><<<g, t, 0, s>>>(a);
         return ok();
     }
-    static ztoep_status_t update_x(const GArgs &a, dim3 g, cudaStream_t s) { KScope ks(K_MISC, s); k_update_x<ELEM><<<g, NT_, 0, s>>>(a); return ok(); }
-    static ztoep_status_t ok() { ZT_CUDA(cudaGetLastError()); return ZTOEP_OK; }
+    static ztoep_status_t residual(const GArgs &a, dim3 g, int t, int first, cudaStream_t s) {
+        KScope ks(K_MISC, s);
+        k_residual<ELEM><<<g, t, 0, s>>>(a, first);
+        return ok();
+    }
+    static ztoep_status_t arnoldi(const GArgs &a, dim3 g, int t, cudaStream_t s) {
+        KScope ks(K_ARNOLDI, s);
+        ks.add(4);
+        k_dots<ELEM, 1><<<g, t, 0, s>>>(a);
+        k_upd<ELEM, 1><<<g, t, 0, s>>>(a);
+        k_dots<ELEM, 2><<<g, t, 0, s>>>(a);
+        k_upd<ELEM, 2><<<g, t, 0, s>>>(a);
+        return ok();
+    }
+    static ztoep_status_t update_x(const GArgs &a, dim3 g, int t, cudaStream_t s) {
+        KScope ks(K_MISC, s);
+        k_update_x<ELEM><<<g, t, 0, s>>>(a);
+        return ok();
+    }
+    static ztoep_status_t ok() {
+        ZT_CUDA(cudaGetLastError());
+        return ZTOEP_OK;
+    }
 };
 
 struct Ops {
-    int elem;
+    Geom gm;
     dim3 grid;
-    ztoep_status_t vnorm(const GArgs &a, cudaStream_t s) const { return elem == 4 ? Launch<4>::vnorm(a, grid, s) : Launch<1>::vnorm(a, grid, s); }
-    ztoep_status_t residual(const GArgs &a, int zero, cudaStream_t s) const { return elem == 4 ? Launch<4>::residual(a, grid, zero, s) : Launch<1>::residual(a, grid, zero, s); }
-    ztoep_status_t start(const GArgs &a, cudaStream_t s) const { return elem == 4 ? Launch<4>::start(a, grid, s) : Launch<1>::start(a, grid, s); }
-    ztoep_status_t arnoldi(const GArgs &a, int j, cudaStream_t s) const { return elem == 4 ? Launch<4>::arnoldi(a, grid, j, s) : Launch<1>::arnoldi(a, grid, j, s); }
-    ztoep_status_t update_x(const GArgs &a, cudaStream_t s) const { return elem == 4 ? Launch<4>::update_x(a, grid, s) : Launch<1>::update_x(a, grid, s); }
+    ztoep_status_t vnorm(const GArgs &a, cudaStream_t s) const {
+        return gm.elem == 4 ? Launch<4>::vnorm(a, grid, gm.threads, s) : Launch<2>::vnorm(a, grid, gm.threads, s);
+    }
+    ztoep_status_t residual(const GArgs &a, int first, cudaStream_t s) const {
+        return gm.elem == 4 ? Launch<4>::residual(a, grid, gm.threads, first, s)
+                            : Launch<2>::residual(a, grid, gm.threads, first, s);
+    }
+    ztoep_status_t arnoldi(const GArgs &a, cudaStream_t s) const {
+        return gm.elem == 4 ? Launch<4>::arnoldi(a, grid, gm.threads, s) : Launch<2>::arnoldi(a, grid, gm.threads, s);
+    }
+    ztoep_status_t update_x(const GArgs &a, cudaStream_t s) const {
+        return gm.elem == 4 ? Launch<4>::update_x(a, grid, gm.threads, s)
+                            : Launch<2>::update_x(a, grid, gm.threads, s);
+    }
 };
 
-static ztoep_status_t solve_impl(ztoep_plan_t p, const ztoep_solve_opts_t *o, int nrhs, const double2 *V,
-                                 double2 *X, ztoep_solve_info_t *info, cudaStream_t s) {
-    const auto t_start = std::chrono::steady_clock::now();
-    const int m = o->restart;
-    const bool mixed = o->prec == ZTOEP_MIXED;
-    ZT_TRY(ensure_solve_ws(p, nrhs, m));
-    if (mixed) ZT_TRY(ensure_ws<float>(p, nrhs));
-    ZT_TRY(ensure_ws<double>(p, nrhs));
-    SolveWs &w = p->sws;
-    const int elem = elem_for(p->N, p->nsm);
-    const int nchunk = (int)((p->N + (int64_t)NT_ * elem - 1) / ((int64_t)NT_ * elem));
-    GArgs a{};
-    a.Vb = w.Vb; a.w = w.w; a.r = w.r; a.x = X; a.v = V;
-    a.x32 = (float2 *)p->ws32.xin; a.y32 = (const float2 *)p->ws32.yout;
-    a.H = w.H; a.cs = w.cs; a.sn = w.sn; a.g = w.g; a.y = w.y; a.h1 = w.h1; a.h2 = w.h2; a.part = w.part;
-    a.nrm = w.nrm; a.st = w.st; a.cnt = w.cnt;
-    a.N = p->N; a.cap = w.cap; a.m = m; a.nchunk = nchunk; a.pstride = w.m + 2;
-    a.mixed = mixed ? 1 : 0;
-    a.tol = o->tol; a.inner_tol = o->inner_tol; a.max_iter = o->max_iter;
-    Ops ops{elem, dim3(nchunk, nrhs)};
+static ztoep_status_t launch_small(void (*k)(GArgs, cudaGraphConditionalHandle), int blocks, const GArgs &a,
+                                   cudaGraphConditionalHandle h, cudaStream_t s) {
+    KScope ks(K_MISC, s);
+    k<<<blocks, 256, 0, s>>>(a, h);
+    ZT_CUDA(cudaGetLastError());
+    return ZTOEP_OK;
+}
 
+// Add a conditional node after the work captured so far on `s`; returns its body.
+static ztoep_status_t add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                                      cudaGraph_t *body) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    ZT_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, nullptr, &ndeps));
+    if (cst != cudaStreamCaptureStatusActive) return ZTOEP_ERR_CUDA;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = type;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    ZT_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
+    *body = cp.conditional.phGraph_out[0];
+    ZT_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return ZTOEP_OK;
+}
+
+static ztoep_status_t capture_begin(cudaStream_t s, cudaGraph_t g, uint64_t *count) {
+    ZT_CUDA(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    capture_count_begin(count);
+    return ZTOEP_OK;
+}
+static ztoep_status_t capture_end(cudaStream_t s) {
+    capture_count_end();
+    cudaGraph_t out = nullptr;
+    ZT_CUDA(cudaStreamEndCapture(s, &out));
+    return ZTOEP_OK;
+}
+
+// Whole solve as one graph:
+//   begin -> IF(x != 0){FP64 product} -> residual -> sweep control ->
+//   WHILE(sweep){ cycle begin -> WHILE(iter){product, Arnoldi, iteration control}
+//                 -> x update -> FP64 product -> residual -> sweep control }
+static ztoep_status_t build_graph(ztoep_plan_t p, SolveGraph &sg, int prec, int nrhs, int m) {
+    const bool mixed = prec == ZTOEP_MIXED;
+    SolveWs &w = p->sws;
+    const Geom gm = geom_for(p->N, p->nsm);
+    const int per_cta = gm.threads * gm.elem;
+    const int nchunk = (int)((p->N + per_cta - 1) / per_cta);
+    const GArgs a = make_args(p, nrhs, m, mixed, nchunk);
+    const Ops ops{gm, dim3(nchunk, nrhs)};
+    cudaStream_t s = p->cap;
+    cudaGraph_t top = nullptr;
+    ZT_CUDA(cudaGraphCreate(&top, 0));
+    sg.graph = top;
+    cudaGraphConditionalHandle h_first, h_sweep, h_iter;
+    ZT_CUDA(cudaGraphConditionalHandleCreate(&h_first, top, 0, 0));
+    ZT_CUDA(cudaGraphConditionalHandleCreate(&h_sweep, top, 0, 0));
+    cudaGraph_t body_first = nullptr, body_sweep = nullptr, body_iter = nullptr;
+
+    // top level
+    ZT_TRY(capture_begin(s, top, &sg.k_fixed));
     ZT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(int) * (size_t)w.cap * ST_STRIDE, s));
     ZT_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(unsigned) * (size_t)w.cap * CNT_STRIDE, s));
-    const bool zero = (o->flags & ZTOEP_FLAG_ZERO_GUESS) != 0;
-    if (zero) ZT_CUDA(cudaMemsetAsync(X, 0, sizeof(double2) * (size_t)nrhs * p->N, s));
+    const int zblocks = (int)std::min<int64_t>(4 * p->nsm, ((int64_t)nrhs * p->N + 255) / 256);
+    ZT_TRY(launch_small(k_solve_begin, std::max(1, zblocks), a, h_first, s));
     ZT_TRY(ops.vnorm(a, s));
+    ZT_TRY(add_conditional(s, h_first, cudaGraphCondTypeIf, &body_first));
+    ZT_TRY(ops.residual(a, 1, s));
+    ZT_TRY(launch_small(k_sweep_ctl, 1, a, h_sweep, s));
+    ZT_TRY(add_conditional(s, h_sweep, cudaGraphCondTypeWhile, &body_sweep));
+    ZT_TRY(capture_end(s));
 
-    ztoep_status_t worst = ZTOEP_OK;
-    bool timed_out = false;
-    const int poll = 4;
-    for (int outer = 0;; ++outer) {
-        // true residual in FP64
-        if (!(zero && outer == 0)) ZT_TRY(run_matvec<double>(p, nrhs, X, w.r, s));
-        ZT_TRY(ops.residual(a, (zero && outer == 0) ? 1 : 0, s));
-        ZT_CUDA(cudaMemcpyAsync(w.hst, w.st, sizeof(int) * (size_t)nrhs * ST_STRIDE, cudaMemcpyDeviceToHost, s));
-        ZT_CUDA(cudaStreamSynchronize(s));
-        int nact = 0;
-        for (int rr = 0; rr < nrhs; ++rr) nact += w.hst[rr * ST_STRIDE + ST_ACTIVE];
-        if (nact == 0) break;
-        if (outer + 1 >= o->max_outer) { worst = ZTOEP_ERR_NOCONV; break; }
-        if (o->timeout_ns > 0) {
-            const auto el = std::chrono::duration_cast<std::chrono::nanoseconds>(
-                std::chrono::steady_clock::now() - t_start).count();
-            if (el > o->timeout_ns) { timed_out = true; break; }
+    // first product (skipped for a zero guess)
+    ZT_TRY(capture_begin(s, body_first, &sg.k_first_product));
+    ZT_TRY(run_matvec<double>(p, nrhs, w.xbuf, w.w, s));
+    ZT_TRY(capture_end(s));
+
+    // one sweep
+    ZT_CUDA(cudaGraphConditionalHandleCreate(&h_iter, body_sweep, 0, 0));
+    ZT_TRY(capture_begin(s, body_sweep, &sg.k_sweep));
+    ZT_TRY(launch_small(k_cycle_begin, 1, a, h_iter, s));
+    ZT_TRY(add_conditional(s, h_iter, cudaGraphCondTypeWhile, &body_iter));
+    ZT_TRY(ops.update_x(a, s));
+    ZT_TRY(run_matvec<double>(p, nrhs, w.xbuf, w.w, s));
+    ZT_TRY(ops.residual(a, 0, s));
+    ZT_TRY(launch_small(k_sweep_ctl, 1, a, h_sweep, s));
+    ZT_TRY(capture_end(s));
+
+    // one iteration
+    ZT_TRY(capture_begin(s, body_iter, &sg.k_iter));
+    if (mixed)
+        ZT_TRY(run_matvec<float>(p, nrhs, a.x32, (float2 *)p->ws32.yout, s));
+    else
+        ZT_TRY(run_matvec<double>(p, nrhs, w.xin64, w.w, s));
+    ZT_TRY(ops.arnoldi(a, s));
+    ZT_TRY(launch_small(k_iter_ctl, 1, a, h_iter, s));
+    ZT_TRY(capture_end(s));
+
+    ZT_CUDA(cudaGraphInstantiate(&sg.exec, top, 0));
+    sg.prec = prec;
+    sg.nrhs = nrhs;
+    sg.m = m;
+    return ZTOEP_OK;
+}
+
+static ztoep_status_t get_graph(ztoep_plan_t p, int prec, int nrhs, int m, SolveGraph **out) {
+    for (auto &g : p->graphs)
+        if (g.exec && g.prec == prec && g.nrhs == nrhs && g.m == m) {
+            *out = &g;
+            return ZTOEP_OK;
         }
-        // one GMRES cycle
-        ZT_TRY(ops.start(a, s));
-        for (int j = 0; j < m; ++j) {
-            if (mixed)
-                ZT_TRY(run_matvec<float>(p, nrhs, a.x32, (float2 *)p->ws32.yout, s));
-            else
-                ZT_TRY(run_matvec<double>(p, nrhs, w.Vb + (int64_t)j * w.cap * p->N, w.w, s));
-            ZT_TRY(ops.arnoldi(a, j, s));
-            if ((j + 1) % poll == 0 && j + 1 < m) {
-                ZT_CUDA(cudaMemcpyAsync(w.hst, w.st, sizeof(int) * (size_t)nrhs * ST_STRIDE,
-                                        cudaMemcpyDeviceToHost, s));
-                ZT_CUDA(cudaStreamSynchronize(s));
-                int na = 0;
-                for (int rr = 0; rr < nrhs; ++rr) na += w.hst[rr * ST_STRIDE + ST_ACTIVE];
-                if (na == 0) break;
-            }
+    SolveGraph &slot = p->graphs[p->graph_next];
+    p->graph_next = (p->graph_next + 1) % 4;
+    if (slot.exec) cudaGraphExecDestroy(slot.exec);
+    if (slot.graph) cudaGraphDestroy(slot.graph);
+    slot = SolveGraph{};
+    ztoep_status_t st = build_graph(p, slot, prec, nrhs, m);
+    if (st != ZTOEP_OK) {
+        capture_count_end();
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(p->cap, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(p->cap, &junk);
         }
-        ZT_TRY(ops.update_x(a, s));
+        cudaGetLastError();
+        if (slot.exec) cudaGraphExecDestroy(slot.exec);
+        if (slot.graph) cudaGraphDestroy(slot.graph);
+        slot = SolveGraph{};
+        return st;
     }
+    *out = &slot;
+    return ZTOEP_OK;
+}
+
+// Prepare buffers and the graph; V/X must already be in vbuf/xbuf (X only when
+// no zero guess).  Runs the solve graph on `s` and fetches the per-RHS state.
+static ztoep_status_t solve_core(ztoep_plan_t p, const ztoep_solve_opts_t *o, int nrhs, ztoep_solve_info_t *info,
+                                 cudaStream_t s) {
+    const int m = o->restart;
+    SolveGraph *g = nullptr;
+    ZT_TRY(get_graph(p, o->prec, nrhs, m, &g));
+    SolveWs &w = p->sws;
+    SolveCtl *hc = reinterpret_cast<SolveCtl *>(w.hst + (size_t)w.cap * ST_STRIDE);
+    std::memset(hc, 0, sizeof(SolveCtl));
+    hc->zero = (o->flags & ZTOEP_FLAG_ZERO_GUESS) ? 1 : 0;
+    hc->max_iter = o->max_iter;
+    hc->max_outer = o->max_outer;
+    hc->tol = o->tol;
+    hc->inner_tol = o->inner_tol;
+    hc->timeout_ns = o->timeout_ns;
+    ZT_CUDA(cudaMemcpyAsync(w.ctl, hc, sizeof(SolveCtl), cudaMemcpyHostToDevice, s));
+    ZT_CUDA(cudaGraphLaunch(g->exec, s));
     ZT_CUDA(cudaMemcpyAsync(w.hst, w.st, sizeof(int) * (size_t)nrhs * ST_STRIDE, cudaMemcpyDeviceToHost, s));
+    ZT_CUDA(cudaMemcpyAsync(hc, w.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
     ZT_CUDA(cudaMemcpyAsync(w.hnrm, w.nrm, sizeof(double) * (size_t)nrhs * NM_STRIDE, cudaMemcpyDeviceToHost, s));
+    int dev_err = 0;
+    ZT_CUDA(cudaMemcpyAsync(&dev_err, p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     ZT_CUDA(cudaStreamSynchronize(s));
+    add_launches(g->k_fixed + (hc->zero ? 0 : g->k_first_product) + (uint64_t)hc->outer_bodies * g->k_sweep +
+                 (uint64_t)hc->inner_bodies * g->k_iter);
+    bool timed_out = hc->timed_out != 0;
+    if (dev_err != 0) {  // a bounded device-side wait gave up
+        ZT_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), s));
+        timed_out = true;
+    }
+    ztoep_status_t worst = ZTOEP_OK;
     for (int rr = 0; rr < nrhs; ++rr) {
         const int *st = w.hst + rr * ST_STRIDE;
         const double *nm = w.hnrm + rr * NM_STRIDE;
@@ -544,6 +823,7 @@ static ztoep_status_t solve_impl(ztoep_plan_t p, const ztoep_solve_opts_t *o, in
             case RS_MAXITER: rs = ZTOEP_ERR_NOCONV; break;
             default: rs = timed_out ? ZTOEP_ERR_TIMEOUT : ZTOEP_ERR_NOCONV; break;
         }
+        if (dev_err != 0) rs = ZTOEP_ERR_TIMEOUT;
         if (rs != ZTOEP_OK && (worst == ZTOEP_OK || rs == ZTOEP_ERR_NONFINITE || rs == ZTOEP_ERR_TIMEOUT))
             worst = rs;
         if (info) {
@@ -553,8 +833,14 @@ static ztoep_status_t solve_impl(ztoep_plan_t p, const ztoep_solve_opts_t *o, in
             info[rr].rel_residual = nm[NM_VNORM] > 0 ? nm[NM_RNORM] / nm[NM_VNORM] : nm[NM_RNORM];
         }
     }
-    if (timed_out && worst == ZTOEP_ERR_NOCONV) worst = ZTOEP_ERR_TIMEOUT;
     return worst;
+}
+
+static ztoep_status_t prepare(ztoep_plan_t p, const ztoep_solve_opts_t *o, int nrhs) {
+    ZT_TRY(ensure_solve_ws(p, nrhs, o->restart));
+    if (o->prec == ZTOEP_MIXED) ZT_TRY(ensure_ws<float>(p, nrhs));
+    ZT_TRY(ensure_ws<double>(p, nrhs));
+    return ZTOEP_OK;
 }
 
 }  // namespace ztoep
@@ -573,7 +859,17 @@ ztoep_status_t ztoep_solve(ztoep_plan_t p, const ztoep_solve_opts_t *o, int32_t 
                            ztoep_solve_info_t *info, void *stream) {
     if (!p || !valid_opts(o) || nrhs < 1 || !V || !X || V == X) return ZTOEP_ERR_ARG;
     std::lock_guard<std::mutex> lk(p->mu);
-    return solve_impl(p, o, nrhs, (const double2 *)V, (double2 *)X, info, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    ZT_TRY(prepare(p, o, nrhs));
+    SolveWs &w = p->sws;
+    const size_t bytes = sizeof(double2) * (size_t)nrhs * p->N;
+    ZT_CUDA(cudaMemcpyAsync(w.vbuf, V, bytes, cudaMemcpyDeviceToDevice, s));
+    if (!(o->flags & ZTOEP_FLAG_ZERO_GUESS)) ZT_CUDA(cudaMemcpyAsync(w.xbuf, X, bytes, cudaMemcpyDeviceToDevice, s));
+    const ztoep_status_t st = solve_core(p, o, nrhs, info, s);
+    if (st == ZTOEP_ERR_ARG || st == ZTOEP_ERR_CUDA || st == ZTOEP_ERR_NOMEM || st == ZTOEP_ERR_UNSUPPORTED)
+        return st;
+    ZT_CUDA(cudaMemcpyAsync(X, w.xbuf, bytes, cudaMemcpyDeviceToDevice, s));
+    return st;
 }
 
 ztoep_status_t ztoep_solve_host(ztoep_plan_t p, const ztoep_solve_opts_t *o, int32_t nrhs, const void *Vh,
@@ -581,15 +877,15 @@ ztoep_status_t ztoep_solve_host(ztoep_plan_t p, const ztoep_solve_opts_t *o, int
     if (!p || !valid_opts(o) || nrhs < 1 || !Vh || !Xh) return ZTOEP_ERR_ARG;
     std::lock_guard<std::mutex> lk(p->mu);
     cudaStream_t s = (cudaStream_t)stream;
-    ZT_TRY(ensure_ws<double>(p, nrhs));
-    // the FP64 workspace in/out buffers hold V and X on the device
-    double2 *Vd = (double2 *)p->ws64.xin, *Xd = (double2 *)p->ws64.yout;
+    ZT_TRY(prepare(p, o, nrhs));
+    SolveWs &w = p->sws;
     const size_t bytes = sizeof(double2) * (size_t)nrhs * p->N;
-    ZT_CUDA(cudaMemcpyAsync(Vd, Vh, bytes, cudaMemcpyHostToDevice, s));
-    if (!(o->flags & ZTOEP_FLAG_ZERO_GUESS)) ZT_CUDA(cudaMemcpyAsync(Xd, Xh, bytes, cudaMemcpyHostToDevice, s));
-    ztoep_status_t st = solve_impl(p, o, nrhs, Vd, Xd, info, s);
-    if (st == ZTOEP_ERR_ARG || st == ZTOEP_ERR_CUDA || st == ZTOEP_ERR_NOMEM) return st;
-    ZT_CUDA(cudaMemcpyAsync(Xh, Xd, bytes, cudaMemcpyDeviceToHost, s));
+    ZT_CUDA(cudaMemcpyAsync(w.vbuf, Vh, bytes, cudaMemcpyHostToDevice, s));
+    if (!(o->flags & ZTOEP_FLAG_ZERO_GUESS)) ZT_CUDA(cudaMemcpyAsync(w.xbuf, Xh, bytes, cudaMemcpyHostToDevice, s));
+    const ztoep_status_t st = solve_core(p, o, nrhs, info, s);
+    if (st == ZTOEP_ERR_ARG || st == ZTOEP_ERR_CUDA || st == ZTOEP_ERR_NOMEM || st == ZTOEP_ERR_UNSUPPORTED)
+        return st;
+    ZT_CUDA(cudaMemcpyAsync(Xh, w.xbuf, bytes, cudaMemcpyDeviceToHost, s));
     ZT_CUDA(cudaStreamSynchronize(s));
     return st;
 }

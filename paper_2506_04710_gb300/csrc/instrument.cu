@@ -13,6 +13,11 @@ namespace ztoep {
 
 static std::atomic<uint64_t> g_launches{0};
 static std::atomic<int> g_mask{0};
+static thread_local uint64_t *t_capture_sink = nullptr;  // launches recorded into a graph
+
+void capture_count_begin(uint64_t *sink) { t_capture_sink = sink; }
+void capture_count_end() { t_capture_sink = nullptr; }
+void add_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 struct Pending {
     int cls;
@@ -37,7 +42,10 @@ static cudaEvent_t take_event() {
 }
 
 KScope::KScope(KClass c, cudaStream_t s) : cls_(c), s_(s), a_(nullptr) {
-    if (g_mask.load(std::memory_order_relaxed) & (1 << c)) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s_, &cs);
+    capturing_ = cs != cudaStreamCaptureStatusNone;
+    if (!capturing_ && (g_mask.load(std::memory_order_relaxed) & (1 << c))) {
         std::lock_guard<std::mutex> lk(g_mu);
         a_ = take_event();
         cudaEventRecord(a_, s_);
@@ -45,6 +53,10 @@ KScope::KScope(KClass c, cudaStream_t s) : cls_(c), s_(s), a_(nullptr) {
 }
 
 KScope::~KScope() {
+    if (capturing_) {  // counted when the graph runs
+        if (t_capture_sink) *t_capture_sink += n_;
+        return;
+    }
     g_launches.fetch_add(n_, std::memory_order_relaxed);
     if (a_) {
         std::lock_guard<std::mutex> lk(g_mu);

@@ -22,6 +22,14 @@ class KScope {
     cudaStream_t s_;
     cudaEvent_t a_;
     int n_ = 1;
+    bool capturing_ = false;
 };
+
+// Launches made while a stream is being captured are added to *sink (on this
+// thread) instead of the process counter; graph replays are counted with
+// add_launches.
+void capture_count_begin(uint64_t *sink);
+void capture_count_end();
+void add_launches(uint64_t n);
 
 }  // namespace ztoep

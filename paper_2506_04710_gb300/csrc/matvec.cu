@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "tma.cuh"
 
 namespace ztoep {
 
@@ -148,6 +149,120 @@ __global__ void __launch_bounds__(256) k_blockprod(const int2 *__restrict__ pair
     }
 }
 
+// Pipelined variant: persistent CTAs walk their pairs; for each pair the
+// T^ block and the X^[f], X^[-f] slabs arrive by bulk async copies (TMA) into
+// one of NST shared-memory stages, so NST pairs are in flight per CTA while
+// the current one is multiplied.  Each output dot product may be split over S
+// threads (S | b) so that every thread has work when 2 nrhs b < threads.
+constexpr uint32_t kWaitTries = 1u << 22;  // bounded mbarrier waits
+enum { ZT_ERRBIT_BLOCKPROD_WAIT = 1 };
+
+template <typename R, int NST>
+__global__ void __launch_bounds__(256) k_blockprod_tma(const int2 *__restrict__ pairs, int npairs,
+                                                       const cplx_t<R> *__restrict__ That, cplx_t<R> *Xh, int b,
+                                                       int nrhs, int S, int *err) {
+    using C = cplx_t<R>;
+    extern __shared__ __align__(128) unsigned char zt_smem[];
+    __shared__ __align__(8) uint64_t full[NST];
+    __shared__ double2 red_raw[256];
+    C *red = reinterpret_cast<C *>(red_raw);
+    const int bb = b * b, rb = nrhs * b;
+    const int stage_elems = bb + 2 * rb;
+    C *stages = reinterpret_cast<C *>(zt_smem);
+    const uint32_t tbytes = (uint32_t)(bb * sizeof(C)), xbytes = (uint32_t)(rb * sizeof(C));
+    const int my = (npairs - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) mbar_init(&full[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    auto issue = [&](int it) {  // thread 0
+        const int p = blockIdx.x + it * gridDim.x;
+        const int s = it % NST;
+        const int2 fg = pairs[p];
+        C *st = stages + (size_t)s * stage_elems;
+        mbar_arrive_expect_tx(&full[s], tbytes + xbytes * (fg.y != fg.x ? 2u : 1u));
+        bulk_g2s(st, That + (size_t)p * bb, tbytes, &full[s]);
+        bulk_g2s(st + bb, Xh + (size_t)fg.x * rb, xbytes, &full[s]);
+        if (fg.y != fg.x) bulk_g2s(st + bb + rb, Xh + (size_t)fg.y * rb, xbytes, &full[s]);
+    };
+    if (threadIdx.x == 0)
+        for (int it = 0; it < NST && it < my; ++it) issue(it);
+    const int seg = b / S;
+    for (int it = 0; it < my; ++it) {
+        const int s = it % NST;
+        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((it / NST) & 1), kWaitTries);
+        if (__syncthreads_or(!ok)) {  // a copy never landed: record, drain what is in flight, leave
+            if (threadIdx.x == 0) {
+                atomicOr(err, ZT_ERRBIT_BLOCKPROD_WAIT);
+                for (int k = it + 1; k < my && k < it + NST; ++k)
+                    mbar_wait_bounded(&full[k % NST], (uint32_t)((k / NST) & 1), kWaitTries);
+            }
+            return;
+        }
+        const int p = blockIdx.x + it * gridDim.x;
+        const int2 fg = pairs[p];
+        const bool two = fg.y != fg.x;
+        const C *T = stages + (size_t)s * stage_elems;
+        const C *xf = T + bb, *xg = xf + rb;
+        C *of = Xh + (size_t)fg.x * rb, *og = Xh + (size_t)fg.y * rb;
+        const int nout = (two ? 2 : 1) * rb;
+        if (S == 1) {
+            for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+                C acc = czero<C>();
+                if (o < rb) {
+                    const int rr = o / b, i = o - rr * b;
+                    const C *row = T + (size_t)i * b, *xv = xf + (size_t)rr * b;
+                    int j = i;
+                    for (int jj = 0; jj < b; ++jj) {
+                        acc = cfma(row[j], xv[j], acc);
+                        if (++j == b) j = 0;
+                    }
+                    of[o] = acc;
+                } else {
+                    const int o2 = o - rb, rr = o2 / b, j = o2 - rr * b;
+                    const C *xv = xg + (size_t)rr * b;
+                    for (int i = 0; i < b; ++i) acc = cfma(T[(size_t)i * b + j], xv[i], acc);
+                    og[o2] = acc;
+                }
+            }
+        } else {
+            // outputs in chunks of opc, each dot split over S threads; the split
+            // depends on b only, so a RHS is summed identically in any batch
+            const int opc = blockDim.x / S;
+            const int t = threadIdx.x, ol = t % opc, sp = t / opc;
+            for (int ob = 0; ob < nout; ob += opc) {
+                const int o = ob + ol;
+                C acc = czero<C>();
+                if (o < rb) {
+                    const int rr = o / b, i = o - rr * b;
+                    const C *row = T + (size_t)i * b, *xv = xf + (size_t)rr * b;
+                    int j = i + sp * seg;
+                    if (j >= b) j -= b;
+                    for (int jj = 0; jj < seg; ++jj) {
+                        acc = cfma(row[j], xv[j], acc);
+                        if (++j == b) j = 0;
+                    }
+                } else if (o < nout) {
+                    const int o2 = o - rb, rr = o2 / b, j = o2 - rr * b;
+                    const C *xv = xg + (size_t)rr * b;
+                    for (int i = sp * seg; i < (sp + 1) * seg; ++i) acc = cfma(T[(size_t)i * b + j], xv[i], acc);
+                }
+                red[sp * opc + ol] = acc;
+                __syncthreads();
+                if (sp == 0 && o < nout) {
+                    C tot = red[ol];
+                    for (int q = 1; q < S; ++q) tot = tot + red[q * opc + ol];
+                    if (o < rb) of[o] = tot; else og[o - rb] = tot;
+                }
+                __syncthreads();
+            }
+        }
+        __syncthreads();  // stage s is free again
+        if (threadIdx.x == 0 && it + NST < my) issue(it + NST);
+    }
+}
+
 // ------------------------------------------------------------ edge coupling
 // One pass over B [E][ldb] (row e = edge unknown, column t = Toeplitz unknown)
 // computing, for RHS r0..r0+RC-1,
@@ -212,29 +327,45 @@ __global__ void __launch_bounds__(256) k_edge(const cplx_t<R> *__restrict__ x, c
             sxe[el][q] = (el < ne && q < rc) ? x[(int64_t)(r0 + q) * N + NT + ec + el] : czero<C>();
         }
         __syncthreads();
-        for (int el = 0; el < ne; ++el) {
-            const C *brow = B + (int64_t)(ec + el) * ldb + tbase;
-            C bv[U][CPL];
+        // Rows are consumed in groups of UNR whose loads are all issued first,
+        // so each warp keeps UNR * 512 bytes of B in flight.
+        constexpr int UNR = 4;
+        for (int el0 = 0; el0 < ne; el0 += UNR) {
+            float4 raw[UNR][U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const float4 raw = __ldg(reinterpret_cast<const float4 *>(brow + (int64_t)(u * 32 + lane) * CPL));
-                const C *pc = reinterpret_cast<const C *>(&raw);
-#pragma unroll
-                for (int c = 0; c < CPL; ++c) bv[u][c] = pc[c];
-            }
-#pragma unroll
-            for (int q = 0; q < RC; ++q) {
-                const C xe = sxe[el][q];
-                C part = czero<C>();
+            for (int k = 0; k < UNR; ++k) {
+                const C *brow = B + (int64_t)(ec + el0 + k) * ldb + tbase;
 #pragma unroll
                 for (int u = 0; u < U; ++u)
+                    raw[k][u] = (el0 + k < ne)
+                                    ? __ldcs(reinterpret_cast<const float4 *>(brow + (int64_t)(u * 32 + lane) * CPL))
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
 #pragma unroll
-                    for (int c = 0; c < CPL; ++c) {
-                        acc[u][c][q] = cfma(bv[u][c], xe, acc[u][c][q]);
-                        part = cfma(bv[u][c], xt[u][c][q], part);
-                    }
-                part = warp_sum<R>(part);
-                if (lane == 0) red[warp][el][q] = part;
+            for (int k = 0; k < UNR; ++k) {
+                const int el = el0 + k;
+                if (el >= ne) break;  // uniform across the CTA
+                C bv[U][CPL];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const C *pc = reinterpret_cast<const C *>(&raw[k][u]);
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) bv[u][c] = pc[c];
+                }
+#pragma unroll
+                for (int q = 0; q < RC; ++q) {
+                    const C xe = sxe[el][q];
+                    C part = czero<C>();
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+#pragma unroll
+                        for (int c = 0; c < CPL; ++c) {
+                            acc[u][c][q] = cfma(bv[u][c], xe, acc[u][c][q]);
+                            part = cfma(bv[u][c], xt[u][c][q], part);
+                        }
+                    part = warp_sum<R>(part);
+                    if (lane == 0) red[warp][el][q] = part;
+                }
             }
         }
         __syncthreads();
@@ -318,9 +449,11 @@ static int edge_ntile(ztoep_plan_t p, size_t csize) {
     int tile = (csize == 8) ? EdgeGeom<float>::TILE : EdgeGeom<double>::TILE;
     return (int)((p->NT + tile - 1) / tile);
 }
-static int edge_nsplit(ztoep_plan_t p, int ntile) {
+static int edge_nsplit(ztoep_plan_t p, int ntile, size_t csize) {
     if (p->E == 0) return 0;
-    int want = (2 * p->nsm + ntile - 1) / ntile;
+    // enough CTAs for several resident per SM (FP32: 4 per SM, FP64: 2)
+    const int per_sm = csize == 8 ? 4 : 2;
+    int want = (per_sm * p->nsm + ntile - 1) / ntile;
     int maxs = std::max(1, p->E / 32);
     return std::max(1, std::min(want, maxs));
 }
@@ -333,10 +466,11 @@ static void free_ws(MatvecWs &w) {
 template <typename R> ztoep_status_t ensure_ws(ztoep_plan_t p, int nrhs) {
     MatvecWs &w = ws_of<R>(p);
     if (w.cap >= nrhs) return ZTOEP_OK;
+    free_solve_graphs(p);
     free_ws(w);
     const size_t cs = sizeof(cplx_t<R>);
     const int ntile = edge_ntile(p, cs);
-    const int nsplit = edge_nsplit(p, ntile);
+    const int nsplit = edge_nsplit(p, ntile, cs);
     size_t acc = 0;
     ZT_TRY(dalloc(&w.xin, cs * nrhs * p->N, &acc));
     ZT_TRY(dalloc(&w.yout, cs * nrhs * p->N, &acc));
@@ -396,6 +530,31 @@ static ztoep_status_t launch_blockprod(ztoep_plan_t p, int nrhs, cplx_t<R> *Xh, 
     const size_t cs = sizeof(cplx_t<R>);
     const size_t budget = 200 * 1024;
     const size_t tbytes = cs * (size_t)p->b * p->b;
+    const size_t xbytes = cs * (size_t)nrhs * p->b;
+    const size_t stage = tbytes + 2 * xbytes;
+    KScope ks(K_BLOCKPROD, s);
+    if (tbytes % 16 == 0 && xbytes % 16 == 0 && 2 * stage <= budget) {
+        // pipelined bulk-copy path
+        const int nst = 3 * stage <= budget ? 3 : 2;
+        const size_t smem = nst * stage;
+        const int per_sm = std::max<int>(1, std::min<int>(4, (int)((227 * 1024) / (smem + 6 * 1024))));
+        const int grid = std::min(p->npairs, p->nsm * per_sm);
+        int S = 1;  // threads per dot product: from b only (batch-independent sums)
+        for (int c : {8, 4, 2})
+            if (p->b % c == 0 && c * 2 * p->b <= 256) { S = c; break; }
+        static bool attr = false;
+        if (!attr) {
+            ZT_CUDA(cudaFuncSetAttribute(k_blockprod_tma<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
+            ZT_CUDA(cudaFuncSetAttribute(k_blockprod_tma<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
+            attr = true;
+        }
+        if (nst == 3)
+            k_blockprod_tma<R, 3><<<grid, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, p->b, nrhs, S, p->err);
+        else
+            k_blockprod_tma<R, 2><<<grid, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, p->b, nrhs, S, p->err);
+        ZT_CUDA(cudaGetLastError());
+        return ZTOEP_OK;
+    }
     if (tbytes + 2 * cs * p->b > budget) return ZTOEP_ERR_UNSUPPORTED;
     const int rch = (int)std::min<size_t>((size_t)nrhs, (budget - tbytes) / (2 * cs * p->b));
     const size_t smem = tbytes + 2 * cs * (size_t)rch * p->b;
@@ -404,7 +563,6 @@ static ztoep_status_t launch_blockprod(ztoep_plan_t p, int nrhs, cplx_t<R> *Xh, 
         ZT_CUDA(cudaFuncSetAttribute(k_blockprod<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         attr = true;
     }
-    KScope ks(K_BLOCKPROD, s);
     k_blockprod<R><<<p->npairs, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, p->b, nrhs, rch);
     ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
@@ -415,7 +573,7 @@ static ztoep_status_t launch_edge(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, 
                                   MatvecWs &w, cudaStream_t s) {
     const size_t cs = sizeof(cplx_t<R>);
     const int ntile = edge_ntile(p, cs);
-    const int nsplit = edge_nsplit(p, ntile);
+    const int nsplit = edge_nsplit(p, ntile, cs);
     const int eps = (p->E + nsplit - 1) / nsplit;
     cplx_t<R> *ET = reinterpret_cast<cplx_t<R> *>(w.ET);
     cplx_t<R> *Ep = reinterpret_cast<cplx_t<R> *>(w.Ep);
@@ -447,7 +605,7 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
     cplx_t<R> *X1 = reinterpret_cast<cplx_t<R> *>(w.X1);
     cplx_t<R> *Xh = reinterpret_cast<cplx_t<R> *>(w.Xh);
     const int ntile = edge_ntile(p, cs);
-    const int nsplit = edge_nsplit(p, ntile);
+    const int nsplit = edge_nsplit(p, ntile, cs);
     if (p->E > 0) {  // edge branch on the side stream, concurrent with the FFT chain
         ZT_CUDA(cudaEventRecord(p->ev_fork, s));
         ZT_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
@@ -564,7 +722,7 @@ extern "C" ztoep_status_t ztoep_edge_product_noalloc(ztoep_plan_t p, int32_t nrh
         return ZTOEP_OK;
     }
     const int ntile = edge_ntile(p, sizeof(double2));
-    const int nsplit = edge_nsplit(p, ntile);
+    const int nsplit = edge_nsplit(p, ntile, sizeof(double2));
     const size_t et_bytes = round256(sizeof(double2) * (size_t)nsplit * nrhs * p->NT);
     const size_t ep_bytes = round256(sizeof(double2) * (size_t)ntile * nrhs * p->E);
     if (et_bytes + ep_bytes > kNoAllocScratchBytes) return ZTOEP_ERR_NOMEM;

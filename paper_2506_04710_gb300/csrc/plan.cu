@@ -215,6 +215,7 @@ void ztoep_plan_destroy(ztoep_plan_t p) {
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
     if (p->side) cudaStreamDestroy(p->side);
+    if (p->cap) cudaStreamDestroy(p->cap);
     cudaSetDevice(cur);
     delete p;
 }
@@ -249,6 +250,7 @@ static ztoep_status_t plan_build(ztoep_plan_t p, const ztoep_desc_t *d, const do
     ZT_CUDA(cudaGetDevice(&p->device));
     ZT_CUDA(cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device));
     ZT_CUDA(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+    ZT_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
     ZT_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     ZT_CUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
     ZT_TRY(dalloc((void **)&p->err, sizeof(int) * 4, &acc));
