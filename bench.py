@@ -196,7 +196,7 @@ def run_ours(args, world, rank, local):
     def opts(prec):
         o = ztoep.ztoep_default_opts()
         o.prec, o.tol, o.restart = prec, tol, args.restart
-        o.flags = ztoep.ZTOEP_FLAG_ZERO_GUESS
+        o.flags = ztoep.ZTOEP_FLAG_ZERO_GUESS | (ztoep.ZTOEP_FLAG_HOST_LOOP if args.host_loop else 0)
         return o
 
     o_mixed = opts(ztoep.ZTOEP_MIXED)
@@ -370,6 +370,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the solver loops from the host (for profilers; slower)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

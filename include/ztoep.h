@@ -102,6 +102,10 @@ typedef struct {
 
 /* Ignore X on entry and start from x = 0 (saves the first FP64 product). */
 #define ZTOEP_FLAG_ZERO_GUESS 1
+/* Drive the refinement and GMRES loops from the host, one kernel launch at a
+ * time, instead of one CUDA graph with conditional nodes (same kernels and
+ * results; slower; for profilers that cannot look inside such graphs). */
+#define ZTOEP_FLAG_HOST_LOOP 2
 
 typedef struct {
     int32_t outer;        /* true-residual evaluations (refinement sweeps) */

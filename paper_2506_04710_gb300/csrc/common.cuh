@@ -106,6 +106,8 @@ struct SolveWs {  // Krylov workspace, sized for `cap` RHS and restart `m`
     double2 *xin64 = nullptr;  // [cap][N] FP64 product input (next basis vector)
     double2 *vbuf = nullptr;   // [cap][N] right-hand sides (graph-owned copy)
     double2 *xbuf = nullptr;   // [cap][N] iterate (graph-owned copy)
+    double2 *rbuf = nullptr;   // [cap][N] FP64 true residual of the current sweep
+    double2 *dbuf = nullptr;   // [cap][N] correction accumulated over the sweep's restarts
     double2 *H = nullptr;      // [cap][m+1][m] Hessenberg (rotated to R)
     double2 *cs = nullptr;     // [cap][m]
     double2 *sn = nullptr;     // [cap][m]
@@ -128,7 +130,7 @@ struct SolveGraph {
     int prec = -1, nrhs = 0, m = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    uint64_t k_fixed = 0, k_sweep = 0, k_iter = 0, k_first_product = 0;  // kernels per part
+    uint64_t k_fixed = 0, k_sweep = 0, k_restart = 0, k_iter = 0, k_first_product = 0;  // kernels per part
 };
 
 struct PlanImpl;

@@ -148,9 +148,24 @@ inline size_t fft_smem_bytes(int L, int lib, size_t csize) {
     return (size_t)(L + 2 * (size_t)L * ((size_t)1 << lib)) * csize;
 }
 
+// Pass geometry: the channel batch is shrunk (down to 32-byte chunks per
+// line) until the grid covers every SM twice, and the CTA gets about one
+// thread per radix-4 butterfly.
+struct PassCfg {
+    int lib, threads;
+};
+inline PassCfg pass_cfg(int L, int channels, int lines, size_t csize, int nsm) {
+    int lib = pick_lib(L, channels, csize, 64 * 1024);
+    const int min_lib = csize == 8 ? 2 : 1;
+    while (lib > min_lib && (int64_t)((channels + (1 << lib) - 1) >> lib) * lines < 2LL * nsm) --lib;
+    int thr = ((L << lib) / 4 + 31) / 32 * 32;
+    thr = thr < 64 ? 64 : (thr > 256 ? 256 : thr);
+    return {lib, thr};
+}
+
 template <typename R, typename Ld, typename St>
 ztoep_status_t launch_fft_pass(const Fft1D &pl, const cplx_t<R> *tw, int lib, bool inv, dim3 grid,
-                               Ld ld, St st, cudaStream_t s) {
+                               Ld ld, St st, cudaStream_t s, int threads = 256) {
     size_t smem = fft_smem_bytes(pl.L, lib, sizeof(cplx_t<R>));
     static bool attr_set = false;  // one instantiation per (R, Ld, St)
     if (!attr_set) {
@@ -159,7 +174,7 @@ ztoep_status_t launch_fft_pass(const Fft1D &pl, const cplx_t<R> *tw, int lib, bo
         attr_set = true;
     }
     KScope ks(K_FFT, s);
-    k_fft_pass<R, Ld, St><<<grid, 256, smem, s>>>(pl, tw, lib, inv ? 1 : 0, ld, st);
+    k_fft_pass<R, Ld, St><<<grid, threads, smem, s>>>(pl, tw, lib, inv ? 1 : 0, ld, st);
     ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
 }

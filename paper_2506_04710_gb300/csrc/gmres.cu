@@ -6,8 +6,8 @@
 // Inner cycle:         GMRES(m) on Z' d = r (Saad & Schultz 1986) with
 //                      classical Gram-Schmidt and selective
 //                      reorthogonalisation (a second pass only when the first
-//                      one cancels more than 1 - 1/sqrt(2) of ||w||, the
-//                      criterion of Daniel, Gragg, Kaufman & Stewart 1976),
+//                      one leaves less than eta ||w||, the criterion of
+//                      Daniel, Gragg, Kaufman & Stewart 1976),
 //                      Givens rotations, least squares R y = g, x <- x + V y.
 //                      The products inside the cycle are FP32 (MIXED) or FP64
 //                      (FP64); Arnoldi, rotations and updates are FP64.
@@ -29,11 +29,20 @@
 namespace ztoep {
 
 enum { ST_ACTIVE = 0, ST_JLEN = 1, ST_ITERS = 2, ST_STATUS = 3, ST_OUTER = 4, ST_PENDING = 5, ST_REORTH = 6,
-       ST_STRIDE = 8 };
+       ST_INNER = 7, ST_RESTARTS = 8, ST_STRIDE = 12 };
 enum { RS_RUNNING = 0, RS_CONVERGED = 1, RS_NONFINITE = 2, RS_MAXITER = 3 };
-enum { NM_VNORM = 0, NM_TARGET = 2, NM_RNORM = 3, NM_W0 = 5, NM_STRIDE = 8 };
+enum { NM_VNORM = 0, NM_TARGET = 2, NM_RNORM = 3, NM_W0 = 5, NM_RIN = 6, NM_STRIDE = 8 };
+// Inner (FP32-residual) restarts of one sweep: at most this many, and they stop
+// early when a restart reduces the inner residual by less than 10%.
+constexpr int kMaxRestarts = 64;
+constexpr double kStagnation = 0.9;
 enum { CNT_STRIDE = 4 };
-constexpr double kReorthEta = 0.70710678118654752440;  // 1/sqrt(2)
+// Second Gram-Schmidt pass when ||w'|| < eta ||w||.  The orthogonality lost by
+// one classical pass is about u ||w|| / ||w'||, so eta = 1/64 keeps it below
+// 64 u (~7e-15), far under what the residual targets need, while skipping the
+// pass in the usual case (the stricter 1/sqrt(2) of "twice is enough" asked
+// for it at every step on these systems, doubling the FP64 work).
+constexpr double kReorthEta = 1.0 / 64.0;
 
 // Device-side control of one solve (written by the host before each launch of
 // the solve graph; loop counters advanced by the control kernels).
@@ -45,6 +54,8 @@ struct SolveCtl {
     int max_iter, max_outer;
     int outer_bodies;    // executions of the sweep body (for launch accounting)
     int inner_bodies;    // executions of the iteration body
+    int restart_bodies;  // executions of the restart body
+    int cond_first, cond_sweep, cond_restart, cond_iter;  // loop decisions (read by the host-driven mode)
     double tol, inner_tol;
     long long timeout_ns;
     unsigned long long deadline;  // %globaltimer value, 0 = none
@@ -60,6 +71,8 @@ struct GArgs {
     double2 *H, *cs, *sn, *g, *y, *h1, *h2, *part;
     double *beta;      // [cap][m+1] ||u_k||
     double2 *xin64;    // [cap][N] FP64 copy of the next product input (FP64)
+    double2 *rbuf;     // [cap][N] FP64 residual r of the sweep
+    double2 *dbuf;     // [cap][N] correction d of the sweep
     double *nrm;
     int *st;
     unsigned *cnt;
@@ -199,6 +212,8 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_residual(GArgs a, i
             const int64_t o = (int64_t)rr * a.N + idx;
             const double2 t = zero ? a.v[o] : a.v[o] - a.w[o];
             u0[idx] = t;
+            a.rbuf[o] = t;
+            a.dbuf[o] = make_double2(0, 0);
             if (a.mixed)
                 a.x32[o] = make_float2((float)t.x, (float)t.y);
             else
@@ -220,6 +235,8 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_residual(GArgs a, i
     st[ST_JLEN] = 0;
     st[ST_ACTIVE] = 0;
     st[ST_REORTH] = 0;
+    st[ST_INNER] = 0;
+    st[ST_RESTARTS] = 0;
     if (!isfinite(vn) || !isfinite(rn)) {
         st[ST_STATUS] = RS_NONFINITE;
     } else if (rn <= a.ctl->tol * vn || rn == 0.0) {
@@ -228,6 +245,8 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_residual(GArgs a, i
         st[ST_STATUS] = RS_MAXITER;
     } else {
         st[ST_ACTIVE] = 1;
+        st[ST_INNER] = 1;
+        nm[NM_RIN] = rn;
         a.beta[(int64_t)rr * (a.m + 1)] = rn;
         const double floor_abs = 0.5 * a.ctl->tol * vn;
         nm[NM_TARGET] = a.mixed ? fmax(a.ctl->inner_tol * rn, floor_abs) : floor_abs;
@@ -284,14 +303,65 @@ __device__ void finalize_column(const GArgs &a, int rr, int j, const double2 *h,
     }
 }
 
-// Gram-Schmidt dots.  PASS 1: w = (product of u_j) / beta_j is formed (from the
-// FP32 or FP64 product) and stored as u_{j+1}; h1_k = <v_k, w>, ||w||.
-// PASS 2 (only RHS flagged for reorthogonalisation): h2_k = <v_k, u_{j+1}>.
+// Partial dot products <u_k, w> for k in [k0, k0+8) (k <= j) plus, when
+// with_norm and k0 + kk == j + 1, ||w||^2 in that slot; CTA totals -> part.
+template <int ELEM>
+__device__ __forceinline__ void dots_group(const GArgs &a, int rr, int j, int k0, bool with_norm,
+                                           const double2 (&wv)[ELEM], int64_t base, double2 *part, double2 *red) {
+    double2 acc[8];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) acc[kk] = make_double2(0, 0);
+    if (k0 + 7 <= j) {  // full group: the 8 loads of an element are in flight together
+        const double2 *u0 = basis(a, k0, rr);
+        const int64_t vstride = (int64_t)a.cap * a.N;
+#pragma unroll
+        for (int e = 0; e < ELEM; ++e) {
+            const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
+            if (idx < a.N) {
+                double2 uv[8];
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) uv[kk] = u0[kk * vstride + idx];
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) acc[kk] = cfmac(uv[kk], wv[e], acc[kk]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const int k = k0 + kk;
+            if (k <= j) {
+                const double2 *uk = basis(a, k, rr);
+#pragma unroll
+                for (int e = 0; e < ELEM; ++e) {
+                    const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
+                    if (idx < a.N) acc[kk] = cfmac(uk[idx], wv[e], acc[kk]);
+                }
+            } else if (with_norm && k == j + 1) {
+#pragma unroll
+                for (int e = 0; e < ELEM; ++e) acc[kk].x += cabs2(wv[e]);
+            }
+        }
+    }
+    block_sum8(acc, red);
+    const int K = j + 1 + (with_norm ? 1 : 0);
+    if (threadIdx.x < 8 && k0 + (int)threadIdx.x < K)
+        part[(int64_t)blockIdx.x * a.pstride + k0 + threadIdx.x] = red[threadIdx.x];
+    __syncthreads();
+}
+
+// Gram-Schmidt dots.
+// PASS 1: w = (product of u_j) / beta_j is formed (from the FP32 or FP64
+//   product) and stored as u_{j+1}; h1_k = <v_k, w> and ||w||.  The last CTA
+//   gets ||w - V h1|| from ||w||^2 - sum |h1_k|^2 (exact for orthonormal v_k up
+//   to rounding of order u ||w||^2 / ||w'||^2, below 4096 u when no second pass
+//   is taken); it either flags the RHS for a second pass or finalises the
+//   Hessenberg column at once, so the update pass needs no reduction.
+// PASS 2 (flagged RHS only): h2_k = <v_k, u_{j+1}>.
 template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(GArgs a) {
     __shared__ double2 red[64];
     __shared__ double2 tot[130];
     const int rr = blockIdx.y;
-    const int *st = a.st + rr * ST_STRIDE;
+    int *st = a.st + rr * ST_STRIDE;
     if (!st[ST_ACTIVE]) return;
     if (PASS == 2 && !st[ST_REORTH]) return;
     const int j = a.ctl->j;
@@ -321,41 +391,34 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(GArg
             }
         }
     }
-    const int K = j + 1 + (PASS == 1 ? 1 : 0);  // dots with u_0..u_j (+ ||w||^2 last in pass 1)
+    const int K = j + 1 + (PASS == 1 ? 1 : 0);
     double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
-    for (int k0 = 0; k0 < K; k0 += 8) {
-        double2 acc[8];
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-            acc[kk] = make_double2(0, 0);
-            const int k = k0 + kk;
-            if (k <= j) {
-                const double2 *uk = basis(a, k, rr);
-#pragma unroll
-                for (int e = 0; e < ELEM; ++e) {
-                    const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
-                    if (idx < a.N) acc[kk] = cfmac(uk[idx], wv[e], acc[kk]);
-                }
-            } else if (PASS == 1 && k == j + 1) {
-#pragma unroll
-                for (int e = 0; e < ELEM; ++e) acc[kk].x += cabs2(wv[e]);
-            }
-        }
-        block_sum8(acc, red);
-        if (threadIdx.x < 8 && k0 + (int)threadIdx.x < K)
-            part[(int64_t)blockIdx.x * a.pstride + k0 + threadIdx.x] = red[threadIdx.x];
-        __syncthreads();
-    }
+    for (int k0 = 0; k0 < K; k0 += 8) dots_group<ELEM>(a, rr, j, k0, PASS == 1, wv, base, part, red);
     if (!last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk)) return;
     reduce_partials(part, a.nchunk, a.pstride, K, tot);
     double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
-    for (int k = threadIdx.x; k <= j; k += blockDim.x) h[k] = cscale(tot[k], 1.0 / beta[k]);
-    if (PASS == 1 && threadIdx.x == 0) a.nrm[rr * NM_STRIDE + NM_W0] = sqrt(tot[j + 1].x);
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) {
+        const double2 hk = cscale(tot[k], 1.0 / beta[k]);
+        h[k] = hk;
+        tot[k] = hk;
+    }
+    __syncthreads();
+    if (PASS == 2 || threadIdx.x != 0) return;
+    const double w2 = tot[j + 1].x;
+    double hsq = 0;
+    for (int k = 0; k <= j; ++k) hsq += cabs2(tot[k]);
+    const double wn2 = w2 - hsq;
+    if (!(wn2 > kReorthEta * kReorthEta * w2)) {  // strong cancellation (or NaN): second pass
+        st[ST_REORTH] = 1;
+        return;
+    }
+    st[ST_REORTH] = 0;
+    finalize_column(a, rr, j, h, sqrt(wn2));
 }
 
-// u_{j+1} <- u_{j+1} - sum_k (h_k / beta_k) u_k, its FP32 copy, ||u_{j+1}||.
-// PASS 1 decides whether a second pass is needed; otherwise (and after PASS 2)
-// the Hessenberg column is finalised.
+// u_{j+1} <- u_{j+1} - sum_k (h_k / beta_k) u_k and its copy for the next
+// product.  PASS 1 needs no reduction; PASS 2 (after a second Gram-Schmidt
+// pass) also forms ||u_{j+1}|| and finalises the Hessenberg column.
 template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(GArgs a) {
     __shared__ double red[8];
     __shared__ double2 cf[129];
@@ -377,7 +440,23 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(GArgs
         const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
         wv[e] = idx < a.N ? un[idx] : make_double2(0, 0);
     }
-    for (int k = 0; k <= j; ++k) {
+    int k = 0;
+    const int64_t vstride = (int64_t)a.cap * a.N;
+    for (; k + 4 <= j + 1; k += 4) {  // 4 basis vectors per step, loads first
+        const double2 *u0 = basis(a, k, rr);
+#pragma unroll
+        for (int e = 0; e < ELEM; ++e) {
+            const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
+            if (idx < a.N) {
+                double2 uv[4];
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) uv[kk] = u0[kk * vstride + idx];
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) wv[e] = wv[e] - cmul(cf[k + kk], uv[kk]);
+            }
+        }
+    }
+    for (; k <= j; ++k) {
         const double2 c = cf[k];
         const double2 *uk = basis(a, k, rr);
 #pragma unroll
@@ -399,6 +478,7 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(GArgs
             acc += cabs2(wv[e]);
         }
     }
+    if (PASS == 1) return;
     acc = block_sum1(acc, red);
     double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
     if (threadIdx.x == 0) part[(int64_t)blockIdx.x * a.pstride] = make_double2(acc, 0);
@@ -407,22 +487,14 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(GArgs
     if (threadIdx.x != 0) return;
     const double wn = sqrt(tot[0].x);
     const double2 *h1 = a.h1 + (int64_t)rr * (a.m + 1);
-    if (PASS == 1) {
-        if (wn < kReorthEta * a.nrm[rr * NM_STRIDE + NM_W0]) {
-            st[ST_REORTH] = 1;
-            return;
-        }
-        finalize_column(a, rr, j, h1, wn);
-    } else {
-        double2 *h2 = a.h2 + (int64_t)rr * (a.m + 1);
-        for (int k = 0; k <= j; ++k) h2[k] = h1[k] + h2[k];  // total coefficients
-        st[ST_REORTH] = 0;
-        finalize_column(a, rr, j, h2, wn);
-    }
+    double2 *h2 = a.h2 + (int64_t)rr * (a.m + 1);
+    for (int kk = 0; kk <= j; ++kk) h2[kk] = h1[kk] + h2[kk];  // total coefficients
+    st[ST_REORTH] = 0;
+    finalize_column(a, rr, j, h2, wn);
 }
 
-// x <- x + sum_k (y_k / beta_k) u_k for RHS whose cycle produced an update.
-template <int ELEM> __global__ void __launch_bounds__(256) k_update_x(GArgs a) {
+// d <- d + sum_k (y_k / beta_k) u_k for RHS whose cycle produced an update.
+template <int ELEM> __global__ void __launch_bounds__(256) k_update_d(GArgs a) {
     __shared__ double2 ys[128];
     const int rr = blockIdx.y;
     const int *st = a.st + rr * ST_STRIDE;
@@ -437,11 +509,73 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_update_x(GArgs a) {
     for (int e = 0; e < ELEM; ++e) {
         const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
         if (idx < a.N) {
-            double2 s = a.x[(int64_t)rr * a.N + idx];
+            const int64_t o = (int64_t)rr * a.N + idx;
+            double2 s = a.dbuf[o];
             for (int k = 0; k < jl; ++k) s = cfma(ys[k], basis(a, k, rr)[idx], s);
-            a.x[(int64_t)rr * a.N + idx] = s;
+            a.dbuf[o] = s;
+            if (a.mixed) a.x32[o] = make_float2((float)s.x, (float)s.y);  // input of the restart product
         }
     }
+}
+
+// x <- x + d at the end of a sweep.
+template <int ELEM> __global__ void __launch_bounds__(256) k_apply_d(GArgs a) {
+    const int rr = blockIdx.y;
+    if (!a.st[rr * ST_STRIDE + ST_INNER]) return;
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x * ELEM;
+#pragma unroll
+    for (int e = 0; e < ELEM; ++e) {
+        const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
+        if (idx < a.N) {
+            const int64_t o = (int64_t)rr * a.N + idx;
+            a.x[o] = a.x[o] + a.dbuf[o];
+        }
+    }
+}
+
+// Inner restart (MIXED): r_in = r - Z32 d with the FP32 product of d in y32;
+// r_in becomes u_0 of a new cycle unless the inner target is met, the restart
+// gained less than 10%, or a cap is reached.
+template <int ELEM> __global__ void __launch_bounds__(256) k_inner_residual(GArgs a) {
+    __shared__ double red[8];
+    __shared__ double2 tot[1];
+    const int rr = blockIdx.y;
+    int *st = a.st + rr * ST_STRIDE;
+    if (!st[ST_INNER] || !st[ST_PENDING]) return;
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x * ELEM;
+    double2 *u0 = basis(a, 0, rr);
+    double acc = 0;
+#pragma unroll
+    for (int e = 0; e < ELEM; ++e) {
+        const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
+        if (idx < a.N) {
+            const int64_t o = (int64_t)rr * a.N + idx;
+            const float2 f = a.y32[o];
+            const double2 t = a.rbuf[o] - make_double2(f.x, f.y);
+            u0[idx] = t;
+            a.x32[o] = make_float2((float)t.x, (float)t.y);
+            acc += cabs2(t);
+        }
+    }
+    acc = block_sum1(acc, red);
+    double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * a.pstride] = make_double2(acc, 0);
+    if (!last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk)) return;
+    reduce_partials(part, a.nchunk, a.pstride, 1, tot);
+    if (threadIdx.x != 0) return;
+    double *nm = a.nrm + rr * NM_STRIDE;
+    const double rin = sqrt(tot[0].x), prev = nm[NM_RIN];
+    nm[NM_RIN] = rin;
+    st[ST_PENDING] = 0;
+    const bool more = (rin > nm[NM_TARGET]) && (rin < kStagnation * prev) && st[ST_ITERS] < a.ctl->max_iter &&
+                      st[ST_RESTARTS] < kMaxRestarts;  // false for NaN
+    if (!more) return;
+    st[ST_RESTARTS] += 1;
+    st[ST_ACTIVE] = 1;
+    a.beta[(int64_t)rr * (a.m + 1)] = rin;
+    double2 *g = a.g + (int64_t)rr * (a.m + 1);
+    g[0] = make_double2(rin, 0);
+    for (int i = 1; i <= a.m; ++i) g[i] = make_double2(0, 0);
 }
 
 // ---------------------------------------------------------------- loop control
@@ -453,7 +587,7 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 
 // Start of a solve: counters, deadline, x = 0 for a zero guess, and whether the
 // first true residual needs a product (it does not when x = 0).
-__global__ void k_solve_begin(GArgs a, cudaGraphConditionalHandle h_first_product) {
+__global__ void k_solve_begin(GArgs a, cudaGraphConditionalHandle h_first_product, int use_graph) {
     SolveCtl *c = a.ctl;
     const int64_t total = (int64_t)a.nrhs * a.N;
     if (c->zero)
@@ -464,9 +598,11 @@ __global__ void k_solve_begin(GArgs a, cudaGraphConditionalHandle h_first_produc
         c->sweeps = 0;
         c->timed_out = 0;
         c->outer_bodies = 0;
+        c->restart_bodies = 0;
         c->inner_bodies = 0;
         c->deadline = c->timeout_ns > 0 ? globaltimer_ns() + (unsigned long long)c->timeout_ns : 0ull;
-        cudaGraphSetConditional(h_first_product, c->zero ? 0u : 1u);
+        c->cond_first = c->zero ? 0 : 1;
+        if (use_graph) cudaGraphSetConditional(h_first_product, c->zero ? 0u : 1u);
     }
 }
 
@@ -482,25 +618,47 @@ __device__ __forceinline__ bool past_deadline(const SolveCtl *c) {
 
 // After a true residual: another sweep while some RHS is active, within the
 // sweep cap and the deadline.
-__global__ void k_sweep_ctl(GArgs a, cudaGraphConditionalHandle h_sweep) {
+__global__ void k_sweep_ctl(GArgs a, cudaGraphConditionalHandle h_sweep, int use_graph) {
     const bool any = any_active(a);
     if (threadIdx.x != 0) return;
     SolveCtl *c = a.ctl;
     c->sweeps += 1;
     const bool late = past_deadline(c);
     if (any && late) c->timed_out = 1;
-    cudaGraphSetConditional(h_sweep, (any && c->sweeps < c->max_outer && !late) ? 1u : 0u);
+    const unsigned cond = (any && c->sweeps < c->max_outer && !late) ? 1u : 0u;
+    c->cond_sweep = (int)cond;
+    if (use_graph) cudaGraphSetConditional(h_sweep, cond);
 }
 
-__global__ void k_cycle_begin(GArgs a, cudaGraphConditionalHandle h_iter) {
+__global__ void k_restart_begin(GArgs a, cudaGraphConditionalHandle h_restart, int use_graph) {
+    if (threadIdx.x != 0) return;
+    a.ctl->outer_bodies += 1;
+    a.ctl->cond_restart = 1;
+    if (use_graph) cudaGraphSetConditional(h_restart, 1u);
+}
+
+// After a restart: another cycle while some RHS started one (MIXED only).
+__global__ void k_restart_ctl(GArgs a, cudaGraphConditionalHandle h_restart, int use_graph) {
+    const bool any = a.mixed && any_active(a);
+    if (threadIdx.x != 0) return;
+    SolveCtl *c = a.ctl;
+    const bool late = past_deadline(c);
+    if (any && late) c->timed_out = 1;
+    const unsigned cond = (any && !late) ? 1u : 0u;
+    c->cond_restart = (int)cond;
+    if (use_graph) cudaGraphSetConditional(h_restart, cond);
+}
+
+__global__ void k_cycle_begin(GArgs a, cudaGraphConditionalHandle h_iter, int use_graph) {
     if (threadIdx.x != 0) return;
     a.ctl->j = 0;
-    a.ctl->outer_bodies += 1;
-    cudaGraphSetConditional(h_iter, 1u);
+    a.ctl->restart_bodies += 1;
+    a.ctl->cond_iter = 1;
+    if (use_graph) cudaGraphSetConditional(h_iter, 1u);
 }
 
 // After an Arnoldi step: next iteration while some RHS is still in its cycle.
-__global__ void k_iter_ctl(GArgs a, cudaGraphConditionalHandle h_iter) {
+__global__ void k_iter_ctl(GArgs a, cudaGraphConditionalHandle h_iter, int use_graph) {
     const bool any = any_active(a);
     if (threadIdx.x != 0) return;
     SolveCtl *c = a.ctl;
@@ -508,7 +666,9 @@ __global__ void k_iter_ctl(GArgs a, cudaGraphConditionalHandle h_iter) {
     c->inner_bodies += 1;
     const bool late = past_deadline(c);
     if (any && late) c->timed_out = 1;
-    cudaGraphSetConditional(h_iter, (any && c->j < a.m && !late) ? 1u : 0u);
+    const unsigned cond = (any && c->j < a.m && !late) ? 1u : 0u;
+    c->cond_iter = (int)cond;
+    if (use_graph) cudaGraphSetConditional(h_iter, cond);
 }
 
 // ---------------------------------------------------------------- workspace
@@ -524,7 +684,7 @@ void free_solve_graphs(ztoep_plan_t p) {
 void free_solve_ws(ztoep_plan_t p) {
     free_solve_graphs(p);
     SolveWs &w = p->sws;
-    cudaFree(w.Vb); cudaFree(w.w); cudaFree(w.xin64); cudaFree(w.vbuf); cudaFree(w.xbuf); cudaFree(w.H);
+    cudaFree(w.Vb); cudaFree(w.w); cudaFree(w.xin64); cudaFree(w.vbuf); cudaFree(w.xbuf); cudaFree(w.rbuf); cudaFree(w.dbuf); cudaFree(w.H);
     cudaFree(w.cs); cudaFree(w.sn); cudaFree(w.g); cudaFree(w.y); cudaFree(w.h1); cudaFree(w.h2);
     cudaFree(w.part); cudaFree(w.nrm); cudaFree(w.st); cudaFree(w.cnt); cudaFree(w.ctl);
     if (w.hst) cudaFreeHost(w.hst);
@@ -533,7 +693,7 @@ void free_solve_ws(ztoep_plan_t p) {
 }
 
 // Launch geometry: depends on N only, so a RHS is summed in the same order
-// alone and in any batch.  Small systems: 128 threads x 2 elements (enough
+// alone and in any batch.  Small systems: 128 threads x 1 element (enough
 // CTAs to cover every SM); large ones: 256 threads x 4 elements.
 struct Geom {
     int threads, elem;
@@ -541,7 +701,7 @@ struct Geom {
 static Geom geom_for(int64_t N, int nsm) {
     const int64_t ctas_small = (N + 255) / 256;
     if (ctas_small >= 8LL * nsm) return {256, 4};
-    return {128, 2};
+    return {128, 1};
 }
 
 constexpr int kHostCtlInts = 32;  // host mirror of SolveCtl after st
@@ -551,7 +711,8 @@ static ztoep_status_t ensure_solve_ws(ztoep_plan_t p, int nrhs, int m) {
     if (w.cap >= nrhs && w.m >= m) return ZTOEP_OK;
     free_solve_ws(p);
     const int64_t N = p->N;
-    const int nchunk = (int)((N + 255) / 256);  // upper bound over the geometries
+    const Geom gm = geom_for(N, p->nsm);
+    const int nchunk = (int)((N + gm.threads * gm.elem - 1) / (gm.threads * gm.elem));
     const int pstride = m + 2;
     const size_t vec = sizeof(double2) * (size_t)nrhs * N;
     size_t acc = 0;
@@ -560,6 +721,8 @@ static ztoep_status_t ensure_solve_ws(ztoep_plan_t p, int nrhs, int m) {
     ZT_TRY(dalloc((void **)&w.xin64, vec, &acc));
     ZT_TRY(dalloc((void **)&w.vbuf, vec, &acc));
     ZT_TRY(dalloc((void **)&w.xbuf, vec, &acc));
+    ZT_TRY(dalloc((void **)&w.rbuf, vec, &acc));
+    ZT_TRY(dalloc((void **)&w.dbuf, vec, &acc));
     ZT_TRY(dalloc((void **)&w.H, sizeof(double2) * (size_t)nrhs * (m + 1) * m, &acc));
     ZT_TRY(dalloc((void **)&w.cs, sizeof(double2) * (size_t)nrhs * m, &acc));
     ZT_TRY(dalloc((void **)&w.sn, sizeof(double2) * (size_t)nrhs * m, &acc));
@@ -584,7 +747,7 @@ static ztoep_status_t ensure_solve_ws(ztoep_plan_t p, int nrhs, int m) {
 static GArgs make_args(ztoep_plan_t p, int nrhs, int m, bool mixed, int nchunk) {
     SolveWs &w = p->sws;
     GArgs a{};
-    a.Vb = w.Vb; a.w = w.w; a.x = w.xbuf; a.v = w.vbuf; a.xin64 = w.xin64;
+    a.Vb = w.Vb; a.w = w.w; a.x = w.xbuf; a.v = w.vbuf; a.xin64 = w.xin64; a.rbuf = w.rbuf; a.dbuf = w.dbuf;
     a.x32 = (float2 *)p->ws32.xin; a.y32 = (const float2 *)p->ws32.yout;
     a.H = w.H; a.cs = w.cs; a.sn = w.sn; a.g = w.g; a.y = w.y; a.h1 = w.h1; a.h2 = w.h2; a.part = w.part;
     a.nrm = w.nrm; a.beta = w.nrm + (size_t)w.cap * NM_STRIDE; a.st = w.st; a.cnt = w.cnt;
@@ -614,9 +777,19 @@ template <int ELEM> struct Launch {
         k_upd<ELEM, 2><<<g, t, 0, s>>>(a);
         return ok();
     }
-    static ztoep_status_t update_x(const GArgs &a, dim3 g, int t, cudaStream_t s) {
+    static ztoep_status_t update_d(const GArgs &a, dim3 g, int t, cudaStream_t s) {
         KScope ks(K_MISC, s);
-        k_update_x<ELEM><<<g, t, 0, s>>>(a);
+        k_update_d<ELEM><<<g, t, 0, s>>>(a);
+        return ok();
+    }
+    static ztoep_status_t apply_d(const GArgs &a, dim3 g, int t, cudaStream_t s) {
+        KScope ks(K_MISC, s);
+        k_apply_d<ELEM><<<g, t, 0, s>>>(a);
+        return ok();
+    }
+    static ztoep_status_t inner_residual(const GArgs &a, dim3 g, int t, cudaStream_t s) {
+        KScope ks(K_MISC, s);
+        k_inner_residual<ELEM><<<g, t, 0, s>>>(a);
         return ok();
     }
     static ztoep_status_t ok() {
@@ -629,25 +802,33 @@ struct Ops {
     Geom gm;
     dim3 grid;
     ztoep_status_t vnorm(const GArgs &a, cudaStream_t s) const {
-        return gm.elem == 4 ? Launch<4>::vnorm(a, grid, gm.threads, s) : Launch<2>::vnorm(a, grid, gm.threads, s);
+        return gm.elem == 4 ? Launch<4>::vnorm(a, grid, gm.threads, s) : Launch<1>::vnorm(a, grid, gm.threads, s);
     }
     ztoep_status_t residual(const GArgs &a, int first, cudaStream_t s) const {
         return gm.elem == 4 ? Launch<4>::residual(a, grid, gm.threads, first, s)
-                            : Launch<2>::residual(a, grid, gm.threads, first, s);
+                            : Launch<1>::residual(a, grid, gm.threads, first, s);
     }
     ztoep_status_t arnoldi(const GArgs &a, cudaStream_t s) const {
-        return gm.elem == 4 ? Launch<4>::arnoldi(a, grid, gm.threads, s) : Launch<2>::arnoldi(a, grid, gm.threads, s);
+        return gm.elem == 4 ? Launch<4>::arnoldi(a, grid, gm.threads, s) : Launch<1>::arnoldi(a, grid, gm.threads, s);
     }
-    ztoep_status_t update_x(const GArgs &a, cudaStream_t s) const {
-        return gm.elem == 4 ? Launch<4>::update_x(a, grid, gm.threads, s)
-                            : Launch<2>::update_x(a, grid, gm.threads, s);
+    ztoep_status_t update_d(const GArgs &a, cudaStream_t s) const {
+        return gm.elem == 4 ? Launch<4>::update_d(a, grid, gm.threads, s)
+                            : Launch<1>::update_d(a, grid, gm.threads, s);
+    }
+    ztoep_status_t apply_d(const GArgs &a, cudaStream_t s) const {
+        return gm.elem == 4 ? Launch<4>::apply_d(a, grid, gm.threads, s)
+                            : Launch<1>::apply_d(a, grid, gm.threads, s);
+    }
+    ztoep_status_t inner_residual(const GArgs &a, cudaStream_t s) const {
+        return gm.elem == 4 ? Launch<4>::inner_residual(a, grid, gm.threads, s)
+                            : Launch<1>::inner_residual(a, grid, gm.threads, s);
     }
 };
 
-static ztoep_status_t launch_small(void (*k)(GArgs, cudaGraphConditionalHandle), int blocks, const GArgs &a,
-                                   cudaGraphConditionalHandle h, cudaStream_t s) {
+static ztoep_status_t launch_small(void (*k)(GArgs, cudaGraphConditionalHandle, int), int blocks, const GArgs &a,
+                                   cudaGraphConditionalHandle h, cudaStream_t s, int use_graph = 1) {
     KScope ks(K_MISC, s);
-    k<<<blocks, 256, 0, s>>>(a, h);
+    k<<<blocks, 256, 0, s>>>(a, h, use_graph);
     ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
 }
@@ -687,8 +868,11 @@ static ztoep_status_t capture_end(cudaStream_t s) {
 
 // Whole solve as one graph:
 //   begin -> IF(x != 0){FP64 product} -> residual -> sweep control ->
-//   WHILE(sweep){ cycle begin -> WHILE(iter){product, Arnoldi, iteration control}
-//                 -> x update -> FP64 product -> residual -> sweep control }
+//   WHILE(sweep){ restart begin ->
+//                 WHILE(restart){ cycle begin -> WHILE(iter){product, Arnoldi, iteration control}
+//                                 -> d += V y -> [MIXED: FP32 product of d, r_in = r - Z d]
+//                                 -> restart control }
+//                 -> x += d -> FP64 product -> residual -> sweep control }
 static ztoep_status_t build_graph(ztoep_plan_t p, SolveGraph &sg, int prec, int nrhs, int m) {
     const bool mixed = prec == ZTOEP_MIXED;
     SolveWs &w = p->sws;
@@ -724,15 +908,30 @@ static ztoep_status_t build_graph(ztoep_plan_t p, SolveGraph &sg, int prec, int 
     ZT_TRY(run_matvec<double>(p, nrhs, w.xbuf, w.w, s));
     ZT_TRY(capture_end(s));
 
-    // one sweep
-    ZT_CUDA(cudaGraphConditionalHandleCreate(&h_iter, body_sweep, 0, 0));
+    // one sweep: inner restarts, x += d, FP64 residual
+    cudaGraphConditionalHandle h_restart;
+    cudaGraph_t body_restart = nullptr;
+    ZT_CUDA(cudaGraphConditionalHandleCreate(&h_restart, body_sweep, 0, 0));
     ZT_TRY(capture_begin(s, body_sweep, &sg.k_sweep));
-    ZT_TRY(launch_small(k_cycle_begin, 1, a, h_iter, s));
-    ZT_TRY(add_conditional(s, h_iter, cudaGraphCondTypeWhile, &body_iter));
-    ZT_TRY(ops.update_x(a, s));
+    ZT_TRY(launch_small(k_restart_begin, 1, a, h_restart, s));
+    ZT_TRY(add_conditional(s, h_restart, cudaGraphCondTypeWhile, &body_restart));
+    ZT_TRY(ops.apply_d(a, s));
     ZT_TRY(run_matvec<double>(p, nrhs, w.xbuf, w.w, s));
     ZT_TRY(ops.residual(a, 0, s));
     ZT_TRY(launch_small(k_sweep_ctl, 1, a, h_sweep, s));
+    ZT_TRY(capture_end(s));
+
+    // one restart: GMRES cycle, d += V y, FP32 inner residual (MIXED)
+    ZT_CUDA(cudaGraphConditionalHandleCreate(&h_iter, body_restart, 0, 0));
+    ZT_TRY(capture_begin(s, body_restart, &sg.k_restart));
+    ZT_TRY(launch_small(k_cycle_begin, 1, a, h_iter, s));
+    ZT_TRY(add_conditional(s, h_iter, cudaGraphCondTypeWhile, &body_iter));
+    ZT_TRY(ops.update_d(a, s));
+    if (mixed) {
+        ZT_TRY(run_matvec<float>(p, nrhs, a.x32, (float2 *)p->ws32.yout, s));
+        ZT_TRY(ops.inner_residual(a, s));
+    }
+    ZT_TRY(launch_small(k_restart_ctl, 1, a, h_restart, s));
     ZT_TRY(capture_end(s));
 
     // one iteration
@@ -781,13 +980,74 @@ static ztoep_status_t get_graph(ztoep_plan_t p, int prec, int nrhs, int m, Solve
     return ZTOEP_OK;
 }
 
+// The same solve with the loops driven from the host: every kernel is a
+// separate launch (for profilers that cannot see inside conditional graphs).
+// The loop decisions are read back from the control block.
+static ztoep_status_t run_host_loop(ztoep_plan_t p, int prec, int nrhs, int m, cudaStream_t s) {
+    const bool mixed = prec == ZTOEP_MIXED;
+    SolveWs &w = p->sws;
+    const Geom gm = geom_for(p->N, p->nsm);
+    const int per_cta = gm.threads * gm.elem;
+    const int nchunk = (int)((p->N + per_cta - 1) / per_cta);
+    const GArgs a = make_args(p, nrhs, m, mixed, nchunk);
+    const Ops ops{gm, dim3(nchunk, nrhs)};
+    SolveCtl *hc = reinterpret_cast<SolveCtl *>(w.hst + (size_t)w.cap * ST_STRIDE);
+    auto read_ctl = [&]() -> ztoep_status_t {
+        ZT_CUDA(cudaMemcpyAsync(hc, w.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
+        ZT_CUDA(cudaStreamSynchronize(s));
+        return ZTOEP_OK;
+    };
+    const cudaGraphConditionalHandle none = 0;
+    ZT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(int) * (size_t)w.cap * ST_STRIDE, s));
+    ZT_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(unsigned) * (size_t)w.cap * CNT_STRIDE, s));
+    const int zblocks = (int)std::min<int64_t>(4 * p->nsm, ((int64_t)nrhs * p->N + 255) / 256);
+    ZT_TRY(launch_small(k_solve_begin, std::max(1, zblocks), a, none, s, 0));
+    ZT_TRY(ops.vnorm(a, s));
+    ZT_TRY(read_ctl());
+    if (hc->cond_first) ZT_TRY(run_matvec<double>(p, nrhs, w.xbuf, w.w, s));
+    ZT_TRY(ops.residual(a, 1, s));
+    ZT_TRY(launch_small(k_sweep_ctl, 1, a, none, s, 0));
+    ZT_TRY(read_ctl());
+    while (hc->cond_sweep) {
+        ZT_TRY(launch_small(k_restart_begin, 1, a, none, s, 0));
+        for (;;) {
+            ZT_TRY(launch_small(k_cycle_begin, 1, a, none, s, 0));
+            for (int it = 0; it < m; ++it) {
+                if (mixed)
+                    ZT_TRY(run_matvec<float>(p, nrhs, a.x32, (float2 *)p->ws32.yout, s));
+                else
+                    ZT_TRY(run_matvec<double>(p, nrhs, w.xin64, w.w, s));
+                ZT_TRY(ops.arnoldi(a, s));
+                ZT_TRY(launch_small(k_iter_ctl, 1, a, none, s, 0));
+                ZT_TRY(read_ctl());
+                if (!hc->cond_iter) break;
+            }
+            ZT_TRY(ops.update_d(a, s));
+            if (mixed) {
+                ZT_TRY(run_matvec<float>(p, nrhs, a.x32, (float2 *)p->ws32.yout, s));
+                ZT_TRY(ops.inner_residual(a, s));
+            }
+            ZT_TRY(launch_small(k_restart_ctl, 1, a, none, s, 0));
+            ZT_TRY(read_ctl());
+            if (!hc->cond_restart) break;
+        }
+        ZT_TRY(ops.apply_d(a, s));
+        ZT_TRY(run_matvec<double>(p, nrhs, w.xbuf, w.w, s));
+        ZT_TRY(ops.residual(a, 0, s));
+        ZT_TRY(launch_small(k_sweep_ctl, 1, a, none, s, 0));
+        ZT_TRY(read_ctl());
+    }
+    return ZTOEP_OK;
+}
+
 // Prepare buffers and the graph; V/X must already be in vbuf/xbuf (X only when
 // no zero guess).  Runs the solve graph on `s` and fetches the per-RHS state.
 static ztoep_status_t solve_core(ztoep_plan_t p, const ztoep_solve_opts_t *o, int nrhs, ztoep_solve_info_t *info,
                                  cudaStream_t s) {
     const int m = o->restart;
+    const bool host_loop = (o->flags & ZTOEP_FLAG_HOST_LOOP) != 0;
     SolveGraph *g = nullptr;
-    ZT_TRY(get_graph(p, o->prec, nrhs, m, &g));
+    if (!host_loop) ZT_TRY(get_graph(p, o->prec, nrhs, m, &g));
     SolveWs &w = p->sws;
     SolveCtl *hc = reinterpret_cast<SolveCtl *>(w.hst + (size_t)w.cap * ST_STRIDE);
     std::memset(hc, 0, sizeof(SolveCtl));
@@ -798,15 +1058,19 @@ static ztoep_status_t solve_core(ztoep_plan_t p, const ztoep_solve_opts_t *o, in
     hc->inner_tol = o->inner_tol;
     hc->timeout_ns = o->timeout_ns;
     ZT_CUDA(cudaMemcpyAsync(w.ctl, hc, sizeof(SolveCtl), cudaMemcpyHostToDevice, s));
-    ZT_CUDA(cudaGraphLaunch(g->exec, s));
+    if (host_loop)
+        ZT_TRY(run_host_loop(p, o->prec, nrhs, m, s));
+    else
+        ZT_CUDA(cudaGraphLaunch(g->exec, s));
     ZT_CUDA(cudaMemcpyAsync(w.hst, w.st, sizeof(int) * (size_t)nrhs * ST_STRIDE, cudaMemcpyDeviceToHost, s));
     ZT_CUDA(cudaMemcpyAsync(hc, w.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
     ZT_CUDA(cudaMemcpyAsync(w.hnrm, w.nrm, sizeof(double) * (size_t)nrhs * NM_STRIDE, cudaMemcpyDeviceToHost, s));
     int dev_err = 0;
     ZT_CUDA(cudaMemcpyAsync(&dev_err, p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     ZT_CUDA(cudaStreamSynchronize(s));
-    add_launches(g->k_fixed + (hc->zero ? 0 : g->k_first_product) + (uint64_t)hc->outer_bodies * g->k_sweep +
-                 (uint64_t)hc->inner_bodies * g->k_iter);
+    if (g)
+        add_launches(g->k_fixed + (hc->zero ? 0 : g->k_first_product) + (uint64_t)hc->outer_bodies * g->k_sweep +
+                     (uint64_t)hc->restart_bodies * g->k_restart + (uint64_t)hc->inner_bodies * g->k_iter);
     bool timed_out = hc->timed_out != 0;
     if (dev_err != 0) {  // a bounded device-side wait gave up
         ZT_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), s));

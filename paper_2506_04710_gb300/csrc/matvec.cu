@@ -288,6 +288,31 @@ __device__ __forceinline__ cplx_t<R> warp_sum(cplx_t<R> v) {
     return v;
 }
 
+template <typename R>
+__device__ __forceinline__ cplx_t<R> shfl_xor_c(cplx_t<R> v, int o) {
+    v.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+    return v;
+}
+
+// Warp reduce-scatter of 4 values: the result in lane l is the warp total of
+// value ((l >> 4) & 1) * 2 + ((l >> 3) & 1).
+template <typename R>
+__device__ __forceinline__ cplx_t<R> warp_rs4(cplx_t<R> (&v)[4]) {
+    const int lane = threadIdx.x & 31;
+    const bool b4 = lane & 16, b3 = lane & 8;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const cplx_t<R> recv = shfl_xor_c<R>(b4 ? v[i] : v[i + 2], 16);
+        v[i] = (b4 ? v[i + 2] : v[i]) + recv;
+    }
+    cplx_t<R> t = (b3 ? v[1] : v[0]) + shfl_xor_c<R>(b3 ? v[0] : v[1], 8);
+    t = t + shfl_xor_c<R>(t, 4);
+    t = t + shfl_xor_c<R>(t, 2);
+    t = t + shfl_xor_c<R>(t, 1);
+    return t;
+}
+
 template <typename R, int RC>
 __global__ void __launch_bounds__(256) k_edge(const cplx_t<R> *__restrict__ x, const cplx_t<R> *__restrict__ B,
                                               cplx_t<R> *__restrict__ ET, cplx_t<R> *__restrict__ Ep,
@@ -341,10 +366,10 @@ __global__ void __launch_bounds__(256) k_edge(const cplx_t<R> *__restrict__ x, c
                                     ? __ldcs(reinterpret_cast<const float4 *>(brow + (int64_t)(u * 32 + lane) * CPL))
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+            C part[UNR][RC];
 #pragma unroll
             for (int k = 0; k < UNR; ++k) {
                 const int el = el0 + k;
-                if (el >= ne) break;  // uniform across the CTA
                 C bv[U][CPL];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
@@ -354,18 +379,28 @@ __global__ void __launch_bounds__(256) k_edge(const cplx_t<R> *__restrict__ x, c
                 }
 #pragma unroll
                 for (int q = 0; q < RC; ++q) {
-                    const C xe = sxe[el][q];
-                    C part = czero<C>();
+                    const C xe = el < ne ? sxe[el][q] : czero<C>();  // padded rows hold zeros
+                    C pt = czero<C>();
 #pragma unroll
                     for (int u = 0; u < U; ++u)
 #pragma unroll
                         for (int c = 0; c < CPL; ++c) {
-                            acc[u][c][q] = cfma(bv[u][c], xe, acc[u][c][q]);
-                            part = cfma(bv[u][c], xt[u][c][q], part);
+                            if (el < ne) acc[u][c][q] = cfma(bv[u][c], xe, acc[u][c][q]);
+                            pt = cfma(bv[u][c], xt[u][c][q], pt);
                         }
-                    part = warp_sum<R>(part);
-                    if (lane == 0) red[warp][el][q] = part;
+                    part[k][q] = pt;
                 }
+            }
+            // reduce the 4 row partials across the warp at once: lane 8*k ends
+            // with the total of row k (6 exchanges instead of 4 x 5)
+#pragma unroll
+            for (int q = 0; q < RC; ++q) {
+                C v4[UNR];
+#pragma unroll
+                for (int k = 0; k < UNR; ++k) v4[k] = part[k][q];
+                const C tot = warp_rs4<R>(v4);
+                const int k = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
+                if ((lane & 7) == 0 && el0 + k < ne) red[warp][el0 + k][q] = tot;
             }
         }
         __syncthreads();
@@ -390,6 +425,17 @@ __global__ void __launch_bounds__(256) k_edge(const cplx_t<R> *__restrict__ x, c
                     if (q < rc) ET[((int64_t)split * nrhs + r0 + q) * NT + t] = acc[u][c][q];
             }
         }
+}
+
+// ET[0][r][t] += sum_{s >= 1} ET[s][r][t]: the B^T x_E rows in one buffer, so the
+// inverse x pass reads a single value per output.
+template <typename R>
+__global__ void __launch_bounds__(256) k_fold_splits(cplx_t<R> *__restrict__ ET, int64_t count, int nsplit) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
+        cplx_t<R> s = ET[k];
+        for (int sp = 1; sp < nsplit; ++sp) s = s + ET[(int64_t)sp * count + k];
+        ET[k] = s;
+    }
 }
 
 // y_E[r][e] = sum_tile Ep[tile][r][e] + sum_e' C[e][e'] x_E[r][e'].  One warp per (e, r).
@@ -510,18 +556,18 @@ static ztoep_status_t forward_passes(ztoep_plan_t p, int nrhs, const cplx_t<R> *
                                      cplx_t<R> *Xh, cudaStream_t s) {
     const size_t cs = sizeof(cplx_t<R>);
     const uint8_t *act = p->masked ? p->active : nullptr;
-    const int libx = pick_lib(p->lx, p->b, cs, 64 * 1024);
-    const int ibx = 1 << libx;
+    const PassCfg cx = pass_cfg(p->lx, p->b, p->ny * nrhs, cs, p->nsm);
+    const int ibx = 1 << cx.lib;
     dim3 gx((p->b + ibx - 1) / ibx, p->ny, nrhs);
-    ZT_TRY((launch_fft_pass<R>(p->fx, twx_of<R>(p), libx, false, gx,
+    ZT_TRY((launch_fft_pass<R>(p->fx, twx_of<R>(p), cx.lib, false, gx,
                                LdXFwd<R>{x, act, p->nx, p->b, ibx, p->N},
-                               StX1<R>{X1, p->ny, p->lx, p->b, ibx}, s)));
-    const int liby = pick_lib(p->ly, p->b, cs, 64 * 1024);
-    const int iby = 1 << liby;
+                               StX1<R>{X1, p->ny, p->lx, p->b, ibx}, s, cx.threads)));
+    const PassCfg cy = pass_cfg(p->ly, p->b, p->lx * nrhs, cs, p->nsm);
+    const int iby = 1 << cy.lib;
     dim3 gy((p->b + iby - 1) / iby, p->lx, nrhs);
-    ZT_TRY((launch_fft_pass<R>(p->fy, twy_of<R>(p), liby, false, gy,
+    ZT_TRY((launch_fft_pass<R>(p->fy, twy_of<R>(p), cy.lib, false, gy,
                                LdX1<R>{X1, p->ny, p->lx, p->b, iby},
-                               StXh<R>{Xh, p->lx, p->b, iby, nrhs}, s)));
+                               StXh<R>{Xh, p->lx, p->b, iby, nrhs}, s, cy.threads)));
     return ZTOEP_OK;
 }
 
@@ -570,7 +616,7 @@ static ztoep_status_t launch_blockprod(ztoep_plan_t p, int nrhs, cplx_t<R> *Xh, 
 
 template <typename R>
 static ztoep_status_t launch_edge(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *y,
-                                  MatvecWs &w, cudaStream_t s) {
+                                  MatvecWs &w, cudaStream_t s, bool fold = false) {
     const size_t cs = sizeof(cplx_t<R>);
     const int ntile = edge_ntile(p, cs);
     const int nsplit = edge_nsplit(p, ntile, cs);
@@ -592,7 +638,12 @@ static ztoep_status_t launch_edge(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, 
     }
     dim3 gf((p->E + 7) / 8, nrhs);
     KScope ks(K_MISC, s);
+    ks.add(fold && nsplit > 1 ? 2 : 1);
     k_edge_finish<R><<<gf, 256, 0, s>>>(x, c_of<R>(p), Ep, y, p->NT, p->E, p->N, nrhs, ntile);
+    if (fold && nsplit > 1) {
+        const int64_t count = (int64_t)nrhs * p->NT;
+        k_fold_splits<R><<<grid_for(count, 256), 256, 0, s>>>(ET, count, nsplit);
+    }
     ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
 }
@@ -609,27 +660,27 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
     if (p->E > 0) {  // edge branch on the side stream, concurrent with the FFT chain
         ZT_CUDA(cudaEventRecord(p->ev_fork, s));
         ZT_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
-        ZT_TRY(launch_edge<R>(p, nrhs, x, y, w, p->side));
+        ZT_TRY(launch_edge<R>(p, nrhs, x, y, w, p->side, true));
         ZT_CUDA(cudaEventRecord(p->ev_join, p->side));
     }
     ZT_TRY(forward_passes<R>(p, nrhs, x, X1, Xh, s));
     ZT_TRY(launch_blockprod<R>(p, nrhs, Xh, s));
-    const int liby = pick_lib(p->ly, p->b, cs, 64 * 1024);
-    const int iby = 1 << liby;
+    const PassCfg cy = pass_cfg(p->ly, p->b, p->lx * nrhs, cs, p->nsm);
+    const int iby = 1 << cy.lib;
     dim3 gy((p->b + iby - 1) / iby, p->lx, nrhs);
-    ZT_TRY((launch_fft_pass<R>(p->fy, twy_of<R>(p), liby, true, gy,
+    ZT_TRY((launch_fft_pass<R>(p->fy, twy_of<R>(p), cy.lib, true, gy,
                                LdXh<R>{Xh, p->lx, p->b, iby, nrhs},
-                               StY1<R>{X1, p->ny, p->lx, p->b, iby}, s)));
+                               StY1<R>{X1, p->ny, p->lx, p->b, iby}, s, cy.threads)));
     if (p->E > 0) ZT_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
-    const int libx = pick_lib(p->lx, p->b, cs, 64 * 1024);
-    const int ibx = 1 << libx;
+    const PassCfg cx = pass_cfg(p->lx, p->b, p->ny * nrhs, cs, p->nsm);
+    const int ibx = 1 << cx.lib;
     dim3 gx((p->b + ibx - 1) / ibx, p->ny, nrhs);
     const R scale = (R)(1.0 / ((double)p->lx * (double)p->ly));
-    ZT_TRY((launch_fft_pass<R>(p->fx, twx_of<R>(p), libx, true, gx,
+    ZT_TRY((launch_fft_pass<R>(p->fx, twx_of<R>(p), cx.lib, true, gx,
                                LdY1<R>{X1, p->ny, p->lx, p->b, ibx},
                                StYOut<R>{y, x, reinterpret_cast<const cplx_t<R> *>(w.ET),
                                          p->masked ? p->active : nullptr, p->nx, p->b, ibx, nrhs,
-                                         nsplit, p->N, p->NT, scale}, s)));
+                                         nsplit > 0 ? 1 : 0, p->N, p->NT, scale}, s, cx.threads)));
     return ZTOEP_OK;
 }
 template ztoep_status_t run_matvec<float>(ztoep_plan_t, int, const float2 *, float2 *, cudaStream_t);

@@ -29,6 +29,7 @@ ZTOEP_ERR_NONFINITE = 7
 ZTOEP_FP64 = 0
 ZTOEP_MIXED = 1
 ZTOEP_FLAG_ZERO_GUESS = 1
+ZTOEP_FLAG_HOST_LOOP = 2
 
 
 class ZtoepError(RuntimeError):

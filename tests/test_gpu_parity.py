@@ -245,3 +245,28 @@ def test_initial_guess_is_used():
     X, info, st = plan.solve(dev(prob.V), X=X0.clone(), opts=o)
     assert st == 0 and info[0]["inner_iters"] == 0 and info[0]["outer"] == 1
     plan.close()
+
+
+def test_host_driven_loop_matches_graph_bitwise():
+    prob = make("7x6_b12_e20")
+    plan = ztoep.Plan.from_problem(prob)
+    V = dev(prob.V)
+    for prec in (ztoep.ZTOEP_MIXED, ztoep.ZTOEP_FP64):
+        Xg, ig, _ = plan.solve(V, opts=opts(prec, 1e-9))
+        o = opts(prec, 1e-9)
+        o.flags = ztoep.ZTOEP_FLAG_HOST_LOOP
+        Xh, ih, _ = plan.solve(V, opts=o)
+        assert torch.equal(Xg, Xh)
+        assert [i["inner_iters"] for i in ig] == [i["inner_iters"] for i in ih]
+
+
+def test_timeout_is_enforced_on_device():
+    prob = make("9x4_b40_e24")
+    plan = ztoep.Plan.from_problem(prob)
+    o = opts(ztoep.ZTOEP_FP64, 1e-14, max_iter=100000)
+    o.max_outer = 100000
+    o.timeout_ns = 1  # expires at the first check
+    X, info, st = plan.solve(dev(prob.V), opts=o, check=False)
+    assert st == ztoep.ZTOEP_ERR_TIMEOUT
+    assert all(i["status"] == ztoep.ZTOEP_ERR_TIMEOUT for i in info)
+    plan.close()
