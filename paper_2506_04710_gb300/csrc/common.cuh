@@ -96,6 +96,7 @@ struct MatvecWs {  // per-precision matvec workspace, sized for `cap` RHS
     void *Xh = nullptr;     // [F][cap][b] spectrum (block product runs in place)
     void *ET = nullptr;     // [nsplit][cap][NT] B^T x_E partial sums
     void *Ep = nullptr;     // [ntile][cap][E]   B x_T partial sums
+    void *Yh = nullptr;     // [F][cap][b] tensor-core block-product output (FP32, >= 16 RHS)
     size_t bytes = 0;
 };
 
@@ -153,6 +154,9 @@ struct ztoep_plan_s {
     float2 *B32 = nullptr;
     double2 *C64 = nullptr;         // [E][E]
     float2 *C32 = nullptr;
+    float2 *That32full = nullptr;   // [F][b][b] every frequency, for the tensor-core product
+    float2 *B32T = nullptr;         // [NT][E] transposed B, for the tensor-core B^T x_E
+    size_t tc_bytes = 0;
     uint8_t *active = nullptr;      // [ny*nx] device copy, nullptr if all active
     double2 *twx64 = nullptr, *twy64 = nullptr;  // exp(-2 pi i t / L)
     float2 *twx32 = nullptr, *twy32 = nullptr;
@@ -190,6 +194,11 @@ template <typename R>
 ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *y,
                           cudaStream_t s);
 template <typename R> ztoep_status_t ensure_ws(ztoep_plan_t p, int nrhs);
+// Tensor-core operands (full FP32 spectrum, transposed B) for FP32 products
+// with at least kTcMinRhs right-hand sides.
+constexpr int kTcMinRhs = 16;
+constexpr int kTcMaxRhs = 256;
+ztoep_status_t ensure_tensor_data(ztoep_plan_t p, int nrhs, cudaStream_t s);
 template <typename R> MatvecWs &ws_of(ztoep_plan_t p);
 template <typename R>
 ztoep_status_t run_forward_spectrum(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *Xh,

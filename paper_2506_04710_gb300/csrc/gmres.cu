@@ -1100,9 +1100,12 @@ static ztoep_status_t solve_core(ztoep_plan_t p, const ztoep_solve_opts_t *o, in
     return worst;
 }
 
-static ztoep_status_t prepare(ztoep_plan_t p, const ztoep_solve_opts_t *o, int nrhs) {
+static ztoep_status_t prepare(ztoep_plan_t p, const ztoep_solve_opts_t *o, int nrhs, cudaStream_t s) {
     ZT_TRY(ensure_solve_ws(p, nrhs, o->restart));
-    if (o->prec == ZTOEP_MIXED) ZT_TRY(ensure_ws<float>(p, nrhs));
+    if (o->prec == ZTOEP_MIXED) {
+        ZT_TRY(ensure_ws<float>(p, nrhs));
+        ZT_TRY(ensure_tensor_data(p, nrhs, s));
+    }
     ZT_TRY(ensure_ws<double>(p, nrhs));
     return ZTOEP_OK;
 }
@@ -1124,7 +1127,7 @@ ztoep_status_t ztoep_solve(ztoep_plan_t p, const ztoep_solve_opts_t *o, int32_t 
     if (!p || !valid_opts(o) || nrhs < 1 || !V || !X || V == X) return ZTOEP_ERR_ARG;
     std::lock_guard<std::mutex> lk(p->mu);
     cudaStream_t s = (cudaStream_t)stream;
-    ZT_TRY(prepare(p, o, nrhs));
+    ZT_TRY(prepare(p, o, nrhs, s));
     SolveWs &w = p->sws;
     const size_t bytes = sizeof(double2) * (size_t)nrhs * p->N;
     ZT_CUDA(cudaMemcpyAsync(w.vbuf, V, bytes, cudaMemcpyDeviceToDevice, s));
@@ -1141,7 +1144,7 @@ ztoep_status_t ztoep_solve_host(ztoep_plan_t p, const ztoep_solve_opts_t *o, int
     if (!p || !valid_opts(o) || nrhs < 1 || !Vh || !Xh) return ZTOEP_ERR_ARG;
     std::lock_guard<std::mutex> lk(p->mu);
     cudaStream_t s = (cudaStream_t)stream;
-    ZT_TRY(prepare(p, o, nrhs));
+    ZT_TRY(prepare(p, o, nrhs, s));
     SolveWs &w = p->sws;
     const size_t bytes = sizeof(double2) * (size_t)nrhs * p->N;
     ZT_CUDA(cudaMemcpyAsync(w.vbuf, Vh, bytes, cudaMemcpyHostToDevice, s));

@@ -16,6 +16,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "tma.cuh"
+#include "tcgemm.cuh"
 
 namespace ztoep {
 
@@ -504,8 +505,19 @@ static int edge_nsplit(ztoep_plan_t p, int ntile, size_t csize) {
     return std::max(1, std::min(want, maxs));
 }
 
+// K chunk of the tensor-core B x_T product: enough (row tile, K split) CTAs to
+// cover every SM twice, at least 256 complex k per CTA.
+static int tc_edge_kchunk(ztoep_plan_t p) {
+    const int mt = (p->E + 63) / 64;
+    const int want = std::max(1, (2 * p->nsm + mt - 1) / mt);
+    int kc = (int)((p->NT + want - 1) / want);
+    kc = std::max(256, (kc + 15) / 16 * 16);
+    return kc;
+}
+static int tc_edge_splits(ztoep_plan_t p) { return cgemm_splits((int)p->NT, tc_edge_kchunk(p)); }
+
 static void free_ws(MatvecWs &w) {
-    cudaFree(w.xin); cudaFree(w.yout); cudaFree(w.X1); cudaFree(w.Xh); cudaFree(w.ET); cudaFree(w.Ep);
+    cudaFree(w.xin); cudaFree(w.yout); cudaFree(w.X1); cudaFree(w.Xh); cudaFree(w.ET); cudaFree(w.Ep); cudaFree(w.Yh);
     w = MatvecWs{};
 }
 
@@ -522,10 +534,13 @@ template <typename R> ztoep_status_t ensure_ws(ztoep_plan_t p, int nrhs) {
     ZT_TRY(dalloc(&w.yout, cs * nrhs * p->N, &acc));
     ZT_TRY(dalloc(&w.X1, cs * nrhs * (size_t)p->ny * p->lx * p->b, &acc));
     ZT_TRY(dalloc(&w.Xh, cs * nrhs * (size_t)p->F * p->b, &acc));
+    const bool tc = cs == 8 && nrhs >= kTcMinRhs;
     if (p->E > 0) {
-        ZT_TRY(dalloc(&w.ET, cs * (size_t)nsplit * nrhs * p->NT, &acc));
-        ZT_TRY(dalloc(&w.Ep, cs * (size_t)ntile * nrhs * p->E, &acc));
+        ZT_TRY(dalloc(&w.ET, cs * (size_t)std::max(nsplit, 1) * nrhs * p->NT, &acc));
+        const int parts = std::max(ntile, tc ? tc_edge_splits(p) : 0);
+        ZT_TRY(dalloc(&w.Ep, cs * (size_t)parts * nrhs * p->E, &acc));
     }
+    if (tc) ZT_TRY(dalloc(&w.Yh, cs * nrhs * (size_t)p->F * p->b, &acc));
     w.cap = nrhs;
     w.bytes = acc;
     return ZTOEP_OK;
@@ -648,6 +663,49 @@ static ztoep_status_t launch_edge(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, 
     return ZTOEP_OK;
 }
 
+// Tensor-core edge coupling (FP32 products, kTcMinRhs..kTcMaxRhs RHS):
+//   B x_T    as C[e][q] = sum_t B[e][t] x_T[q][t]   -> K-split partials in Ep
+//   B^T x_E  as C[t][q] = sum_e B^T[t][e] x_E[q][e] -> ET[0]
+// then y_E = sum of the partials + C x_E.
+static ztoep_status_t tc_edge(ztoep_plan_t p, int nrhs, const float2 *x, float2 *y, MatvecWs &w, cudaStream_t s) {
+    const int kc = tc_edge_kchunk(p);
+    CgemmArgs g1{};
+    g1.A = p->B32; g1.lda = edge_ldb(p->NT); g1.strideA = 0;
+    g1.X = x; g1.ldx = p->N; g1.strideX = 0;
+    g1.C = reinterpret_cast<float2 *>(w.Ep); g1.ldc_q = p->E; g1.ldc_m = 1; g1.strideC = 0;
+    g1.strideCk = (int64_t)nrhs * p->E;
+    g1.M = p->E; g1.K = (int)p->NT; g1.N = nrhs; g1.kchunk = kc; g1.err = p->err;
+    ZT_TRY(launch_cgemm_tc(g1, 1, s));
+    CgemmArgs g2{};
+    g2.A = p->B32T; g2.lda = p->E; g2.strideA = 0;
+    g2.X = x + p->NT; g2.ldx = p->N; g2.strideX = 0;
+    g2.C = reinterpret_cast<float2 *>(w.ET); g2.ldc_q = p->NT; g2.ldc_m = 1; g2.strideC = 0; g2.strideCk = 0;
+    g2.M = (int)p->NT; g2.K = p->E; g2.N = nrhs; g2.kchunk = 0; g2.err = p->err;
+    ZT_TRY(launch_cgemm_tc(g2, 1, s));
+    dim3 gf((p->E + 7) / 8, nrhs);
+    KScope ks(K_MISC, s);
+    k_edge_finish<float><<<gf, 256, 0, s>>>(x, p->C32, reinterpret_cast<const float2 *>(w.Ep), y, p->NT, p->E,
+                                            p->N, nrhs, cgemm_splits((int)p->NT, kc));
+    ZT_CUDA(cudaGetLastError());
+    return ZTOEP_OK;
+}
+
+// Tensor-core block product: Yh[f] = T^[f] Xh[f] for every frequency (full
+// FP32 spectrum, separate output buffer).
+static ztoep_status_t tc_blockprod(ztoep_plan_t p, int nrhs, const float2 *Xh, float2 *Yh, cudaStream_t s) {
+    CgemmArgs g{};
+    g.A = p->That32full; g.lda = p->b; g.strideA = (int64_t)p->b * p->b;
+    g.X = Xh; g.ldx = p->b; g.strideX = (int64_t)nrhs * p->b;
+    g.C = Yh; g.ldc_q = p->b; g.ldc_m = 1; g.strideC = (int64_t)nrhs * p->b; g.strideCk = 0;
+    g.M = p->b; g.K = p->b; g.N = nrhs; g.kchunk = 0; g.err = p->err;
+    return launch_cgemm_tc(g, p->F, s);
+}
+
+template <typename R> static bool use_tensor(ztoep_plan_t p, int nrhs) {
+    if (sizeof(R) != sizeof(float) || nrhs < kTcMinRhs || nrhs > kTcMaxRhs) return false;
+    return p->That32full != nullptr && (p->E == 0 || p->B32T != nullptr);
+}
+
 template <typename R>
 ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *y, cudaStream_t s) {
     ZT_TRY(ensure_ws<R>(p, nrhs));
@@ -657,19 +715,29 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
     cplx_t<R> *Xh = reinterpret_cast<cplx_t<R> *>(w.Xh);
     const int ntile = edge_ntile(p, cs);
     const int nsplit = edge_nsplit(p, ntile, cs);
+    const bool tc = use_tensor<R>(p, nrhs) && w.Yh != nullptr;
     if (p->E > 0) {  // edge branch on the side stream, concurrent with the FFT chain
         ZT_CUDA(cudaEventRecord(p->ev_fork, s));
         ZT_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
-        ZT_TRY(launch_edge<R>(p, nrhs, x, y, w, p->side, true));
+        if (tc)
+            ZT_TRY(tc_edge(p, nrhs, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), w, p->side));
+        else
+            ZT_TRY(launch_edge<R>(p, nrhs, x, y, w, p->side, true));
         ZT_CUDA(cudaEventRecord(p->ev_join, p->side));
     }
     ZT_TRY(forward_passes<R>(p, nrhs, x, X1, Xh, s));
-    ZT_TRY(launch_blockprod<R>(p, nrhs, Xh, s));
+    cplx_t<R> *Yh = Xh;
+    if (tc) {
+        Yh = reinterpret_cast<cplx_t<R> *>(w.Yh);
+        ZT_TRY(tc_blockprod(p, nrhs, reinterpret_cast<const float2 *>(Xh), reinterpret_cast<float2 *>(Yh), s));
+    } else {
+        ZT_TRY(launch_blockprod<R>(p, nrhs, Xh, s));
+    }
     const PassCfg cy = pass_cfg(p->ly, p->b, p->lx * nrhs, cs, p->nsm);
     const int iby = 1 << cy.lib;
     dim3 gy((p->b + iby - 1) / iby, p->lx, nrhs);
     ZT_TRY((launch_fft_pass<R>(p->fy, twy_of<R>(p), cy.lib, true, gy,
-                               LdXh<R>{Xh, p->lx, p->b, iby, nrhs},
+                               LdXh<R>{Yh, p->lx, p->b, iby, nrhs},
                                StY1<R>{X1, p->ny, p->lx, p->b, iby}, s, cy.threads)));
     if (p->E > 0) ZT_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
     const PassCfg cx = pass_cfg(p->lx, p->b, p->ny * nrhs, cs, p->nsm);
@@ -702,6 +770,63 @@ void free_matvec_ws(ztoep_plan_t p) {
 }
 
 int64_t edge_row_stride(int64_t NT) { return edge_ldb(NT); }
+
+}  // namespace ztoep
+
+// ------------------------------------------------------------ tensor-core operands
+namespace ztoep {
+
+// Full FP32 spectrum: block of -f is the transpose of the stored block of f.
+__global__ void k_expand_spectrum32(const float2 *__restrict__ T32, const int *__restrict__ rep, float2 *out, int F,
+                                    int b) {
+    const int64_t bb = (int64_t)b * b;
+    const int64_t total = (int64_t)F * bb;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int f = (int)(k / bb);
+        const int64_t c = k - f * bb;
+        const int i = (int)(c / b), j = (int)(c - (int64_t)i * b);
+        const int r = rep[f];
+        out[k] = r >= 0 ? T32[(int64_t)r * bb + c] : T32[(int64_t)(-1 - r) * bb + (int64_t)j * b + i];
+    }
+}
+
+// BT[t][e] = B[e][t] through 32 x 32 shared-memory tiles.
+__global__ void k_transpose32(const float2 *__restrict__ B, int64_t ldb, float2 *__restrict__ BT, int E, int64_t NT) {
+    __shared__ float2 tile[32][33];
+    const int64_t t0 = (int64_t)blockIdx.x * 32;
+    const int e0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int e = e0 + r;
+        const int64_t t = t0 + threadIdx.x;
+        tile[r][threadIdx.x] = (e < E && t < NT) ? B[(int64_t)e * ldb + t] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t t = t0 + r;
+        const int e = e0 + threadIdx.x;
+        if (t < NT && e < E) BT[t * E + e] = tile[threadIdx.x][r];
+    }
+}
+
+ztoep_status_t ensure_tensor_data(ztoep_plan_t p, int nrhs, cudaStream_t s) {
+    if (nrhs < kTcMinRhs || nrhs > kTcMaxRhs) return ZTOEP_OK;
+    size_t acc = 0;
+    if (!p->That32full) {
+        ZT_TRY(dalloc((void **)&p->That32full, sizeof(float2) * (size_t)p->F * p->b * p->b, &acc));
+        KScope ks(K_MISC, s);
+        k_expand_spectrum32<<<1024, 256, 0, s>>>(p->That32, p->rep, p->That32full, p->F, p->b);
+        ZT_CUDA(cudaGetLastError());
+    }
+    if (p->E > 0 && !p->B32T) {
+        ZT_TRY(dalloc((void **)&p->B32T, sizeof(float2) * (size_t)p->NT * p->E, &acc));
+        dim3 g((unsigned)((p->NT + 31) / 32), (unsigned)((p->E + 31) / 32));
+        KScope ks(K_MISC, s);
+        k_transpose32<<<g, dim3(32, 8), 0, s>>>(p->B32, edge_ldb(p->NT), p->B32T, p->E, p->NT);
+        ZT_CUDA(cudaGetLastError());
+    }
+    p->tc_bytes += acc;
+    return ZTOEP_OK;
+}
 
 }  // namespace ztoep
 

@@ -209,6 +209,7 @@ void ztoep_plan_destroy(ztoep_plan_t p) {
     cudaFree(p->pairs); cudaFree(p->rep);
     cudaFree(p->That64); cudaFree(p->That32);
     cudaFree(p->B64); cudaFree(p->B32); cudaFree(p->C64); cudaFree(p->C32);
+    cudaFree(p->That32full); cudaFree(p->B32T);
     cudaFree(p->active);
     cudaFree(p->twx64); cudaFree(p->twy64); cudaFree(p->twx32); cudaFree(p->twy32);
     cudaFree(p->err);
@@ -352,7 +353,7 @@ ztoep_status_t ztoep_plan_get_info(ztoep_plan_t p, ztoep_plan_info_t *info) {
     info->lx = p->lx; info->ly = p->ly;
     info->n_toep = p->NT; info->n = p->N;
     info->n_pairs = p->npairs;
-    info->resident_bytes = p->resident + p->ws32.bytes + p->ws64.bytes + p->sws.bytes;
+    info->resident_bytes = p->resident + p->tc_bytes + p->ws32.bytes + p->ws64.bytes + p->sws.bytes;
     info->dense_bytes = (size_t)p->N * (size_t)p->N * 16;
     return ZTOEP_OK;
 }
@@ -367,7 +368,10 @@ size_t ztoep_footprint(const ztoep_desc_t *d, int32_t max_nrhs, int32_t restart)
     const size_t per_rhs = (size_t)(2 * N + (int64_t)d->ny * lx * d->b + (int64_t)lx * ly * d->b + 8 * NT) * 24;
     s += per_rhs * max_nrhs;
     // Krylov basis and vectors (FP64)
-    s += (size_t)max_nrhs * N * 16 * (restart + 3);
+    s += (size_t)max_nrhs * N * 16 * (restart + 8);
+    // tensor-core operands for 16+ RHS: full FP32 spectrum, transposed B, product output
+    if (max_nrhs >= kTcMinRhs)
+        s += (size_t)lx * ly * d->b * d->b * 8 + (size_t)NT * d->n_edge * 8 + (size_t)lx * ly * d->b * max_nrhs * 8;
     return s;
 }
 
@@ -379,6 +383,7 @@ ztoep_status_t ztoep_matvec(ztoep_plan_t p, int32_t prec, int32_t nrhs, const vo
     if (prec == ZTOEP_FP64)
         return run_matvec<double>(p, nrhs, (const double2 *)X, (double2 *)Y, s);
     ZT_TRY(ensure_ws<float>(p, nrhs));
+    ZT_TRY(ensure_tensor_data(p, nrhs, s));
     float2 *xin = (float2 *)p->ws32.xin, *yout = (float2 *)p->ws32.yout;
     ZT_TRY(launch_c128_to_c64((const double2 *)X, xin, (int64_t)nrhs * p->N, s));
     ZT_TRY(run_matvec<float>(p, nrhs, xin, yout, s));

@@ -1,0 +1,292 @@
+// Batched complex GEMM on the 5th-generation tensor cores (tcgen05, sm_100
+// family) with 3xTF32 split products and FP32 accumulation in TMEM.
+//
+//   C_p[m][q] = sum_k A_p[m][k] X_p[q][k]      (complex, per problem p)
+//
+// A is the resident operand (row-major, k contiguous), X the batch operand
+// ([q][k], k contiguous).  Complex arithmetic is mapped to one real GEMM: A's
+// complex row i becomes the real rows 2i = (ar, -ai, ...) and 2i+1 =
+// (ai, ar, ...) over the interleaved real k axis, X's complex row q is read as
+// the real row (xr, xi, ...), so real row 2i of D is Re C[i][q] and row 2i+1
+// is Im C[i][q].  Each real operand value v is split as hi = tf32(v),
+// lo = tf32(v - hi) and D += Ahi Xhi + Ahi Xlo + Alo Xhi (the 3xTF32 scheme),
+// which keeps the products close to FP32 accuracy.
+//
+// One CTA (4 warps) computes 64 complex rows (M = 128 real rows) x all N
+// columns over a K range: every k-block of 16 complex (32 real, 128 bytes) is
+// loaded by the threads, expanded, split and stored into 128-byte-swizzled
+// K-major tiles in shared memory; one thread issues the MMAs and commits them
+// to an mbarrier; the next k-block is staged while the MMAs run.  The
+// accumulator (128 lanes x N columns FP32) lives in tensor memory and is read
+// back with tcgen05.ld for the epilogue.
+#include <algorithm>
+
+#include "common.cuh"
+#include "instrument.cuh"
+#include "tcgemm.cuh"
+#include "tma.cuh"
+
+namespace ztoep {
+
+namespace {
+
+constexpr int TC_THREADS = 128;
+constexpr int TC_MC = 64;       // complex rows of A per CTA (128 real rows)
+constexpr int TC_KC = 16;       // complex k per k-block (32 real = 128 bytes)
+constexpr int TC_NST = 2;       // shared-memory stages
+constexpr uint32_t TC_WAIT = 1u << 22;
+
+__device__ __forceinline__ float tf32_rna(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+// byte offset of (row, 16-byte chunk) in a K-major tile with 128-byte rows and
+// the 128B swizzle (chunk index XOR row mod 8); 8-row groups are 1024 B apart.
+__device__ __forceinline__ uint32_t sw128(int row, int chunk) {
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+// Shared-memory matrix descriptor: K-major, 128B swizzle, SBO = 1024 B.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;                      // leading-dimension offset (unused with this swizzle)
+    d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32; // stride between 8-row groups
+    d |= (uint64_t)1 << 46;                      // descriptor version for sm_100
+    d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Stage layout (bytes, each tile 1024-aligned):
+//   A_hi [128 rows][128 B], A_lo [128][128], X_hi [NP rows][128], X_lo [NP][128]
+struct Stage {
+    uint32_t a_hi, a_lo, x_hi, x_lo;
+};
+
+__device__ __forceinline__ Stage stage_at(uint32_t base, int s, int np) {
+    const uint32_t a = 128 * 128, x = (uint32_t)np * 128;
+    const uint32_t sz = 2 * a + 2 * x;
+    Stage st;
+    st.a_hi = base + s * sz;
+    st.a_lo = st.a_hi + a;
+    st.x_hi = st.a_lo + a;
+    st.x_lo = st.x_hi + x;
+    return st;
+}
+
+// Expand + split + store the A k-block (64 complex rows x 16 complex k) and the
+// X k-block (np rows x 16 complex k) into the stage.
+__device__ __forceinline__ void stage_load(const CgemmArgs &g, int p, int m0, int k0, int kend, const Stage &st,
+                                           unsigned char *smem, uint32_t sbase) {
+    const float2 *A = g.A + (int64_t)p * g.strideA;
+    const float2 *X = g.X + (int64_t)p * g.strideX;
+    // A: thread t -> complex row t/2, complex k [8*(t%2), 8*(t%2)+8)
+    {
+        const int t = threadIdx.x;
+        const int i = t >> 1, half = t & 1;
+        const int m = m0 + i;
+        float2 v[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int k = k0 + half * 8 + c;
+            v[c] = (m < g.M && k < kend) ? A[(int64_t)m * g.lda + k] : make_float2(0.f, 0.f);
+        }
+        // real row 2i: (ar, -ai); row 2i+1: (ai, ar); real col 2c+{0,1} -> chunk (half*16 + 2c)/4
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {  // 4 chunks of 4 floats = 2 complex
+            const float2 a0 = v[2 * ch], a1 = v[2 * ch + 1];
+            const int chunk = half * 4 + ch;
+            const float4 re = make_float4(a0.x, -a0.y, a1.x, -a1.y);
+            const float4 im = make_float4(a0.y, a0.x, a1.y, a1.x);
+            const float4 reh = make_float4(tf32_rna(re.x), tf32_rna(re.y), tf32_rna(re.z), tf32_rna(re.w));
+            const float4 imh = make_float4(tf32_rna(im.x), tf32_rna(im.y), tf32_rna(im.z), tf32_rna(im.w));
+            const float4 rel = make_float4(tf32_rna(re.x - reh.x), tf32_rna(re.y - reh.y), tf32_rna(re.z - reh.z),
+                                           tf32_rna(re.w - reh.w));
+            const float4 iml = make_float4(tf32_rna(im.x - imh.x), tf32_rna(im.y - imh.y), tf32_rna(im.z - imh.z),
+                                           tf32_rna(im.w - imh.w));
+            const uint32_t o0 = sw128(2 * i, chunk), o1 = sw128(2 * i + 1, chunk);
+            *reinterpret_cast<float4 *>(smem + (st.a_hi - sbase) + o0) = reh;
+            *reinterpret_cast<float4 *>(smem + (st.a_lo - sbase) + o0) = rel;
+            *reinterpret_cast<float4 *>(smem + (st.a_hi - sbase) + o1) = imh;
+            *reinterpret_cast<float4 *>(smem + (st.a_lo - sbase) + o1) = iml;
+        }
+    }
+    // X: np rows x 8 chunks (each chunk = 2 complex)
+    for (int idx = threadIdx.x; idx < g.np * 8; idx += blockDim.x) {
+        const int q = idx >> 3, chunk = idx & 7;
+        const int k = k0 + chunk * 2;
+        float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+        if (q < g.N) {
+            const float2 *xr = X + (int64_t)q * g.ldx;
+            if (k < kend) a0 = xr[k];
+            if (k + 1 < kend) a1 = xr[k + 1];
+        }
+        const float4 v = make_float4(a0.x, a0.y, a1.x, a1.y);
+        const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+        const float4 l =
+            make_float4(tf32_rna(v.x - h.x), tf32_rna(v.y - h.y), tf32_rna(v.z - h.z), tf32_rna(v.w - h.w));
+        const uint32_t o = sw128(q, chunk);
+        *reinterpret_cast<float4 *>(smem + (st.x_hi - sbase) + o) = h;
+        *reinterpret_cast<float4 *>(smem + (st.x_lo - sbase) + o) = l;
+    }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(TC_THREADS) k_cgemm_tc(CgemmArgs g) {
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    __shared__ __align__(8) uint64_t done[TC_NST];
+    __shared__ uint32_t tmem_base;
+    __shared__ int fail;
+    // 1024-byte aligned base for the swizzled tiles
+    const uint32_t raw = smem_u32(tc_smem_raw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    unsigned char *smem = tc_smem_raw + (sbase - raw);
+
+    const int p = blockIdx.z;
+    const int m0 = blockIdx.x * TC_MC;
+    const int kbeg = blockIdx.y * g.kchunk;
+    const int kend = min(g.K, kbeg + g.kchunk);
+    const int nkb = (kend - kbeg + TC_KC - 1) / TC_KC;
+    const int warp = threadIdx.x >> 5;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(g.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_NST; ++s) mbar_init(&done[s], 1);
+        mbar_fence_init();
+        fail = 0;
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = idesc_tf32(g.np);
+
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % TC_NST;
+        if (kb >= TC_NST) {  // stage s is free once the MMAs of k-block kb - NST are done
+            const bool ok = mbar_wait_bounded(&done[s], (uint32_t)(((kb / TC_NST) - 1) & 1), TC_WAIT);
+            if (!ok) fail = 1;
+        }
+        if (__syncthreads_or(fail)) break;
+        const Stage st = stage_at(sbase, s, g.np);
+        stage_load(g, p, m0, kbeg + kb * TC_KC, kend, st, smem, sbase);
+        fence_proxy_async();  // generic-proxy stores -> visible to the tensor core
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            fence_after();
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {  // 4 x (K = 8 real = 32 bytes)
+                const uint32_t off = ks * 32;
+                const uint64_t ah = sdesc(st.a_hi + off), al = sdesc(st.a_lo + off);
+                const uint64_t xh = sdesc(st.x_hi + off), xl = sdesc(st.x_lo + off);
+                mma_tf32(tmem, ah, xh, idesc, (kb > 0 || ks > 0) ? 1 : 0);
+                mma_tf32(tmem, ah, xl, idesc, 1);
+                mma_tf32(tmem, al, xh, idesc, 1);
+            }
+            mma_commit(&done[s]);
+        }
+    }
+    // wait for the last commit (covers every earlier MMA)
+    if (!fail && nkb > 0) {
+        const int kb = nkb - 1;
+        const bool ok = mbar_wait_bounded(&done[kb % TC_NST], (uint32_t)((kb / TC_NST) & 1), TC_WAIT);
+        if (!ok) fail = 1;
+    }
+    const int failed = __syncthreads_or(fail);
+    fence_after();
+    if (failed) {
+        if (threadIdx.x == 0) atomicOr(g.err, 2);
+    } else {
+        // epilogue: warp w holds real rows 32w..32w+31 (TMEM lanes), columns = q
+        const int row = warp * 32 + (threadIdx.x & 31);
+        const int i = row >> 1, c = row & 1;
+        const int m = m0 + i;
+        float *C = reinterpret_cast<float *>(g.C + (int64_t)p * g.strideC + (int64_t)blockIdx.y * g.strideCk);
+        for (int q0 = 0; q0 < g.np; q0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)q0, r);
+            if (m < g.M && nkb > 0) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int q = q0 + j;
+                    if (q < g.N) C[2 * ((int64_t)q * g.ldc_q + (int64_t)m * g.ldc_m) + c] = __uint_as_float(r[j]);
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols) : "memory");
+}
+
+size_t cgemm_smem_bytes(int np) { return (size_t)TC_NST * (2 * 128 * 128 + 2 * (size_t)np * 128) + 1024; }
+
+ztoep_status_t launch_cgemm_tc(CgemmArgs g, int nprob, cudaStream_t s) {
+    if (g.N < 1 || g.N > 256 || g.M < 1 || g.K < 1 || nprob < 1) return ZTOEP_ERR_ARG;
+    g.np = (g.N + 15) / 16 * 16;  // N of the MMA: multiple of 16 for M = 128
+    if (g.np < 32) g.np = 32;     // epilogue reads 32 columns at a time
+    int cols = 32;
+    while (cols < g.np) cols <<= 1;
+    g.tmem_cols = cols;
+    if (g.kchunk <= 0) g.kchunk = g.K;
+    g.kchunk = (g.kchunk + TC_KC - 1) / TC_KC * TC_KC;
+    const size_t smem = cgemm_smem_bytes(g.np);
+    static bool attr = false;
+    if (!attr) {
+        ZT_CUDA(cudaFuncSetAttribute(k_cgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr = true;
+    }
+    if (smem > 200 * 1024) return ZTOEP_ERR_UNSUPPORTED;
+    dim3 grid((g.M + TC_MC - 1) / TC_MC, (g.K + g.kchunk - 1) / g.kchunk, nprob);
+    KScope ks(K_TENSOR, s);
+    k_cgemm_tc<<<grid, TC_THREADS, smem, s>>>(g);
+    ZT_CUDA(cudaGetLastError());
+    return ZTOEP_OK;
+}
+
+}  // namespace ztoep

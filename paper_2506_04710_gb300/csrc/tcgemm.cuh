@@ -1,0 +1,34 @@
+// Batched complex GEMM on tcgen05 tensor cores (3xTF32, FP32 accumulate):
+//   C_p[m][q] = sum_k A_p[m][k] X_p[q][k]
+// A: complex row-major (k contiguous), lda; X: complex [q][k], ldx.
+// C element (q, m) of problem p and K split s lives at
+//   C + p * strideC + s * strideCk + q * ldc_q + m * ldc_m.
+#pragma once
+
+#include "common.cuh"
+
+namespace ztoep {
+
+struct CgemmArgs {
+    const float2 *A;
+    int64_t lda, strideA;
+    const float2 *X;
+    int64_t ldx, strideX;
+    float2 *C;
+    int64_t ldc_q, ldc_m, strideC, strideCk;
+    int M, K, N;     // complex sizes; N <= 256
+    int kchunk;      // complex k per CTA (0 = all of K); partial sums per split
+    int np, tmem_cols;  // set by the launcher
+    int *err;        // device error word (bounded waits)
+};
+
+size_t cgemm_smem_bytes(int np);
+ztoep_status_t launch_cgemm_tc(CgemmArgs g, int nprob, cudaStream_t s);
+
+// Number of K splits the launcher uses for a given K and chunk.
+inline int cgemm_splits(int K, int kchunk) {
+    const int kc = (kchunk + 15) / 16 * 16;
+    return (K + kc - 1) / kc;
+}
+
+}  // namespace ztoep

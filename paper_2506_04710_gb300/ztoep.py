@@ -71,7 +71,7 @@ EXPORTS = ["ztoep_default_opts", "ztoep_plan", "ztoep_matvec", "ztoep_solve", "z
            "ztoep_plan_destroy", "ztoep_status_string", "ztoep_version", "ztoep_launch_count",
            "ztoep_timing_enable", "ztoep_timing_reset", "ztoep_timing_read", "ztoep_edge_product_noalloc"]
 
-K_FFT, K_BLOCKPROD, K_EDGE, K_ARNOLDI, K_MISC = range(5)
+K_FFT, K_BLOCKPROD, K_EDGE, K_ARNOLDI, K_MISC, K_TENSOR = range(6)
 
 
 def lib(path: str | None = None):

@@ -270,3 +270,41 @@ def test_timeout_is_enforced_on_device():
     assert st == ztoep.ZTOEP_ERR_TIMEOUT
     assert all(i["status"] == ztoep.ZTOEP_ERR_TIMEOUT for i in info)
     plan.close()
+
+
+TC_CASES = [("9x4_b40_e24", 16), ("7x6_b12_e20", 20), ("6x6_b33_e0_gap", 33), ("3x5_b4_e12_pw3", 40),
+            ("4x4_b8_e16", 17)]
+
+
+@pytest.mark.parametrize("key,nrhs", TC_CASES)
+def test_matvec_mixed_tensor_core_path_vs_oracle(key, nrhs):
+    # 16..256 RHS take the tcgen05 3xTF32 path for the block and edge products
+    kw = dict(CASES[key])
+    kw.update(rhs="planewave", nrhs=nrhs)
+    prob = synth.make_problem(**kw)
+    ref = oracle.matvec_dense(oracle.assemble(prob), prob.V)
+    plan = ztoep.Plan.from_problem(prob)
+    ztoep.ztoep_timing_reset()
+    ztoep.ztoep_timing_enable(1 << ztoep.K_TENSOR)
+    got = host(plan.matvec(dev(prob.V), ztoep.ZTOEP_MIXED))
+    ztoep.ztoep_timing_enable(0)
+    assert ztoep.ztoep_timing_read(ztoep.K_TENSOR)[0] >= 1  # the tensor-core kernels ran
+    err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= 2e-6
+    plan.close()
+
+
+def test_solve_mixed_tensor_core_path_vs_lu():
+    kw = dict(CASES["9x4_b40_e24"])
+    kw.update(rhs="planewave", nrhs=24)
+    prob = synth.make_problem(**kw)
+    Z = oracle.assemble(prob)
+    Xref = oracle.LU(Z).solve(prob.V)
+    plan = ztoep.Plan.from_problem(prob)
+    X, info, st = plan.solve(dev(prob.V), opts=opts(ztoep.ZTOEP_MIXED, 1e-8))
+    assert st == 0 and oracle.relres(Z, host(X), prob.V).max() <= 1e-8
+    X2, _, st2 = plan.solve(dev(prob.V), opts=opts(ztoep.ZTOEP_MIXED, 1e-11))
+    assert st2 == 0
+    err = np.linalg.norm(host(X2) - Xref, axis=1) / np.linalg.norm(Xref, axis=1)
+    assert err.max() <= 1e-7
+    plan.close()
