@@ -241,6 +241,72 @@ ZTOEP_API ztoep_status_t ztoep_timing_read(int32_t cls, uint64_t *timed_launches
 /* Library version string, e.g. "ztoep 0.1 sm_103a". */
 ZTOEP_API const char *ztoep_version(void);
 
+/* ---- Serving: continuous batching of array solves ----
+ * A scheduler owns worker threads, each with its own CUDA stream.  Submitted
+ * requests (any nx, ny, b, n_edge, nrhs) wait in a FIFO queue and are
+ * admitted as soon as a worker is free and the device bytes they need fit in
+ * the budget (ztoep_footprint of the request, plus the plans kept resident);
+ * admitted requests run concurrently, so their kernels overlap on the device.
+ * Plans (the FFT'd generating blocks, B and C) stay resident under their
+ * plan_key and are reused by later requests with the same key; idle ones are
+ * evicted least-recently-used when the budget requires.  Each request gets
+ * exactly the arithmetic of a ztoep_solve of the same request alone. */
+typedef struct ztoep_sched_s *ztoep_sched_t;
+
+typedef struct {
+    size_t hbm_budget;   /* device bytes the scheduler may hold (plans + work) */
+    int32_t workers;     /* concurrent requests (worker threads / streams), 1..64 */
+    int32_t device;      /* CUDA device index */
+    int32_t fake_backend;/* 1: no CUDA work; each request sleeps fake_us (host-logic tests) */
+    int64_t fake_us;
+} ztoep_sched_opts_t;
+
+typedef struct {
+    ztoep_desc_t desc;
+    int32_t inputs_on_device; /* 1: T, B, C, V and X are device pointers, else host */
+    uint64_t plan_key;        /* nonzero: requests with equal keys share one resident plan */
+    const void *T, *B, *C;    /* complex128, layouts as in ztoep_plan */
+    int32_t nrhs;
+    const void *V;            /* complex128 [nrhs][N] */
+    void *X;                  /* complex128 [nrhs][N] solution (initial guess ignored) */
+    ztoep_solve_opts_t opts;
+    ztoep_solve_info_t *info; /* host [nrhs] or NULL */
+} ztoep_request_t;
+/* The request's buffers must stay valid until it completes. */
+
+typedef struct {
+    int32_t state;           /* 0 queued, 1 running, 2 done */
+    int32_t status;          /* ztoep_status_t of the solve (when done) */
+    int32_t plan_reused;     /* the resident plan of plan_key was used */
+    double queue_ms;         /* submit -> start */
+    double latency_ms;       /* submit -> done */
+} ztoep_request_state_t;
+
+typedef struct {
+    int64_t submitted, completed, max_in_flight;
+    size_t bytes_in_use, peak_bytes, resident_plan_bytes;
+    int64_t plans_built, plans_reused, plans_evicted;
+} ztoep_sched_stats_t;
+
+/* Errors: ARG (bad options), CUDA. */
+ZTOEP_API ztoep_status_t ztoep_sched_create(const ztoep_sched_opts_t *opts, ztoep_sched_t *out);
+
+/* Queue a request; *id identifies it.  A request whose footprint alone exceeds
+ * the budget is rejected with NOMEM; a bad descriptor with ARG. */
+ZTOEP_API ztoep_status_t ztoep_sched_submit(ztoep_sched_t s, const ztoep_request_t *req, int64_t *id);
+
+/* Current state of request id (ARG if unknown). */
+ZTOEP_API ztoep_status_t ztoep_sched_poll(ztoep_sched_t s, int64_t id, ztoep_request_state_t *st);
+
+/* Block until request id is done or timeout_ms passes (TIMEOUT); < 0 waits forever. */
+ZTOEP_API ztoep_status_t ztoep_sched_wait(ztoep_sched_t s, int64_t id, int64_t timeout_ms,
+                                          ztoep_request_state_t *st);
+
+ZTOEP_API ztoep_status_t ztoep_sched_get_stats(ztoep_sched_t s, ztoep_sched_stats_t *st);
+
+/* Finish queued and running requests, free resident plans, stop the workers. */
+ZTOEP_API void ztoep_sched_destroy(ztoep_sched_t s);
+
 #ifdef __cplusplus
 }
 #endif

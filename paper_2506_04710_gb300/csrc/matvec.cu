@@ -702,7 +702,7 @@ static ztoep_status_t tc_blockprod(ztoep_plan_t p, int nrhs, const float2 *Xh, f
 }
 
 template <typename R> static bool use_tensor(ztoep_plan_t p, int nrhs) {
-    if (sizeof(R) != sizeof(float) || nrhs < kTcMinRhs || nrhs > kTcMaxRhs) return false;
+    if (sizeof(R) != sizeof(float) || nrhs < kTcMinRhs || nrhs > kTcMaxRhs || !cgemm_fits(nrhs)) return false;
     return p->That32full != nullptr && (p->E == 0 || p->B32T != nullptr);
 }
 

@@ -1,0 +1,341 @@
+// Serving scheduler: continuous batching of array solves with admission by
+// device-memory footprint and resident plans (the FFT'd generating blocks, B
+// and C stay on the device under a caller-chosen key).
+//
+// Worker threads each own a CUDA stream.  A request is admitted when a worker
+// is free and   bytes reserved by running requests + idle resident plans +
+// ztoep_footprint(request) <= budget;   idle plans are evicted least-recently
+// used to make room.  Admitted requests run concurrently on their streams, so
+// the kernels of different requests overlap on the device; a request that
+// arrives while others run starts as soon as a worker and memory free up.
+// The queue is FIFO (only its head is considered, so large requests are not
+// starved).  Every request runs exactly the ztoep_solve it would run alone.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+    int64_t id = 0;
+    ztoep_request_t r{};
+    size_t fp = 0;          // reserved bytes while running
+    int state = 0;          // 0 queued, 1 running, 2 done
+    int status = 0;
+    int reused = 0;
+    bool holds_ref = false;  // holds a reference on the resident plan of its key
+    Clock::time_point t_submit, t_start, t_done;
+};
+
+struct CachedPlan {
+    ztoep_plan_t plan = nullptr;
+    size_t bytes = 0;
+    int refs = 0;
+    uint64_t last_use = 0;
+};
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+}  // namespace
+
+struct ztoep_sched_s {
+    ztoep_sched_opts_t o{};
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Req *> queue;
+    std::unordered_map<int64_t, std::unique_ptr<Req>> reqs;
+    std::unordered_map<uint64_t, CachedPlan> plans;
+    std::vector<std::thread> threads;
+    bool stop = false;
+    int64_t next_id = 1, submitted = 0, completed = 0, in_flight = 0, max_in_flight = 0;
+    size_t bytes_work = 0, peak = 0;
+    int64_t built = 0, reused = 0, evicted = 0;
+    uint64_t tick = 0;
+
+    size_t idle_plan_bytes() const {
+        size_t s = 0;
+        for (const auto &kv : plans)
+            if (kv.second.refs == 0) s += kv.second.bytes;
+        return s;
+    }
+    size_t plan_bytes() const {
+        size_t s = 0;
+        for (const auto &kv : plans) s += kv.second.bytes;
+        return s;
+    }
+
+    // Under mu: reserve the head request's bytes, evicting idle plans if needed.
+    bool try_admit(Req *q) {
+        for (;;) {
+            const size_t held = bytes_work + idle_plan_bytes();
+            if (held + q->fp <= o.hbm_budget) {
+                bytes_work += q->fp;
+                peak = std::max(peak, bytes_work + idle_plan_bytes());
+                return true;
+            }
+            // evict the least recently used idle plan (never the one this request reuses)
+            auto victim = plans.end();
+            for (auto it = plans.begin(); it != plans.end(); ++it)
+                if (it->second.refs == 0 && it->first != q->r.plan_key &&
+                    (victim == plans.end() || it->second.last_use < victim->second.last_use))
+                    victim = it;
+            if (victim == plans.end()) return false;
+            if (!o.fake_backend) ztoep_plan_destroy(victim->second.plan);
+            plans.erase(victim);
+            ++evicted;
+        }
+    }
+
+    void run(Req *q, cudaStream_t s) {
+        ztoep_request_t &r = q->r;
+        if (o.fake_backend) {  // host logic only: no device work, plans are bookkeeping entries
+            std::this_thread::sleep_for(std::chrono::microseconds(o.fake_us));
+            std::lock_guard<std::mutex> lk(mu);
+            q->status = ZTOEP_OK;
+            if (r.plan_key) {
+                auto it = plans.find(r.plan_key);
+                if (it != plans.end()) {
+                    ++reused;
+                    q->reused = 1;
+                } else {
+                    ++built;
+                    CachedPlan cp;
+                    cp.bytes = q->fp / 2;
+                    plans.emplace(r.plan_key, cp);
+                    it = plans.find(r.plan_key);
+                }
+                it->second.refs++;
+                q->holds_ref = true;
+            }
+            return;
+        }
+        cudaSetDevice(o.device);
+        ztoep_plan_t plan = nullptr;
+        bool from_cache = false;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            if (r.plan_key) {
+                auto it = plans.find(r.plan_key);
+                if (it != plans.end()) {
+                    plan = it->second.plan;
+                    from_cache = true;
+                    it->second.refs++;  // not evictable while this request uses it
+                    q->holds_ref = true;
+                }
+            }
+        }
+        ztoep_status_t st = ZTOEP_OK;
+        if (!plan) {
+            if (r.inputs_on_device) {
+                st = ztoep_plan(&r.desc, r.T, r.B, r.C, s, &plan);
+            } else {  // stage the host blocks on the device for the plan build
+                const int64_t nt = (int64_t)r.desc.nx * r.desc.ny * r.desc.b, e = r.desc.n_edge;
+                const size_t tb = sizeof(double2) * (size_t)(2 * r.desc.ny - 1) * (2 * r.desc.nx - 1) * r.desc.b * r.desc.b;
+                const size_t bb = sizeof(double2) * (size_t)e * nt, cb = sizeof(double2) * (size_t)e * e;
+                void *dT = nullptr, *dB = nullptr, *dC = nullptr;
+                bool ok = cudaMalloc(&dT, tb) == cudaSuccess;
+                if (ok && e > 0) ok = cudaMalloc(&dB, bb) == cudaSuccess && cudaMalloc(&dC, cb) == cudaSuccess;
+                if (ok) {
+                    cudaMemcpyAsync(dT, r.T, tb, cudaMemcpyHostToDevice, s);
+                    if (e > 0) {
+                        cudaMemcpyAsync(dB, r.B, bb, cudaMemcpyHostToDevice, s);
+                        cudaMemcpyAsync(dC, r.C, cb, cudaMemcpyHostToDevice, s);
+                    }
+                    st = ztoep_plan(&r.desc, dT, dB, dC, s, &plan);
+                    cudaStreamSynchronize(s);
+                } else {
+                    cudaGetLastError();
+                    st = ZTOEP_ERR_NOMEM;
+                }
+                cudaFree(dT);
+                cudaFree(dB);
+                cudaFree(dC);
+            }
+        }
+        if (st == ZTOEP_OK) {
+            ztoep_solve_opts_t so = r.opts;
+            so.flags |= ZTOEP_FLAG_ZERO_GUESS;
+            st = r.inputs_on_device ? ztoep_solve(plan, &so, r.nrhs, r.V, r.X, r.info, s)
+                                    : ztoep_solve_host(plan, &so, r.nrhs, r.V, r.X, r.info, s);
+            cudaStreamSynchronize(s);
+        }
+        q->status = st;
+        q->reused = from_cache ? 1 : 0;
+        std::lock_guard<std::mutex> lk(mu);
+        if (from_cache) {
+            ++reused;
+        } else if (plan) {
+            ++built;
+            if (r.plan_key && plans.find(r.plan_key) == plans.end()) {
+                ztoep_plan_info_t pi{};
+                ztoep_plan_get_info(plan, &pi);
+                CachedPlan cp;
+                cp.plan = plan;
+                cp.bytes = pi.resident_bytes;
+                cp.refs = 1;  // released when the request completes
+                plans.emplace(r.plan_key, cp);
+                q->holds_ref = true;
+            } else {
+                ztoep_plan_destroy(plan);
+            }
+        }
+    }
+
+    void worker() {
+        cudaStream_t s = nullptr;
+        if (!o.fake_backend) {
+            cudaSetDevice(o.device);
+            cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        }
+        for (;;) {
+            Req *q = nullptr;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv_work.wait(lk, [&] { return (stop && queue.empty()) || (!queue.empty() && try_admit(queue.front())); });
+                if (queue.empty()) break;
+                q = queue.front();
+                queue.pop_front();
+                q->state = 1;
+                q->t_start = Clock::now();
+                ++in_flight;
+                max_in_flight = std::max(max_in_flight, in_flight);
+            }
+            run(q, s);
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                bytes_work -= q->fp;
+                if (q->holds_ref) {
+                    auto it = plans.find(q->r.plan_key);
+                    if (it != plans.end()) {
+                        it->second.refs--;
+                        it->second.last_use = ++tick;
+                    }
+                }
+                --in_flight;
+                ++completed;
+                q->t_done = Clock::now();
+                q->state = 2;
+            }
+            cv_done.notify_all();
+            cv_work.notify_all();
+        }
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
+extern "C" {
+
+ztoep_status_t ztoep_sched_create(const ztoep_sched_opts_t *o, ztoep_sched_t *out) {
+    if (!o || !out || o->workers < 1 || o->workers > 64 || o->hbm_budget == 0 || o->fake_us < 0) return ZTOEP_ERR_ARG;
+    *out = nullptr;
+    auto *s = new (std::nothrow) ztoep_sched_s();
+    if (!s) return ZTOEP_ERR_NOMEM;
+    s->o = *o;
+    if (!o->fake_backend && cudaSetDevice(o->device) != cudaSuccess) {
+        delete s;
+        return ZTOEP_ERR_CUDA;
+    }
+    for (int i = 0; i < o->workers; ++i) s->threads.emplace_back([s] { s->worker(); });
+    *out = s;
+    return ZTOEP_OK;
+}
+
+ztoep_status_t ztoep_sched_submit(ztoep_sched_t s, const ztoep_request_t *r, int64_t *id) {
+    if (!s || !r || !id || r->nrhs < 1 || !r->T || !r->V || !r->X) return ZTOEP_ERR_ARG;
+    if (r->desc.n_edge > 0 && (!r->B || !r->C)) return ZTOEP_ERR_ARG;
+    const size_t fp = ztoep_footprint(&r->desc, r->nrhs, r->opts.restart > 0 ? r->opts.restart : 30);
+    if (fp == 0) return ZTOEP_ERR_ARG;
+    if (fp > s->o.hbm_budget) return ZTOEP_ERR_NOMEM;
+    auto q = std::make_unique<Req>();
+    q->r = *r;
+    q->fp = fp;
+    q->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return ZTOEP_ERR_ARG;
+        q->id = s->next_id++;
+        *id = q->id;
+        s->queue.push_back(q.get());
+        s->reqs.emplace(q->id, std::move(q));
+        ++s->submitted;
+    }
+    s->cv_work.notify_one();
+    return ZTOEP_OK;
+}
+
+static void fill_state(const Req *q, ztoep_request_state_t *st) {
+    st->state = q->state;
+    st->status = q->state == 2 ? q->status : 0;
+    st->plan_reused = q->reused;
+    st->queue_ms = q->state >= 1 ? ms_between(q->t_submit, q->t_start) : 0.0;
+    st->latency_ms = q->state == 2 ? ms_between(q->t_submit, q->t_done) : 0.0;
+}
+
+ztoep_status_t ztoep_sched_poll(ztoep_sched_t s, int64_t id, ztoep_request_state_t *st) {
+    if (!s || !st) return ZTOEP_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return ZTOEP_ERR_ARG;
+    fill_state(it->second.get(), st);
+    return ZTOEP_OK;
+}
+
+ztoep_status_t ztoep_sched_wait(ztoep_sched_t s, int64_t id, int64_t timeout_ms, ztoep_request_state_t *st) {
+    if (!s || !st) return ZTOEP_ERR_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return ZTOEP_ERR_ARG;
+    Req *q = it->second.get();
+    auto done = [&] { return q->state == 2; };
+    if (timeout_ms < 0)
+        s->cv_done.wait(lk, done);
+    else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) {
+        fill_state(q, st);
+        return ZTOEP_ERR_TIMEOUT;
+    }
+    fill_state(q, st);
+    return ZTOEP_OK;
+}
+
+ztoep_status_t ztoep_sched_get_stats(ztoep_sched_t s, ztoep_sched_stats_t *st) {
+    if (!s || !st) return ZTOEP_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    st->submitted = s->submitted;
+    st->completed = s->completed;
+    st->max_in_flight = s->max_in_flight;
+    st->bytes_in_use = s->bytes_work + s->idle_plan_bytes();
+    st->peak_bytes = s->peak;
+    st->resident_plan_bytes = s->plan_bytes();
+    st->plans_built = s->built;
+    st->plans_reused = s->reused;
+    st->plans_evicted = s->evicted;
+    return ZTOEP_OK;
+}
+
+void ztoep_sched_destroy(ztoep_sched_t s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    for (auto &t : s->threads) t.join();
+    if (!s->o.fake_backend) {
+        cudaSetDevice(s->o.device);
+        for (auto &kv : s->plans) ztoep_plan_destroy(kv.second.plan);
+    }
+    delete s;
+}
+
+}  // extern "C"

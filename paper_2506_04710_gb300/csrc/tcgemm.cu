@@ -112,60 +112,77 @@ __device__ __forceinline__ Stage stage_at(uint32_t base, int s, int np) {
     return st;
 }
 
-// Expand + split + store the A k-block (64 complex rows x 16 complex k) and the
-// X k-block (np rows x 16 complex k) into the stage.
-__device__ __forceinline__ void stage_load(const CgemmArgs &g, int p, int m0, int k0, int kend, const Stage &st,
-                                           unsigned char *smem, uint32_t sbase) {
-    const float2 *A = g.A + (int64_t)p * g.strideA;
-    const float2 *X = g.X + (int64_t)p * g.strideX;
-    // A: thread t -> complex row t/2, complex k [8*(t%2), 8*(t%2)+8)
-    {
-        const int t = threadIdx.x;
-        const int i = t >> 1, half = t & 1;
-        const int m = m0 + i;
-        float2 v[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int k = k0 + half * 8 + c;
-            v[c] = (m < g.M && k < kend) ? A[(int64_t)m * g.lda + k] : make_float2(0.f, 0.f);
-        }
-        // real row 2i: (ar, -ai); row 2i+1: (ai, ar); real col 2c+{0,1} -> chunk (half*16 + 2c)/4
-#pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {  // 4 chunks of 4 floats = 2 complex
-            const float2 a0 = v[2 * ch], a1 = v[2 * ch + 1];
-            const int chunk = half * 4 + ch;
-            const float4 re = make_float4(a0.x, -a0.y, a1.x, -a1.y);
-            const float4 im = make_float4(a0.y, a0.x, a1.y, a1.x);
-            const float4 reh = make_float4(tf32_rna(re.x), tf32_rna(re.y), tf32_rna(re.z), tf32_rna(re.w));
-            const float4 imh = make_float4(tf32_rna(im.x), tf32_rna(im.y), tf32_rna(im.z), tf32_rna(im.w));
-            const float4 rel = make_float4(tf32_rna(re.x - reh.x), tf32_rna(re.y - reh.y), tf32_rna(re.z - reh.z),
-                                           tf32_rna(re.w - reh.w));
-            const float4 iml = make_float4(tf32_rna(im.x - imh.x), tf32_rna(im.y - imh.y), tf32_rna(im.z - imh.z),
-                                           tf32_rna(im.w - imh.w));
-            const uint32_t o0 = sw128(2 * i, chunk), o1 = sw128(2 * i + 1, chunk);
-            *reinterpret_cast<float4 *>(smem + (st.a_hi - sbase) + o0) = reh;
-            *reinterpret_cast<float4 *>(smem + (st.a_lo - sbase) + o0) = rel;
-            *reinterpret_cast<float4 *>(smem + (st.a_hi - sbase) + o1) = imh;
-            *reinterpret_cast<float4 *>(smem + (st.a_lo - sbase) + o1) = iml;
-        }
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// One 16-byte piece (two complex values at k, k+1) of row `row` of a complex
+// matrix into shared memory; out-of-range values are zero-filled.
+__device__ __forceinline__ void copy_pair(uint32_t dst, const float2 *rowp, bool row_ok, int k, int kend) {
+    const float2 *src = rowp + k;
+    const bool v0 = row_ok && k < kend, v1 = row_ok && k + 1 < kend;
+    if (v0 && v1 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0)) {
+        cp_async16(dst, src, 16);
+    } else {
+        cp_async8(dst, v0 ? (const void *)src : (const void *)rowp, v0 ? 8u : 0u);
+        cp_async8(dst + 8, v1 ? (const void *)(src + 1) : (const void *)rowp, v1 ? 8u : 0u);
     }
-    // X: np rows x 8 chunks (each chunk = 2 complex)
+}
+
+// Raw k-block (A: 64 complex rows x 16 complex k; X: np rows x 16 complex k)
+// into a raw staging buffer, row-major, by asynchronous copies.
+__device__ __forceinline__ void raw_issue(const CgemmArgs &g, const float2 *A, const float2 *X, int m0, int k0,
+                                          int kend, uint32_t raw_a, uint32_t raw_x) {
+    for (int idx = threadIdx.x; idx < TC_MC * 8; idx += blockDim.x) {
+        const int i = idx >> 3, pr = idx & 7;
+        const int m = m0 + i;
+        const bool ok = m < g.M;
+        copy_pair(raw_a + (uint32_t)(i * 128 + pr * 16), A + (int64_t)(ok ? m : 0) * g.lda, ok, k0 + 2 * pr, kend);
+    }
     for (int idx = threadIdx.x; idx < g.np * 8; idx += blockDim.x) {
+        const int q = idx >> 3, pr = idx & 7;
+        const bool ok = q < g.N;
+        copy_pair(raw_x + (uint32_t)(q * 128 + pr * 16), X + (int64_t)(ok ? q : 0) * g.ldx, ok, k0 + 2 * pr, kend);
+    }
+}
+
+__device__ __forceinline__ float4 tf32x4(float4 v) {
+    return make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+}
+__device__ __forceinline__ float4 sub4(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+
+// Expand (complex row i -> real rows 2i = (ar, -ai), 2i+1 = (ai, ar)), split
+// into TF32 hi/lo and store into the 128B-swizzled operand tiles.
+__device__ __forceinline__ void stage_transform(const unsigned char *smem, uint32_t sbase, uint32_t raw_a,
+                                                uint32_t raw_x, int np, const Stage &st) {
+    unsigned char *sm = const_cast<unsigned char *>(smem);
+    for (int idx = threadIdx.x; idx < TC_MC * 8; idx += blockDim.x) {
+        const int i = idx >> 3, chunk = idx & 7;  // chunk = 2 complex = 4 real columns
+        const float4 a = *reinterpret_cast<const float4 *>(sm + (raw_a - sbase) + i * 128 + chunk * 16);
+        const float4 re = make_float4(a.x, -a.y, a.z, -a.w);
+        const float4 im = make_float4(a.y, a.x, a.w, a.z);
+        const float4 reh = tf32x4(re), imh = tf32x4(im);
+        const float4 rel = tf32x4(sub4(re, reh)), iml = tf32x4(sub4(im, imh));
+        const uint32_t o0 = sw128(2 * i, chunk), o1 = sw128(2 * i + 1, chunk);
+        *reinterpret_cast<float4 *>(sm + (st.a_hi - sbase) + o0) = reh;
+        *reinterpret_cast<float4 *>(sm + (st.a_lo - sbase) + o0) = rel;
+        *reinterpret_cast<float4 *>(sm + (st.a_hi - sbase) + o1) = imh;
+        *reinterpret_cast<float4 *>(sm + (st.a_lo - sbase) + o1) = iml;
+    }
+    for (int idx = threadIdx.x; idx < np * 8; idx += blockDim.x) {
         const int q = idx >> 3, chunk = idx & 7;
-        const int k = k0 + chunk * 2;
-        float2 a0 = make_float2(0.f, 0.f), a1 = a0;
-        if (q < g.N) {
-            const float2 *xr = X + (int64_t)q * g.ldx;
-            if (k < kend) a0 = xr[k];
-            if (k + 1 < kend) a1 = xr[k + 1];
-        }
-        const float4 v = make_float4(a0.x, a0.y, a1.x, a1.y);
-        const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
-        const float4 l =
-            make_float4(tf32_rna(v.x - h.x), tf32_rna(v.y - h.y), tf32_rna(v.z - h.z), tf32_rna(v.w - h.w));
+        const float4 v = *reinterpret_cast<const float4 *>(sm + (raw_x - sbase) + q * 128 + chunk * 16);
+        const float4 h = tf32x4(v), l = tf32x4(sub4(v, h));
         const uint32_t o = sw128(q, chunk);
-        *reinterpret_cast<float4 *>(smem + (st.x_hi - sbase) + o) = h;
-        *reinterpret_cast<float4 *>(smem + (st.x_lo - sbase) + o) = l;
+        *reinterpret_cast<float4 *>(sm + (st.x_hi - sbase) + o) = h;
+        *reinterpret_cast<float4 *>(sm + (st.x_lo - sbase) + o) = l;
     }
 }
 
@@ -205,15 +222,36 @@ __global__ void __launch_bounds__(TC_THREADS) k_cgemm_tc(CgemmArgs g) {
     const uint32_t tmem = tmem_base;
     const uint32_t idesc = idesc_tf32(g.np);
 
+    const float2 *A = g.A + (int64_t)p * g.strideA;
+    const float2 *X = g.X + (int64_t)p * g.strideX;
+    const uint32_t opbytes = (uint32_t)TC_NST * (2 * 128 * 128 + 2 * (uint32_t)g.np * 128);
+    const uint32_t rawa_sz = TC_MC * 128, rawx_sz = (uint32_t)g.np * 128;
+    const uint32_t raw0 = sbase + opbytes;
+    auto raw_a = [&](int r) { return raw0 + (uint32_t)r * (rawa_sz + rawx_sz); };
+    const int nraw = g.nraw;
+    for (int r = 0; r < nraw - 1; ++r) {  // prologue: k-blocks 0 .. nraw-2 in flight
+        if (r < nkb) raw_issue(g, A, X, m0, kbeg + r * TC_KC, kend, raw_a(r), raw_a(r) + rawa_sz);
+        cp_async_commit();
+    }
     for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % TC_NST;
-        if (kb >= TC_NST) {  // stage s is free once the MMAs of k-block kb - NST are done
+        {  // keep nraw - 1 k-blocks ahead in flight
+            const int kn = kb + nraw - 1;
+            if (kn < nkb) {
+                const int r = kn % nraw;
+                raw_issue(g, A, X, m0, kbeg + kn * TC_KC, kend, raw_a(r), raw_a(r) + rawa_sz);
+            }
+            cp_async_commit();
+        }
+        if (nraw == 3) cp_async_wait<2>(); else cp_async_wait<1>();  // k-block kb has landed (this thread)
+        if (kb >= TC_NST) {  // operand stage s is free once the MMAs of k-block kb - NST are done
             const bool ok = mbar_wait_bounded(&done[s], (uint32_t)(((kb / TC_NST) - 1) & 1), TC_WAIT);
             if (!ok) fail = 1;
         }
-        if (__syncthreads_or(fail)) break;
+        if (__syncthreads_or(fail)) break;  // also makes every thread's raw copies visible
         const Stage st = stage_at(sbase, s, g.np);
-        stage_load(g, p, m0, kbeg + kb * TC_KC, kend, st, smem, sbase);
+        const int r = kb % nraw;
+        stage_transform(smem, sbase, raw_a(r), raw_a(r) + rawa_sz, g.np, st);
         fence_proxy_async();  // generic-proxy stores -> visible to the tensor core
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -230,6 +268,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cgemm_tc(CgemmArgs g) {
             mma_commit(&done[s]);
         }
     }
+    cp_async_wait<0>();
     // wait for the last commit (covers every earlier MMA)
     if (!fail && nkb > 0) {
         const int kb = nkb - 1;
@@ -264,7 +303,17 @@ __global__ void __launch_bounds__(TC_THREADS) k_cgemm_tc(CgemmArgs g) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols) : "memory");
 }
 
-size_t cgemm_smem_bytes(int np) { return (size_t)TC_NST * (2 * 128 * 128 + 2 * (size_t)np * 128) + 1024; }
+static size_t op_bytes(int np) { return (size_t)TC_NST * (2 * 128 * 128 + 2 * (size_t)np * 128); }
+static size_t raw_bytes(int np, int nraw) { return (size_t)nraw * ((size_t)TC_MC * 128 + (size_t)np * 128); }
+constexpr size_t kSmemCap = 227 * 1024 - 2048;  // per-block limit minus static shared memory
+
+size_t cgemm_smem_bytes(int np) { return op_bytes(np) + raw_bytes(np, 2) + 1024; }
+
+bool cgemm_fits(int n) {
+    int np = (n + 15) / 16 * 16;
+    if (np < 32) np = 32;
+    return n >= 1 && n <= 256 && cgemm_smem_bytes(np) <= kSmemCap;
+}
 
 ztoep_status_t launch_cgemm_tc(CgemmArgs g, int nprob, cudaStream_t s) {
     if (g.N < 1 || g.N > 256 || g.M < 1 || g.K < 1 || nprob < 1) return ZTOEP_ERR_ARG;
@@ -275,13 +324,14 @@ ztoep_status_t launch_cgemm_tc(CgemmArgs g, int nprob, cudaStream_t s) {
     g.tmem_cols = cols;
     if (g.kchunk <= 0) g.kchunk = g.K;
     g.kchunk = (g.kchunk + TC_KC - 1) / TC_KC * TC_KC;
-    const size_t smem = cgemm_smem_bytes(g.np);
+    g.nraw = op_bytes(g.np) + raw_bytes(g.np, 3) + 1024 <= kSmemCap ? 3 : 2;
+    const size_t smem = op_bytes(g.np) + raw_bytes(g.np, g.nraw) + 1024;
     static bool attr = false;
     if (!attr) {
-        ZT_CUDA(cudaFuncSetAttribute(k_cgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        ZT_CUDA(cudaFuncSetAttribute(k_cgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap));
         attr = true;
     }
-    if (smem > 200 * 1024) return ZTOEP_ERR_UNSUPPORTED;
+    if (smem > kSmemCap) return ZTOEP_ERR_UNSUPPORTED;
     dim3 grid((g.M + TC_MC - 1) / TC_MC, (g.K + g.kchunk - 1) / g.kchunk, nprob);
     KScope ks(K_TENSOR, s);
     k_cgemm_tc<<<grid, TC_THREADS, smem, s>>>(g);

@@ -18,11 +18,12 @@ struct CgemmArgs {
     int64_t ldc_q, ldc_m, strideC, strideCk;
     int M, K, N;     // complex sizes; N <= 256
     int kchunk;      // complex k per CTA (0 = all of K); partial sums per split
-    int np, tmem_cols;  // set by the launcher
+    int np, tmem_cols, nraw;  // set by the launcher
     int *err;        // device error word (bounded waits)
 };
 
 size_t cgemm_smem_bytes(int np);
+bool cgemm_fits(int n);  // a GEMM with n right-hand sides fits in shared memory
 ztoep_status_t launch_cgemm_tc(CgemmArgs g, int nprob, cudaStream_t s);
 
 // Number of K splits the launcher uses for a given K and chunk.

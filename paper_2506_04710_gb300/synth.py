@@ -278,3 +278,59 @@ def serving_requests(n: int = 2000, rate: float = 50.0, seed: int = 0,
     nrhs = 1 + np.minimum((u[:, 3] * max_rhs).astype(int), max_rhs - 1)
     rseed = (u[:, 4] * (1 << 31)).astype(np.int64) + 1000
     return [(float(t[k]), int(nx[k]), int(b[k]), int(nrhs[k]), int(rseed[k])) for k in range(n)]
+
+
+# ---------------------------------------------------------------- device-side generation
+# The same recipe evaluated with torch on a CUDA device, for request streams
+# whose host generation would take longer than the arrival interval.  Draws
+# come from the same SplitMix64 streams (on the host, O(b) numbers); the
+# Green's function values agree with the NumPy ones to rounding.
+
+def _green_torch(R):
+    import torch
+    Rp = torch.clamp(R, min=R_MIN)
+    return torch.exp(-1j * K0 * Rp.to(torch.complex128)) / (4.0 * math.pi * Rp)
+
+
+def make_problem_device(nx: int, ny: int, b: int, n_edge: int, seed: int, nrhs: int, device="cuda",
+                        chunk_elems: int = 1 << 26) -> dict:
+    """Square-cell array with edge points on its perimeter and plane-wave RHS,
+    as torch tensors on `device`: T [2ny-1][2nx-1][b][b], B [E][N_T], C [E][E],
+    V [nrhs][N] (complex128)."""
+    import torch
+    pts_np = basis_points(seed, b)
+    pts = torch.from_numpy(pts_np).to(device)
+    dxs = pts[:, None, 0] - pts[None, :, 0]
+    dys = pts[:, None, 1] - pts[None, :, 1]
+    p = torch.arange(-(nx - 1), nx, device=device, dtype=torch.float64) * PERIOD
+    q = torch.arange(-(ny - 1), ny, device=device, dtype=torch.float64) * PERIOD
+    dx = dxs[None, None] + p[None, :, None, None]
+    dy = dys[None, None] + q[:, None, None, None]
+    T = _green_torch(torch.sqrt(dx * dx + dy * dy))
+    idx = torch.arange(b, device=device)
+    T[ny - 1, nx - 1, idx, idx] += DIAG
+    edge_np = perimeter_points(0.0, 0.0, nx * PERIOD, ny * PERIOD, n_edge)
+    pos_np = toeplitz_positions(pts_np, nx, ny)
+    pos = torch.from_numpy(np.ascontiguousarray(pos_np)).to(device)
+    edge = torch.from_numpy(edge_np).to(device)
+    nt = pos.shape[0]
+    B = torch.empty((n_edge, nt), dtype=torch.complex128, device=device)
+    rows = max(1, chunk_elems // max(1, nt))
+    for e0 in range(0, n_edge, rows):
+        e1 = min(n_edge, e0 + rows)
+        ddx = edge[e0:e1, None, 0] - pos[None, :, 0]
+        ddy = edge[e0:e1, None, 1] - pos[None, :, 1]
+        B[e0:e1] = _green_torch(torch.sqrt(ddx * ddx + ddy * ddy))
+    ddx = edge[:, None, 0] - edge[None, :, 0]
+    ddy = edge[:, None, 1] - edge[None, :, 1]
+    C = _green_torch(torch.sqrt(ddx * ddx + ddy * ddy))
+    C[torch.arange(n_edge, device=device), torch.arange(n_edge, device=device)] += DIAG
+    u = uniform(seed, STREAM_ANGLES, 2 * nrhs).reshape(nrhs, 2)
+    theta = u[:, 0] * (math.pi / 3.0)
+    phi = u[:, 1] * (2.0 * math.pi)
+    kx = torch.from_numpy(K0 * np.sin(theta) * np.cos(phi)).to(device)
+    ky = torch.from_numpy(K0 * np.sin(theta) * np.sin(phi)).to(device)
+    allpos = torch.cat([pos, edge])
+    ph = kx[:, None] * allpos[None, :, 0] + ky[:, None] * allpos[None, :, 1]
+    V = torch.exp(1j * ph.to(torch.complex128))
+    return dict(nx=nx, ny=ny, b=b, n_edge=n_edge, T=T.contiguous(), B=B, C=C.contiguous(), V=V.contiguous())

@@ -62,6 +62,30 @@ class PlanInfo(ctypes.Structure):
                 ("resident_bytes", ctypes.c_size_t), ("dense_bytes", ctypes.c_size_t)]
 
 
+class SchedOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("workers", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("fake_backend", ctypes.c_int32), ("fake_us", ctypes.c_int64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("desc", Desc), ("inputs_on_device", ctypes.c_int32), ("plan_key", ctypes.c_uint64),
+                ("T", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p), ("nrhs", ctypes.c_int32),
+                ("V", ctypes.c_void_p), ("X", ctypes.c_void_p), ("opts", SolveOpts),
+                ("info", ctypes.POINTER(SolveInfo))]
+
+
+class RequestState(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("plan_reused", ctypes.c_int32),
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class SchedStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("max_in_flight", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
+                ("resident_plan_bytes", ctypes.c_size_t), ("plans_built", ctypes.c_int64),
+                ("plans_reused", ctypes.c_int64), ("plans_evicted", ctypes.c_int64)]
+
+
 _lib = None
 c_p = ctypes.c_void_p
 c_i32 = ctypes.c_int32
@@ -69,7 +93,9 @@ c_i32 = ctypes.c_int32
 EXPORTS = ["ztoep_default_opts", "ztoep_plan", "ztoep_matvec", "ztoep_solve", "ztoep_solve_host",
            "ztoep_forward_spectrum", "ztoep_plan_spectrum", "ztoep_plan_get_info", "ztoep_footprint",
            "ztoep_plan_destroy", "ztoep_status_string", "ztoep_version", "ztoep_launch_count",
-           "ztoep_timing_enable", "ztoep_timing_reset", "ztoep_timing_read", "ztoep_edge_product_noalloc"]
+           "ztoep_timing_enable", "ztoep_timing_reset", "ztoep_timing_read", "ztoep_edge_product_noalloc",
+           "ztoep_sched_create", "ztoep_sched_submit", "ztoep_sched_poll", "ztoep_sched_wait",
+           "ztoep_sched_get_stats", "ztoep_sched_destroy"]
 
 K_FFT, K_BLOCKPROD, K_EDGE, K_ARNOLDI, K_MISC, K_TENSOR = range(6)
 
@@ -108,6 +134,18 @@ def lib(path: str | None = None):
     L.ztoep_status_string.restype = ctypes.c_char_p
     L.ztoep_version.argtypes = []
     L.ztoep_version.restype = ctypes.c_char_p
+    L.ztoep_sched_create.argtypes = [ctypes.POINTER(SchedOpts), ctypes.POINTER(c_p)]
+    L.ztoep_sched_create.restype = c_i32
+    L.ztoep_sched_submit.argtypes = [c_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_int64)]
+    L.ztoep_sched_submit.restype = c_i32
+    L.ztoep_sched_poll.argtypes = [c_p, ctypes.c_int64, ctypes.POINTER(RequestState)]
+    L.ztoep_sched_poll.restype = c_i32
+    L.ztoep_sched_wait.argtypes = [c_p, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(RequestState)]
+    L.ztoep_sched_wait.restype = c_i32
+    L.ztoep_sched_get_stats.argtypes = [c_p, ctypes.POINTER(SchedStats)]
+    L.ztoep_sched_get_stats.restype = c_i32
+    L.ztoep_sched_destroy.argtypes = [c_p]
+    L.ztoep_sched_destroy.restype = None
     L.ztoep_edge_product_noalloc.argtypes = [c_p, c_i32, c_p, c_p, c_p]
     L.ztoep_edge_product_noalloc.restype = c_i32
     L.ztoep_launch_count.argtypes = []
@@ -248,6 +286,100 @@ def ztoep_timing_read(cls: int) -> tuple[int, float]:
     ms = ctypes.c_double()
     _check(lib().ztoep_timing_read(cls, ctypes.byref(n), ctypes.byref(ms)), "ztoep_timing_read")
     return int(n.value), float(ms.value)
+
+
+def ztoep_sched_create(opts: SchedOpts):
+    h = ctypes.c_void_p()
+    _check(lib().ztoep_sched_create(ctypes.byref(opts), ctypes.byref(h)), "ztoep_sched_create")
+    return h
+
+
+def ztoep_sched_submit(sched, req: Request) -> tuple[int, int]:
+    rid = ctypes.c_int64(-1)
+    st = lib().ztoep_sched_submit(sched, ctypes.byref(req), ctypes.byref(rid))
+    return st, int(rid.value)
+
+
+def ztoep_sched_poll(sched, rid: int) -> RequestState:
+    st = RequestState()
+    _check(lib().ztoep_sched_poll(sched, rid, ctypes.byref(st)), "ztoep_sched_poll")
+    return st
+
+
+def ztoep_sched_wait(sched, rid: int, timeout_ms: int = -1) -> tuple[int, RequestState]:
+    st = RequestState()
+    rc = lib().ztoep_sched_wait(sched, rid, timeout_ms, ctypes.byref(st))
+    return rc, st
+
+
+def ztoep_sched_get_stats(sched) -> SchedStats:
+    st = SchedStats()
+    _check(lib().ztoep_sched_get_stats(sched, ctypes.byref(st)), "ztoep_sched_get_stats")
+    return st
+
+
+def ztoep_sched_destroy(sched) -> None:
+    lib().ztoep_sched_destroy(sched)
+
+
+class Scheduler:
+    """Owner of a serving scheduler; keeps every submitted request's buffers
+    alive until the request is done."""
+
+    def __init__(self, hbm_budget: int, workers: int = 4, device: int = 0, fake_us: int | None = None):
+        o = SchedOpts(hbm_budget, workers, device, 1 if fake_us is not None else 0, fake_us or 0)
+        self.handle = ztoep_sched_create(o)
+        self._keep = {}
+
+    def submit(self, desc_args, T, B, C, V, X, opts: SolveOpts | None = None, plan_key: int = 0,
+               on_device: bool | None = None):
+        """desc_args = (nx, ny, b, n_edge, active, lx, ly); arrays are torch tensors
+        (all on the device or all on the host) or numpy arrays (host)."""
+        import torch
+        desc, keep = make_desc(*desc_args)
+        if on_device is None:
+            on_device = isinstance(V, torch.Tensor) and V.is_cuda
+
+        def ptr(a):
+            if a is None:
+                return None
+            if isinstance(a, torch.Tensor):
+                return ctypes.c_void_p(a.data_ptr())
+            return ctypes.c_void_p(a.ctypes.data)
+
+        nrhs = V.shape[0]
+        info = info_array(nrhs)
+        req = Request(desc, 1 if on_device else 0, plan_key, ptr(T), ptr(B), ptr(C), nrhs, ptr(V), ptr(X),
+                      opts or ztoep_default_opts(), info)
+        st, rid = ztoep_sched_submit(self.handle, req)
+        if st != ZTOEP_OK:
+            raise ZtoepError(st, "ztoep_sched_submit")
+        self._keep[rid] = (keep, T, B, C, V, X, info, req)
+        return rid
+
+    def wait(self, rid: int, timeout_ms: int = -1):
+        rc, st = ztoep_sched_wait(self.handle, rid, timeout_ms)
+        info = self._keep[rid][6]
+        return rc, st, [dict(outer=i.outer, inner_iters=i.inner_iters, status=i.status,
+                             rel_residual=i.rel_residual) for i in info]
+
+    def release(self, rid: int):
+        self._keep.pop(rid, None)
+
+    def stats(self) -> SchedStats:
+        return ztoep_sched_get_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ztoep_sched_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def info_array(nrhs: int):

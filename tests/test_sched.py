@@ -1,0 +1,88 @@
+"""Host logic of the serving scheduler (admission by device-memory footprint,
+FIFO order, resident-plan cache and eviction) with the fake backend: no GPU."""
+import numpy as np
+import pytest
+
+from paper_2506_04710_gb300 import build, ztoep
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+
+
+def dummy():
+    return np.zeros(4, np.complex128)
+
+
+def fp_of(nx, b, e, nrhs):
+    d, _ = ztoep.make_desc(nx, nx, b, e)
+    return ztoep.ztoep_footprint(d, nrhs, 30)
+
+
+def submit(s, nx, b, e, nrhs, key=0):
+    a = dummy()
+    return s.submit((nx, nx, b, e), a, a, a, np.zeros((nrhs, 4), np.complex128), np.zeros((nrhs, 4), np.complex128),
+                    plan_key=key, on_device=False)
+
+
+def test_admission_never_exceeds_budget():
+    fp = fp_of(16, 32, 256, 8)
+    s = ztoep.Scheduler(hbm_budget=int(2.5 * fp), workers=4, fake_us=20000)
+    ids = [submit(s, 16, 32, 256, 8) for _ in range(8)]
+    for i in ids:
+        rc, st, _ = s.wait(i, 10000)
+        assert rc == 0 and st.state == 2 and st.status == 0
+    stats = s.stats()
+    assert stats.completed == 8 and stats.max_in_flight == 2
+    assert stats.peak_bytes <= int(2.5 * fp)
+    s.close()
+
+
+def test_fifo_order_with_one_worker():
+    s = ztoep.Scheduler(hbm_budget=1 << 40, workers=1, fake_us=5000)
+    ids = [submit(s, 8 + k, 32, 64, 1) for k in range(6)]
+    states = [s.wait(i, 10000)[1] for i in ids]
+    q = [st.queue_ms for st in states]
+    assert q == sorted(q)
+    assert all(st.latency_ms >= st.queue_ms for st in states)
+    s.close()
+
+
+def test_concurrency_up_to_workers():
+    s = ztoep.Scheduler(hbm_budget=1 << 40, workers=3, fake_us=30000)
+    ids = [submit(s, 8, 32, 64, 1) for _ in range(9)]
+    for i in ids:
+        s.wait(i, 10000)
+    assert s.stats().max_in_flight == 3
+    s.close()
+
+
+def test_rejects_oversized_and_bad_requests():
+    fp = fp_of(32, 64, 512, 4)
+    s = ztoep.Scheduler(hbm_budget=fp // 2, workers=2, fake_us=1000)
+    with pytest.raises(ztoep.ZtoepError) as e:
+        submit(s, 32, 64, 512, 4)
+    assert e.value.status == ztoep.ZTOEP_ERR_NOMEM
+    with pytest.raises(ztoep.ZtoepError) as e:
+        submit(s, 0, 64, 16, 1)
+    assert e.value.status == ztoep.ZTOEP_ERR_ARG
+    s.close()
+
+
+def test_resident_plans_are_reused_and_evicted_lru():
+    fp = fp_of(16, 32, 256, 4)
+    # room for one running request plus about one idle resident plan
+    s = ztoep.Scheduler(hbm_budget=int(1.6 * fp), workers=1, fake_us=2000)
+    order = [1, 1, 2, 1, 3, 3]
+    states = []
+    for key in order:
+        rid = submit(s, 16, 32, 256, 4, key=key)
+        states.append(s.wait(rid, 10000)[1])
+    st = s.stats()
+    # key 1 survives the admission of key 2 (plan 2 is the LRU victim when key 1
+    # returns), plan 1 is evicted when key 3 comes back
+    assert [x.plan_reused for x in states] == [0, 1, 0, 1, 0, 1]
+    assert st.plans_built == 3 and st.plans_reused == 3 and st.plans_evicted == 2
+    assert st.peak_bytes <= int(1.6 * fp)
+    s.close()
