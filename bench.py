@@ -362,6 +362,109 @@ def run_ours(args, world, rank, local):
     plan.close()
 
 
+SERVE_DESC = ("Poisson stream, mean 50 requests/s: square arrays Nx=Ny ~ U{8..48}, b ~ {32,48,64,96}, "
+              "E = 16 Nx, 1-64 plane-wave RHS, 4 element designs (seeds); solved to rel. residual 1e-8")
+
+
+def serve_stream(args, prec_name, n_req, dev):
+    """Replays the first n_req requests of the stream at their arrival times
+    through the scheduler.  Inputs are generated on the device by the client
+    ahead of arrival (bounded by --serve-input-gb of unconsumed inputs) and
+    freed once the scheduler has built the plan.  Latency = arrival -> the
+    solution is in device memory (scheduler completion)."""
+    import torch
+    from paper_2506_04710_gb300 import synth, ztoep
+    reqs = synth.serving_requests(n=n_req, rate=50.0, seed=0)
+    prec = ztoep.ZTOEP_MIXED if prec_name == "mixed" else ztoep.ZTOEP_FP64
+    sched = ztoep.Scheduler(hbm_budget=int(args.serve_budget_gb * 2**30), workers=args.serve_workers,
+                            device=dev.index or 0)
+    gen = torch.cuda.Stream(dev)
+    cap = args.serve_input_gb * 2**30
+    live = {}  # rid -> input bytes still held
+    ids = []
+    late = []
+
+    def reap():
+        for rid in list(live):
+            if sched.drop_inputs(rid):
+                del live[rid]
+
+    launches0 = ztoep.ztoep_launch_count()
+    t0 = time.perf_counter()
+    for (t_arr, nx, b, nrhs, seed) in reqs:
+        while live and sum(live.values()) > cap:
+            reap()
+            time.sleep(0.001)
+        with torch.cuda.stream(gen):
+            d = synth.make_problem_device(nx, nx, b, 16 * nx, seed, nrhs, device=dev)
+            X = torch.empty_like(d["V"])
+        gen.synchronize()
+        o = ztoep.ztoep_default_opts()
+        o.prec, o.tol = prec, 1e-8
+        wait = t_arr - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        key = (nx << 40) | (b << 24) | (seed & 0xFFFFFF) | (1 << 62)
+        t_sub = time.perf_counter() - t0
+        rid = sched.submit((nx, nx, b, 16 * nx), d["T"], d["B"], d["C"], d["V"], X, opts=o, plan_key=key,
+                           on_device=True)
+        live[rid] = sum(t.numel() * 16 for t in (d["T"], d["B"], d["C"]))
+        del d, X
+        ids.append((rid, t_arr, nrhs, nx, b))
+        late.append(max(0.0, t_sub - t_arr))
+        reap()
+    lat, worst_res, fails, rhs_total = [], 0.0, 0, 0
+    for (rid, t_arr, nrhs, nx, b), lt in zip(ids, late):
+        rc, st, info = sched.wait(rid, 600000)
+        if rc != 0 or st.status != 0:
+            fails += 1
+        lat.append(lt * 1e3 + st.latency_ms)
+        worst_res = max(worst_res, max(i["rel_residual"] for i in info))
+        rhs_total += nrhs
+        sched.release(rid)
+    t_end = time.perf_counter() - t0
+    stats = sched.stats()
+    launches = ztoep.ztoep_launch_count() - launches0
+    sched.close()
+    lat.sort()
+    span = t_end - reqs[0][0]
+    return {"requests": n_req, "offered_rate_per_s": 50.0, "span_s": span,
+            "requests_per_s": n_req / span, "rhs_solves_per_s": rhs_total / span, "rhs_total": rhs_total,
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "max": lat[-1]},
+            "failed": fails, "worst_rel_residual": worst_res,
+            "max_in_flight": int(stats.max_in_flight), "peak_bytes": int(stats.peak_bytes),
+            "plans_built": int(stats.plans_built), "plans_reused": int(stats.plans_reused),
+            "plans_evicted": int(stats.plans_evicted), "gpu_launches": int(launches),
+            "workers": args.serve_workers, "budget_gb": args.serve_budget_gb}
+
+
+def run_serve(args, world, rank, local):
+    """Serving benchmark: the request stream through the scheduler, mixed
+    precision, then the FP64 plain path on a shorter prefix of the same stream."""
+    import torch
+    from paper_2506_04710_gb300 import build as libbuild
+    libbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank != 0:
+        return
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(getattr(props, "uuid", local))
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
+        gpu_id = "GPU-" + gpu_id
+    serve_stream(args, "mixed", 4, dev)  # warm-up: library, generator, allocator
+    clocks = Clocks(gpu_id)
+    mixed = serve_stream(args, "mixed", args.serve, dev)
+    fp64 = serve_stream(args, "fp64", args.serve_fp64, dev) if args.serve_fp64 > 0 else None
+    clk = clocks.stop()
+    line = {"metric": METRIC, "mode": "serving", "value": mixed["rhs_solves_per_s"], "unit": "RHS solves/s",
+            "higher_is_better": True, "n_gpus": 1, "dtype": "c64 products + f64 refinement",
+            "data": "synthetic", "config": {"workload": SERVE_DESC, "requests": args.serve},
+            "mixed": mixed, "fp64_plain": fp64, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -372,9 +475,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the solver loops from the host (for profilers; slower)")
+    ap.add_argument("--serve", type=int, default=0,
+                    help="serving mode: replay this many requests of the Poisson stream")
+    ap.add_argument("--serve-fp64", type=int, default=0, help="requests replayed through the FP64 path")
+    ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=96.0)
+    ap.add_argument("--serve-input-gb", type=float, default=32.0)
     args = ap.parse_args()
     world, rank, local = dist_setup()
-    if args.impl == "reference":
+    if args.serve > 0:
+        run_serve(args, world, rank, local)
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
         run_ours(args, world, rank, local)

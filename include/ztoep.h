@@ -272,12 +272,14 @@ typedef struct {
     ztoep_solve_opts_t opts;
     ztoep_solve_info_t *info; /* host [nrhs] or NULL */
 } ztoep_request_t;
-/* The request's buffers must stay valid until it completes. */
+/* V and X must stay valid until the request completes; T, B and C until it
+ * reports inputs_consumed (or completes). */
 
 typedef struct {
     int32_t state;           /* 0 queued, 1 running, 2 done */
     int32_t status;          /* ztoep_status_t of the solve (when done) */
     int32_t plan_reused;     /* the resident plan of plan_key was used */
+    int32_t inputs_consumed; /* 1 once the plan exists: T, B and C are no longer read */
     double queue_ms;         /* submit -> start */
     double latency_ms;       /* submit -> done */
 } ztoep_request_state_t;

@@ -32,6 +32,7 @@ struct Req {
     int state = 0;          // 0 queued, 1 running, 2 done
     int status = 0;
     int reused = 0;
+    int consumed = 0;        // the plan exists: T, B, C no longer read
     bool holds_ref = false;  // holds a reference on the resident plan of its key
     Clock::time_point t_submit, t_start, t_done;
 };
@@ -103,6 +104,7 @@ struct ztoep_sched_s {
             std::this_thread::sleep_for(std::chrono::microseconds(o.fake_us));
             std::lock_guard<std::mutex> lk(mu);
             q->status = ZTOEP_OK;
+            q->consumed = 1;
             if (r.plan_key) {
                 auto it = plans.find(r.plan_key);
                 if (it != plans.end()) {
@@ -136,7 +138,10 @@ struct ztoep_sched_s {
             }
         }
         ztoep_status_t st = ZTOEP_OK;
-        if (!plan) {
+        if (plan) {
+            std::lock_guard<std::mutex> lk(mu);
+            q->consumed = 1;
+        } else {
             if (r.inputs_on_device) {
                 st = ztoep_plan(&r.desc, r.T, r.B, r.C, s, &plan);
             } else {  // stage the host blocks on the device for the plan build
@@ -162,6 +167,12 @@ struct ztoep_sched_s {
                 cudaFree(dB);
                 cudaFree(dC);
             }
+        }
+        if (!from_cache) {
+            // ztoep_plan is stream-ordered: the blocks are read once the stream passes it
+            if (st == ZTOEP_OK && r.inputs_on_device) cudaStreamSynchronize(s);
+            std::lock_guard<std::mutex> lk(mu);
+            q->consumed = 1;
         }
         if (st == ZTOEP_OK) {
             ztoep_solve_opts_t so = r.opts;
@@ -278,6 +289,7 @@ static void fill_state(const Req *q, ztoep_request_state_t *st) {
     st->state = q->state;
     st->status = q->state == 2 ? q->status : 0;
     st->plan_reused = q->reused;
+    st->inputs_consumed = q->consumed || q->state == 2;
     st->queue_ms = q->state >= 1 ? ms_between(q->t_submit, q->t_start) : 0.0;
     st->latency_ms = q->state == 2 ? ms_between(q->t_submit, q->t_done) : 0.0;
 }

@@ -267,16 +267,18 @@ def config_problem(key: str, seed: int = 0) -> tuple[Problem, float]:
 
 
 def serving_requests(n: int = 2000, rate: float = 50.0, seed: int = 0,
-                     sizes=(8, 48), bases=(32, 48, 64, 96), max_rhs: int = 64):
+                     sizes=(8, 48), bases=(32, 48, 64, 96), max_rhs: int = 64, designs: int = 4):
     """Poisson stream: (arrival_s, nx, b, nrhs, req_seed).  Square arrays,
-    E = 16*Nx edge unknowns, plane-wave RHS."""
+    E = 16*Nx edge unknowns, plane-wave RHS.  The request seed (which fixes
+    the element geometry, hence the generating blocks) is one of `designs`
+    values, so requests for the same (Nx, b, seed) design share a plan."""
     u = uniform(seed, STREAM_REQUESTS, 5 * n).reshape(n, 5)
     gaps = -np.log1p(-u[:, 0]) / rate
     t = np.cumsum(gaps)
     nx = sizes[0] + np.minimum((u[:, 1] * (sizes[1] - sizes[0] + 1)).astype(int), sizes[1] - sizes[0])
     b = np.array(bases)[np.minimum((u[:, 2] * len(bases)).astype(int), len(bases) - 1)]
     nrhs = 1 + np.minimum((u[:, 3] * max_rhs).astype(int), max_rhs - 1)
-    rseed = (u[:, 4] * (1 << 31)).astype(np.int64) + 1000
+    rseed = 1000 + np.minimum((u[:, 4] * designs).astype(np.int64), designs - 1)
     return [(float(t[k]), int(nx[k]), int(b[k]), int(nrhs[k]), int(rseed[k])) for k in range(n)]
 
 

@@ -76,7 +76,7 @@ class Request(ctypes.Structure):
 
 class RequestState(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("plan_reused", ctypes.c_int32),
-                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+                ("inputs_consumed", ctypes.c_int32), ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
 
 
 class SchedStats(ctypes.Structure):
@@ -362,6 +362,20 @@ class Scheduler:
         info = self._keep[rid][6]
         return rc, st, [dict(outer=i.outer, inner_iters=i.inner_iters, status=i.status,
                              rel_residual=i.rel_residual) for i in info]
+
+    def poll(self, rid: int) -> RequestState:
+        return ztoep_sched_poll(self.handle, rid)
+
+    def drop_inputs(self, rid: int) -> bool:
+        """Forget the request's T, B, C once the scheduler reports them consumed;
+        returns whether it did."""
+        k = self._keep.get(rid)
+        if k is None or k[1] is None:
+            return True
+        if not ztoep_sched_poll(self.handle, rid).inputs_consumed:
+            return False
+        self._keep[rid] = (k[0], None, None, None) + k[4:]
+        return True
 
     def release(self, rid: int):
         self._keep.pop(rid, None)

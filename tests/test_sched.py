@@ -86,3 +86,15 @@ def test_resident_plans_are_reused_and_evicted_lru():
     assert st.plans_built == 3 and st.plans_reused == 3 and st.plans_evicted == 2
     assert st.peak_bytes <= int(1.6 * fp)
     s.close()
+
+
+def test_inputs_released_once_consumed():
+    s = ztoep.Scheduler(hbm_budget=1 << 40, workers=1, fake_us=30000)
+    a = submit(s, 8, 32, 64, 1)
+    b = submit(s, 8, 32, 64, 1)
+    assert not s.drop_inputs(b)  # still queued behind a: its blocks are needed
+    s.wait(b, 10000)
+    assert s.drop_inputs(a) and s.drop_inputs(b)
+    assert s._keep[b][1] is None and s._keep[b][4] is not None  # V, X kept
+    assert s.poll(b).inputs_consumed == 1
+    s.close()
