@@ -131,7 +131,7 @@ struct SolveGraph {
     int prec = -1, nrhs = 0, m = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    uint64_t k_fixed = 0, k_sweep = 0, k_restart = 0, k_iter = 0, k_first_product = 0;  // kernels per part
+    uint64_t k_fixed = 0, k_sweep = 0, k_restart = 0, k_iter = 0, k_first_product = 0, k_reorth = 0;  // kernels per part
 };
 
 struct PlanImpl;

@@ -55,6 +55,7 @@ struct SolveCtl {
     int outer_bodies;    // executions of the sweep body (for launch accounting)
     int inner_bodies;    // executions of the iteration body
     int restart_bodies;  // executions of the restart body
+    int reorth_bodies;   // executions of the second Gram-Schmidt pass
     int cond_first, cond_sweep, cond_restart, cond_iter;  // loop decisions (read by the host-driven mode)
     double tol, inner_tol;
     long long timeout_ns;
@@ -80,11 +81,18 @@ struct GArgs {
     int64_t N;
     int cap, m, nchunk, pstride, nrhs;
     int mixed;
+    int graph;                             // running inside the solve graph
+    cudaGraphConditionalHandle h_reorth;   // second Gram-Schmidt pass needed by some RHS
 };
 
 __device__ __forceinline__ double2 shfl_xor2(double2 v, int o) {
     v.x = __shfl_xor_sync(0xffffffffu, v.x, o);
     v.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+    return v;
+}
+__device__ __forceinline__ double2 shfl_idx2(double2 v, int src) {
+    v.x = __shfl_sync(0xffffffffu, v.x, src);
+    v.y = __shfl_sync(0xffffffffu, v.y, src);
     return v;
 }
 
@@ -155,17 +163,44 @@ __device__ __forceinline__ bool last_cta(unsigned *cnt, unsigned total) {
     return s_last;
 }
 
-// In the last CTA: out[k] = sum_c part[c][k] for k < K (one warp per k).
-__device__ __forceinline__ void reduce_partials(const double2 *part, int nchunk, int pstride, int K, double2 *out) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = warp; k < K; k += nw) {
-        double2 s = make_double2(0, 0);
-        for (int c = lane; c < nchunk; c += 32) s = s + __ldcg(part + (int64_t)c * pstride + k);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s = s + shfl_xor2(s, o);
-        if (lane == 0) out[k] = s;
+// In the last CTA: out[k] = sum_c part[c][k] for k < K.  The threads form G
+// groups of KP (K rounded up to a power of two, at most blockDim); thread
+// (g, kk) adds chunks g, g+G, g+2G, ... of column kb+kk in four independent
+// accumulators (so several loads are in flight), and the G group sums are then
+// added by a pairwise tree.  The order depends only on nchunk, K and blockDim,
+// never on timing or on the other RHS of the batch.
+__device__ void reduce_partials(const double2 *part, int nchunk, int pstride, int K, double2 *out) {
+    __shared__ double2 red2[256];
+    int KP = 1;
+    while (KP < K && KP < (int)blockDim.x) KP <<= 1;
+    const int G = blockDim.x / KP;
+    const int kk = threadIdx.x % KP, g = threadIdx.x / KP;
+    for (int kb = 0; kb < K; kb += KP) {
+        const int k = kb + kk;
+        double2 s0 = make_double2(0, 0), s1 = s0, s2 = s0, s3 = s0;
+        if (k < K) {
+            int c = g;
+            for (; c + 3 * G < nchunk; c += 4 * G) {
+                const double2 a0 = __ldcg(part + (int64_t)c * pstride + k);
+                const double2 a1 = __ldcg(part + (int64_t)(c + G) * pstride + k);
+                const double2 a2 = __ldcg(part + (int64_t)(c + 2 * G) * pstride + k);
+                const double2 a3 = __ldcg(part + (int64_t)(c + 3 * G) * pstride + k);
+                s0 = s0 + a0;
+                s1 = s1 + a1;
+                s2 = s2 + a2;
+                s3 = s3 + a3;
+            }
+            for (; c < nchunk; c += G) s0 = s0 + __ldcg(part + (int64_t)c * pstride + k);
+        }
+        red2[threadIdx.x] = (s0 + s1) + (s2 + s3);
+        __syncthreads();
+        for (int h = G >> 1; h > 0; h >>= 1) {
+            if (g < h) red2[threadIdx.x] = red2[threadIdx.x] + red2[threadIdx.x + h * KP];
+            __syncthreads();
+        }
+        if (threadIdx.x < KP && kb + (int)threadIdx.x < K) out[kb + threadIdx.x] = red2[threadIdx.x];
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 __device__ __forceinline__ double2 *basis(const GArgs &a, int k, int rr) {
@@ -257,50 +292,61 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_residual(GArgs a, i
 }
 
 // ---------------------------------------------------------------- Arnoldi
-// Hessenberg column j from the Gram-Schmidt coefficients h and beta_{j+1},
-// Givens rotations, residual estimate, end-of-cycle least squares.  One thread.
-__device__ void finalize_column(const GArgs &a, int rr, int j, const double2 *h, double beta) {
+// Hessenberg column j from the Gram-Schmidt coefficients hs[0..j] (shared
+// memory, rotated in place) and beta_{j+1}: the earlier Givens rotations, the
+// new one, the residual estimate and the end-of-cycle decision.  Called by
+// every thread of one CTA; the rotation chain runs in one thread on shared
+// copies of (c_i, s_i).  The least squares R y = g is solved at the update
+// (k_update_d).
+__device__ void finalize_column(const GArgs &a, int rr, int j, double2 *hs, double beta) {
+    __shared__ double2 s_cs[128], s_sn[128];
     const int m = a.m;
     int *st = a.st + rr * ST_STRIDE;
     double *nm = a.nrm + rr * NM_STRIDE;
     double2 *H = a.H + (int64_t)rr * (m + 1) * m;
     double2 *cs = a.cs + (int64_t)rr * m, *sn = a.sn + (int64_t)rr * m;
     double2 *g = a.g + (int64_t)rr * (m + 1);
-    a.beta[(int64_t)rr * (m + 1) + j + 1] = beta;
-    for (int i = 0; i <= j; ++i) H[i * m + j] = h[i];
-    for (int i = 0; i < j; ++i) {
-        const double2 p = H[i * m + j], q = H[(i + 1) * m + j];
-        H[i * m + j] = cmulc(cs[i], p) + cmulc(sn[i], q);
-        H[(i + 1) * m + j] = cmul(cs[i], q) - cmul(sn[i], p);
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        s_cs[i] = __ldcg(cs + i);
+        s_sn[i] = __ldcg(sn + i);
     }
-    const double2 p = H[j * m + j];
-    const double d = sqrt(cabs2(p) + beta * beta);
-    if (d > 0) {
-        cs[j] = cscale(p, 1.0 / d);
-        sn[j] = make_double2(beta / d, 0);
-    } else {
-        cs[j] = make_double2(1, 0);
-        sn[j] = make_double2(0, 0);
-    }
-    H[j * m + j] = make_double2(d, 0);
-    const double2 gj = g[j];
-    g[j + 1] = make_double2(-sn[j].x * gj.x, -sn[j].x * gj.y);
-    g[j] = cmulc(cs[j], gj);
-    st[ST_JLEN] = j + 1;
-    st[ST_ITERS] += 1;
-    const double res = sqrt(cabs2(g[j + 1]));
-    const bool end = !(res > nm[NM_TARGET]) || !(beta > 0) || (j + 1 == m) || (st[ST_ITERS] >= a.ctl->max_iter);
-    if (end) {
-        double2 *y = a.y + (int64_t)rr * m;  // R y = g, (j+1) x (j+1) upper triangular
-        for (int i = j; i >= 0; --i) {
-            double2 s = g[i];
-            for (int l = i + 1; l <= j; ++l) s = s - cmul(H[i * m + l], y[l]);
-            const double2 rii = H[i * m + i];
-            y[i] = (rii.x != 0.0 || rii.y != 0.0) ? cdiv(s, rii) : make_double2(0, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.beta[(int64_t)rr * (m + 1) + j + 1] = beta;
+        double2 p = hs[0];
+        for (int i = 0; i < j; ++i) {
+            const double2 q = hs[i + 1];
+            hs[i] = cmulc(s_cs[i], p) + cmulc(s_sn[i], q);
+            p = cmul(s_cs[i], q) - cmul(s_sn[i], p);
         }
-        st[ST_ACTIVE] = 0;
-        st[ST_PENDING] = 1;
+        const double d = sqrt(cabs2(p) + beta * beta);
+        double2 c, sj;
+        if (d > 0) {
+            c = cscale(p, 1.0 / d);
+            sj = make_double2(beta / d, 0);
+        } else {
+            c = make_double2(1, 0);
+            sj = make_double2(0, 0);
+        }
+        cs[j] = c;
+        sn[j] = sj;
+        hs[j] = make_double2(d, 0);
+        const double2 gj = __ldcg(g + j);
+        const double2 gn = make_double2(-sj.x * gj.x, -sj.x * gj.y);
+        g[j + 1] = gn;
+        g[j] = cmulc(c, gj);
+        st[ST_JLEN] = j + 1;
+        st[ST_ITERS] += 1;
+        const double res = sqrt(cabs2(gn));
+        const bool end =
+            !(res > nm[NM_TARGET]) || !(beta > 0) || (j + 1 == m) || (st[ST_ITERS] >= a.ctl->max_iter);
+        if (end) {
+            st[ST_ACTIVE] = 0;
+            st[ST_PENDING] = 1;
+        }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) H[i * m + j] = hs[i];
 }
 
 // Partial dot products <u_k, w> for k in [k0, k0+8) (k <= j) plus, when
@@ -349,6 +395,13 @@ __device__ __forceinline__ void dots_group(const GArgs &a, int rr, int j, int k0
     __syncthreads();
 }
 
+// Lowest RHS index that asked for a second Gram-Schmidt pass (-1 if none).
+__device__ __forceinline__ int first_reorth_rhs(const GArgs &a) {
+    for (int rr = 0; rr < a.nrhs; ++rr)
+        if (a.st[rr * ST_STRIDE + ST_ACTIVE] && a.st[rr * ST_STRIDE + ST_REORTH]) return rr;
+    return -1;
+}
+
 // Gram-Schmidt dots.
 // PASS 1: w = (product of u_j) / beta_j is formed (from the FP32 or FP64
 //   product) and stored as u_{j+1}; h1_k = <v_k, w> and ||w||.  The last CTA
@@ -391,6 +444,7 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(GArg
             }
         }
     }
+    if (PASS == 2 && blockIdx.x == 0 && threadIdx.x == 0 && rr == first_reorth_rhs(a)) a.ctl->reorth_bodies += 1;
     const int K = j + 1 + (PASS == 1 ? 1 : 0);
     double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
     for (int k0 = 0; k0 < K; k0 += 8) dots_group<ELEM>(a, rr, j, k0, PASS == 1, wv, base, part, red);
@@ -403,17 +457,23 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(GArg
         tot[k] = hk;
     }
     __syncthreads();
-    if (PASS == 2 || threadIdx.x != 0) return;
-    const double w2 = tot[j + 1].x;
-    double hsq = 0;
-    for (int k = 0; k <= j; ++k) hsq += cabs2(tot[k]);
-    const double wn2 = w2 - hsq;
-    if (!(wn2 > kReorthEta * kReorthEta * w2)) {  // strong cancellation (or NaN): second pass
-        st[ST_REORTH] = 1;
-        return;
+    if (PASS == 2) return;
+    __shared__ double s_wn2;
+    __shared__ int s_again;
+    if (threadIdx.x == 0) {
+        const double w2 = tot[j + 1].x;
+        double hsq = 0;
+        for (int k = 0; k <= j; ++k) hsq += cabs2(tot[k]);
+        const double wn2 = w2 - hsq;
+        const int again = !(wn2 > kReorthEta * kReorthEta * w2);  // strong cancellation (or NaN)
+        st[ST_REORTH] = again;
+        if (again && a.graph) cudaGraphSetConditional(a.h_reorth, 1u);
+        s_wn2 = wn2;
+        s_again = again;
     }
-    st[ST_REORTH] = 0;
-    finalize_column(a, rr, j, h, sqrt(wn2));
+    __syncthreads();
+    if (s_again) return;  // second pass first
+    finalize_column(a, rr, j, tot, sqrt(s_wn2));
 }
 
 // u_{j+1} <- u_{j+1} - sum_k (h_k / beta_k) u_k and its copy for the next
@@ -442,17 +502,18 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(GArgs
     }
     int k = 0;
     const int64_t vstride = (int64_t)a.cap * a.N;
-    for (; k + 4 <= j + 1; k += 4) {  // 4 basis vectors per step, loads first
+    constexpr int UNR = ELEM == 1 ? 8 : 4;  // basis vectors per step, loads first
+    for (; k + UNR <= j + 1; k += UNR) {
         const double2 *u0 = basis(a, k, rr);
 #pragma unroll
         for (int e = 0; e < ELEM; ++e) {
             const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
             if (idx < a.N) {
-                double2 uv[4];
+                double2 uv[UNR];
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) uv[kk] = u0[kk * vstride + idx];
+                for (int kk = 0; kk < UNR; ++kk) uv[kk] = u0[kk * vstride + idx];
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) wv[e] = wv[e] - cmul(cf[k + kk], uv[kk]);
+                for (int kk = 0; kk < UNR; ++kk) wv[e] = wv[e] - cmul(cf[k + kk], uv[kk]);
             }
         }
     }
@@ -484,13 +545,59 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(GArgs
     if (threadIdx.x == 0) part[(int64_t)blockIdx.x * a.pstride] = make_double2(acc, 0);
     if (!last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk)) return;
     reduce_partials(part, a.nchunk, a.pstride, 1, tot);
-    if (threadIdx.x != 0) return;
     const double wn = sqrt(tot[0].x);
     const double2 *h1 = a.h1 + (int64_t)rr * (a.m + 1);
-    double2 *h2 = a.h2 + (int64_t)rr * (a.m + 1);
-    for (int kk = 0; kk <= j; ++kk) h2[kk] = h1[kk] + h2[kk];  // total coefficients
-    st[ST_REORTH] = 0;
-    finalize_column(a, rr, j, h2, wn);
+    const double2 *h2 = a.h2 + (int64_t)rr * (a.m + 1);
+    for (int kk = threadIdx.x; kk <= j; kk += blockDim.x) cf[kk] = __ldcg(h1 + kk) + __ldcg(h2 + kk);  // totals
+    if (threadIdx.x == 0) st[ST_REORTH] = 0;
+    __syncthreads();
+    finalize_column(a, rr, j, cf, wn);
+}
+
+// Least squares of a finished cycle: R y = g with R the leading jl x jl
+// upper triangle of the rotated Hessenberg matrix; ys[k] = y_k / beta_k.
+// Every CTA of the RHS solves it (the same arithmetic, so the same result):
+// R is staged in shared memory by all threads and one warp runs the
+// column-oriented back substitution (lane l keeps the running right-hand side
+// of row l).  Cycles longer than 32 fall back to one thread reading R from
+// global memory.
+__device__ void cycle_least_squares(const GArgs &a, int rr, int jl, double2 *ys) {
+    __shared__ double2 Rs[32 * 32];
+    const int m = a.m;
+    const double2 *H = a.H + (int64_t)rr * (m + 1) * m;
+    const double2 *g = a.g + (int64_t)rr * (m + 1);
+    const double *beta = a.beta + (int64_t)rr * (m + 1);
+    if (jl <= 32) {
+        for (int idx = threadIdx.x; idx < jl * jl; idx += blockDim.x) {
+            const int i = idx / jl, l = idx - i * jl;
+            if (l >= i) Rs[i * 32 + l] = __ldcg(H + i * m + l);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            double2 sl = lane < jl ? __ldcg(g + lane) : make_double2(0, 0);
+            for (int i = jl - 1; i >= 0; --i) {
+                double2 yi = make_double2(0, 0);
+                if (lane == i) {
+                    const double2 rii = Rs[i * 32 + i];
+                    yi = (rii.x != 0.0 || rii.y != 0.0) ? cdiv(sl, rii) : make_double2(0, 0);
+                    ys[i] = cscale(yi, 1.0 / beta[i]);
+                }
+                yi = shfl_idx2(yi, i);
+                if (lane < i) sl = sl - cmul(Rs[lane * 32 + i], yi);
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        double2 *yv = Rs;  // unused by this path: y_l, l < jl <= 128
+        for (int i = jl - 1; i >= 0; --i) {
+            double2 sacc = __ldcg(g + i);
+            for (int l = i + 1; l < jl; ++l) sacc = sacc - cmul(__ldcg(H + i * m + l), yv[l]);
+            const double2 rii = __ldcg(H + i * m + i);
+            yv[i] = (rii.x != 0.0 || rii.y != 0.0) ? cdiv(sacc, rii) : make_double2(0, 0);
+            ys[i] = cscale(yv[i], 1.0 / beta[i]);
+        }
+    }
+    __syncthreads();
 }
 
 // d <- d + sum_k (y_k / beta_k) u_k for RHS whose cycle produced an update.
@@ -500,10 +607,7 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_update_d(GArgs a) {
     const int *st = a.st + rr * ST_STRIDE;
     if (!st[ST_PENDING]) return;
     const int jl = st[ST_JLEN];
-    const double *beta = a.beta + (int64_t)rr * (a.m + 1);
-    for (int k = threadIdx.x; k < jl; k += blockDim.x)
-        ys[k] = cscale(__ldcg(a.y + (int64_t)rr * a.m + k), 1.0 / beta[k]);
-    __syncthreads();
+    cycle_least_squares(a, rr, jl, ys);
     const int64_t base = (int64_t)blockIdx.x * blockDim.x * ELEM;
 #pragma unroll
     for (int e = 0; e < ELEM; ++e) {
@@ -668,7 +772,10 @@ __global__ void k_iter_ctl(GArgs a, cudaGraphConditionalHandle h_iter, int use_g
     if (any && late) c->timed_out = 1;
     const unsigned cond = (any && c->j < a.m && !late) ? 1u : 0u;
     c->cond_iter = (int)cond;
-    if (use_graph) cudaGraphSetConditional(h_iter, cond);
+    if (use_graph) {
+        cudaGraphSetConditional(h_iter, cond);
+        cudaGraphSetConditional(a.h_reorth, 0u);
+    }
 }
 
 // ---------------------------------------------------------------- workspace
@@ -694,14 +801,15 @@ void free_solve_ws(ztoep_plan_t p) {
 
 // Launch geometry: depends on N only, so a RHS is summed in the same order
 // alone and in any batch.  Small systems: 128 threads x 1 element (enough
-// CTAs to cover every SM); large ones: 256 threads x 4 elements.
+// CTAs to cover every SM while keeping the partial sums of the cross-CTA
+// reductions few); large ones: 256 threads x 4 elements.
 struct Geom {
     int threads, elem;
 };
 static Geom geom_for(int64_t N, int nsm) {
     const int64_t ctas_small = (N + 255) / 256;
     if (ctas_small >= 8LL * nsm) return {256, 4};
-    return {128, 1};
+    return {256, 1};
 }
 
 constexpr int kHostCtlInts = 32;  // host mirror of SolveCtl after st
@@ -768,13 +876,16 @@ template <int ELEM> struct Launch {
         k_residual<ELEM><<<g, t, 0, s>>>(a, first);
         return ok();
     }
-    static ztoep_status_t arnoldi(const GArgs &a, dim3 g, int t, cudaStream_t s) {
+    static ztoep_status_t arnoldi(const GArgs &a, dim3 g, int t, int pass, cudaStream_t s) {
         KScope ks(K_ARNOLDI, s);
-        ks.add(4);
-        k_dots<ELEM, 1><<<g, t, 0, s>>>(a);
-        k_upd<ELEM, 1><<<g, t, 0, s>>>(a);
-        k_dots<ELEM, 2><<<g, t, 0, s>>>(a);
-        k_upd<ELEM, 2><<<g, t, 0, s>>>(a);
+        ks.add(2);
+        if (pass == 1) {
+            k_dots<ELEM, 1><<<g, t, 0, s>>>(a);
+            k_upd<ELEM, 1><<<g, t, 0, s>>>(a);
+        } else {
+            k_dots<ELEM, 2><<<g, t, 0, s>>>(a);
+            k_upd<ELEM, 2><<<g, t, 0, s>>>(a);
+        }
         return ok();
     }
     static ztoep_status_t update_d(const GArgs &a, dim3 g, int t, cudaStream_t s) {
@@ -808,8 +919,9 @@ struct Ops {
         return gm.elem == 4 ? Launch<4>::residual(a, grid, gm.threads, first, s)
                             : Launch<1>::residual(a, grid, gm.threads, first, s);
     }
-    ztoep_status_t arnoldi(const GArgs &a, cudaStream_t s) const {
-        return gm.elem == 4 ? Launch<4>::arnoldi(a, grid, gm.threads, s) : Launch<1>::arnoldi(a, grid, gm.threads, s);
+    ztoep_status_t arnoldi(const GArgs &a, int pass, cudaStream_t s) const {
+        return gm.elem == 4 ? Launch<4>::arnoldi(a, grid, gm.threads, pass, s)
+                            : Launch<1>::arnoldi(a, grid, gm.threads, pass, s);
     }
     ztoep_status_t update_d(const GArgs &a, cudaStream_t s) const {
         return gm.elem == 4 ? Launch<4>::update_d(a, grid, gm.threads, s)
@@ -879,12 +991,13 @@ static ztoep_status_t build_graph(ztoep_plan_t p, SolveGraph &sg, int prec, int 
     const Geom gm = geom_for(p->N, p->nsm);
     const int per_cta = gm.threads * gm.elem;
     const int nchunk = (int)((p->N + per_cta - 1) / per_cta);
-    const GArgs a = make_args(p, nrhs, m, mixed, nchunk);
+    GArgs a = make_args(p, nrhs, m, mixed, nchunk);
     const Ops ops{gm, dim3(nchunk, nrhs)};
     cudaStream_t s = p->cap;
     cudaGraph_t top = nullptr;
     ZT_CUDA(cudaGraphCreate(&top, 0));
     sg.graph = top;
+    a.graph = 1;
     cudaGraphConditionalHandle h_first, h_sweep, h_iter;
     ZT_CUDA(cudaGraphConditionalHandleCreate(&h_first, top, 0, 0));
     ZT_CUDA(cudaGraphConditionalHandleCreate(&h_sweep, top, 0, 0));
@@ -934,14 +1047,21 @@ static ztoep_status_t build_graph(ztoep_plan_t p, SolveGraph &sg, int prec, int 
     ZT_TRY(launch_small(k_restart_ctl, 1, a, h_restart, s));
     ZT_TRY(capture_end(s));
 
-    // one iteration
+    // one iteration; the second Gram-Schmidt pass only when a RHS asked for it
+    // (its condition starts at 0 and is reset by every iteration control)
+    cudaGraph_t body_reorth = nullptr;
+    ZT_CUDA(cudaGraphConditionalHandleCreate(&a.h_reorth, body_iter, 0, cudaGraphCondAssignDefault));
     ZT_TRY(capture_begin(s, body_iter, &sg.k_iter));
     if (mixed)
         ZT_TRY(run_matvec<float>(p, nrhs, a.x32, (float2 *)p->ws32.yout, s));
     else
         ZT_TRY(run_matvec<double>(p, nrhs, w.xin64, w.w, s));
-    ZT_TRY(ops.arnoldi(a, s));
+    ZT_TRY(ops.arnoldi(a, 1, s));
+    ZT_TRY(add_conditional(s, a.h_reorth, cudaGraphCondTypeIf, &body_reorth));
     ZT_TRY(launch_small(k_iter_ctl, 1, a, h_iter, s));
+    ZT_TRY(capture_end(s));
+    ZT_TRY(capture_begin(s, body_reorth, &sg.k_reorth));
+    ZT_TRY(ops.arnoldi(a, 2, s));
     ZT_TRY(capture_end(s));
 
     ZT_CUDA(cudaGraphInstantiate(&sg.exec, top, 0));
@@ -1017,7 +1137,8 @@ static ztoep_status_t run_host_loop(ztoep_plan_t p, int prec, int nrhs, int m, c
                     ZT_TRY(run_matvec<float>(p, nrhs, a.x32, (float2 *)p->ws32.yout, s));
                 else
                     ZT_TRY(run_matvec<double>(p, nrhs, w.xin64, w.w, s));
-                ZT_TRY(ops.arnoldi(a, s));
+                ZT_TRY(ops.arnoldi(a, 1, s));
+                ZT_TRY(ops.arnoldi(a, 2, s));
                 ZT_TRY(launch_small(k_iter_ctl, 1, a, none, s, 0));
                 ZT_TRY(read_ctl());
                 if (!hc->cond_iter) break;
@@ -1070,7 +1191,8 @@ static ztoep_status_t solve_core(ztoep_plan_t p, const ztoep_solve_opts_t *o, in
     ZT_CUDA(cudaStreamSynchronize(s));
     if (g)
         add_launches(g->k_fixed + (hc->zero ? 0 : g->k_first_product) + (uint64_t)hc->outer_bodies * g->k_sweep +
-                     (uint64_t)hc->restart_bodies * g->k_restart + (uint64_t)hc->inner_bodies * g->k_iter);
+                     (uint64_t)hc->restart_bodies * g->k_restart + (uint64_t)hc->inner_bodies * g->k_iter +
+                     (uint64_t)hc->reorth_bodies * g->k_reorth);
     bool timed_out = hc->timed_out != 0;
     if (dev_err != 0) {  // a bounded device-side wait gave up
         ZT_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), s));

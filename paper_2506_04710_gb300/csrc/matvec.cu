@@ -458,6 +458,161 @@ __global__ void __launch_bounds__(256) k_edge_finish(const cplx_t<R> *__restrict
     if (lane == 0) y[(int64_t)r * N + NT + e] = s;
 }
 
+// FP32 edge coupling, one pass over B with no E split: a CTA owns a tile of
+// E2_TW columns of B and reads all E rows of it; warp w takes the rows
+// w*UNR.., w*UNR + W*UNR.., ... (UNR rows per step, loads first).
+//   Ep[tile][r][e] = sum_{t in tile} B[e][t] x_T[r][t]  (complete per warp, no
+//                    cross-warp step: every row of the tile is one warp's)
+//   ET[r][t]       = sum_e B[e][t] x_E[r][e]            (per-warp sums added in
+//                    warp order through shared memory at the end)
+// So B^T x_E needs no partial buffers and no fold, and the loop has no
+// barrier.  Rows are taken in chunks of E2_ECH so x_E fits in shared memory.
+constexpr int E2_W = 8, E2_U = 2, E2_CPL = 2, E2_TW = 32 * E2_U * E2_CPL, E2_ECH = 1024;
+
+template <int RC>
+__global__ void __launch_bounds__(256) k_edge2(const float2 *__restrict__ x, const float2 *__restrict__ B,
+                                               float2 *__restrict__ ET, float2 *__restrict__ Ep, int64_t NT,
+                                               int64_t ldb, int E, int64_t N, int nrhs, int r0, int rc) {
+    constexpr int U = E2_U, CPL = E2_CPL, W = E2_W, UNR = 4;
+    // x_E of the current row chunk, later reused for the cross-warp sums
+    constexpr int SX = E2_ECH * RC, SR = W * E2_TW * RC;
+    __shared__ float2 sh[SX > SR ? SX : SR];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tile = blockIdx.x;
+    const int64_t tbase = (int64_t)tile * E2_TW;
+
+    float2 xt[U][CPL][RC], acc[U][CPL][RC];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int64_t t = tbase + (int64_t)(u * 32 + lane) * CPL + c;
+#pragma unroll
+            for (int q = 0; q < RC; ++q) {
+                acc[u][c][q] = make_float2(0.f, 0.f);
+                xt[u][c][q] = (t < NT && q < rc) ? x[(int64_t)(r0 + q) * N + t] : make_float2(0.f, 0.f);
+            }
+        }
+    for (int ec = 0; ec < E; ec += E2_ECH) {
+        const int ne = min(E2_ECH, E - ec);
+        __syncthreads();
+        for (int k = threadIdx.x; k < ne * RC; k += blockDim.x) {
+            const int el = k / RC, q = k - el * RC;
+            sh[k] = q < rc ? x[(int64_t)(r0 + q) * N + NT + ec + el] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int el0 = warp * UNR; el0 < ne; el0 += W * UNR) {
+            float4 raw[UNR][U];
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                const float2 *brow = B + (int64_t)(ec + el0 + k) * ldb + tbase;
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    raw[k][u] = (el0 + k < ne)
+                                    ? __ldcs(reinterpret_cast<const float4 *>(brow + (int64_t)(u * 32 + lane) * CPL))
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            float2 part[UNR][RC];
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                const int el = el0 + k;
+                float2 bv[U][CPL];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    bv[u][0] = make_float2(raw[k][u].x, raw[k][u].y);
+                    bv[u][1] = make_float2(raw[k][u].z, raw[k][u].w);
+                }
+#pragma unroll
+                for (int q = 0; q < RC; ++q) {
+                    const float2 xe = el < ne ? sh[el * RC + q] : make_float2(0.f, 0.f);
+                    float2 pt = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+#pragma unroll
+                        for (int c = 0; c < CPL; ++c) {
+                            acc[u][c][q] = cfma(bv[u][c], xe, acc[u][c][q]);
+                            pt = cfma(bv[u][c], xt[u][c][q], pt);
+                        }
+                    part[k][q] = pt;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RC; ++q) {
+                float2 v4[UNR];
+#pragma unroll
+                for (int k = 0; k < UNR; ++k) v4[k] = part[k][q];
+                const float2 tot = warp_rs4<float>(v4);
+                const int k = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
+                if ((lane & 7) == 0 && el0 + k < ne && q < rc)
+                    Ep[((int64_t)tile * nrhs + r0 + q) * E + ec + el0 + k] = tot;
+            }
+        }
+    }
+    __syncthreads();
+    // B^T x_E: add the W per-warp sums in warp order
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int q = 0; q < RC; ++q) sh[(warp * E2_TW + (u * 32 + lane) * CPL + c) * RC + q] = acc[u][c][q];
+    __syncthreads();
+    for (int k = threadIdx.x; k < E2_TW * RC; k += blockDim.x) {
+        const int col = k / RC, q = k - col * RC;
+        const int64_t t = tbase + col;
+        if (t < NT && q < rc) {
+            float2 sum = sh[col * RC + q];
+#pragma unroll
+            for (int w = 1; w < W; ++w) sum = sum + sh[(w * E2_TW + col) * RC + q];
+            ET[(int64_t)(r0 + q) * NT + t] = sum;
+        }
+    }
+}
+
+// y_E[r][e] = sum_tile Ep[tile][r][e] + sum_e' C[e][e'] x_E[r][e'].  A CTA
+// owns 32 edge rows of one RHS: thread (g, l) adds tiles g, g+8, ... of row
+// e0+l (coalesced over l, four accumulators), the 8 group sums are added in
+// order, and each warp forms C x_E for 4 of the rows.
+__global__ void __launch_bounds__(256) k_edge_finish2(const float2 *__restrict__ x, const float2 *__restrict__ Cm,
+                                                      const float2 *__restrict__ Ep, float2 *__restrict__ y,
+                                                      int64_t NT, int E, int64_t N, int nrhs, int ntile) {
+    __shared__ float2 red[8][32];
+    __shared__ float2 cx[32];
+    const int l = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int e0 = blockIdx.x * 32, r = blockIdx.y;
+    const int e = e0 + l;
+    float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
+    if (e < E) {
+        int t = g;
+        for (; t + 24 < ntile; t += 32) {
+            s0 = s0 + Ep[((int64_t)t * nrhs + r) * E + e];
+            s1 = s1 + Ep[((int64_t)(t + 8) * nrhs + r) * E + e];
+            s2 = s2 + Ep[((int64_t)(t + 16) * nrhs + r) * E + e];
+            s3 = s3 + Ep[((int64_t)(t + 24) * nrhs + r) * E + e];
+        }
+        for (; t < ntile; t += 8) s0 = s0 + Ep[((int64_t)t * nrhs + r) * E + e];
+    }
+    red[g][l] = (s0 + s1) + (s2 + s3);
+    const float2 *xe = x + (int64_t)r * N + NT;
+    for (int k = 0; k < 4; ++k) {
+        const int row = g * 4 + k, er = e0 + row;
+        float2 c = make_float2(0.f, 0.f);
+        if (er < E) {
+            const float2 *crow = Cm + (int64_t)er * E;
+            for (int j = l; j < E; j += 32) c = cfma(crow[j], xe[j], c);
+        }
+        c = warp_sum<float>(c);
+        if (l == 0) cx[row] = c;
+    }
+    __syncthreads();
+    if (g == 0 && e < E) {
+        float2 sum = red[0][l];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) sum = sum + red[k][l];
+        y[(int64_t)r * N + NT + e] = sum + cx[l];
+    }
+}
+
 // ------------------------------------------------------------ conversions
 __global__ void k_c128_to_c64(const double2 *__restrict__ s, float2 *__restrict__ d, int64_t n) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
@@ -496,6 +651,7 @@ static int edge_ntile(ztoep_plan_t p, size_t csize) {
     int tile = (csize == 8) ? EdgeGeom<float>::TILE : EdgeGeom<double>::TILE;
     return (int)((p->NT + tile - 1) / tile);
 }
+static int edge2_ntile(ztoep_plan_t p) { return (int)((p->NT + E2_TW - 1) / E2_TW); }
 static int edge_nsplit(ztoep_plan_t p, int ntile, size_t csize) {
     if (p->E == 0) return 0;
     // enough CTAs for several resident per SM (FP32: 4 per SM, FP64: 2)
@@ -537,7 +693,7 @@ template <typename R> ztoep_status_t ensure_ws(ztoep_plan_t p, int nrhs) {
     const bool tc = cs == 8 && nrhs >= kTcMinRhs;
     if (p->E > 0) {
         ZT_TRY(dalloc(&w.ET, cs * (size_t)std::max(nsplit, 1) * nrhs * p->NT, &acc));
-        const int parts = std::max(ntile, tc ? tc_edge_splits(p) : 0);
+        const int parts = std::max(cs == 8 ? edge2_ntile(p) : ntile, tc ? tc_edge_splits(p) : 0);
         ZT_TRY(dalloc(&w.Ep, cs * (size_t)parts * nrhs * p->E, &acc));
     }
     if (tc) ZT_TRY(dalloc(&w.Yh, cs * nrhs * (size_t)p->F * p->b, &acc));
@@ -663,6 +819,31 @@ static ztoep_status_t launch_edge(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, 
     return ZTOEP_OK;
 }
 
+// FP32 edge coupling without E splits (k_edge2): ET holds B^T x_E directly.
+static ztoep_status_t launch_edge2(ztoep_plan_t p, int nrhs, const float2 *x, float2 *y, MatvecWs &w,
+                                   cudaStream_t s) {
+    float2 *ET = reinterpret_cast<float2 *>(w.ET);
+    float2 *Ep = reinterpret_cast<float2 *>(w.Ep);
+    const int ntile = edge2_ntile(p);
+    const int64_t ldb = edge_ldb(p->NT);
+    for (int r0 = 0; r0 < nrhs; r0 += 4) {
+        const int rc = std::min(4, nrhs - r0);
+        KScope ks(K_EDGE, s);
+        if (rc == 1)
+            k_edge2<1><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc);
+        else if (rc == 2)
+            k_edge2<2><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc);
+        else
+            k_edge2<4><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc);
+        ZT_CUDA(cudaGetLastError());
+    }
+    dim3 gf((p->E + 31) / 32, nrhs);
+    KScope ks(K_MISC, s);
+    k_edge_finish2<<<gf, 256, 0, s>>>(x, p->C32, Ep, y, p->NT, p->E, p->N, nrhs, ntile);
+    ZT_CUDA(cudaGetLastError());
+    return ZTOEP_OK;
+}
+
 // Tensor-core edge coupling (FP32 products, kTcMinRhs..kTcMaxRhs RHS):
 //   B x_T    as C[e][q] = sum_t B[e][t] x_T[q][t]   -> K-split partials in Ep
 //   B^T x_E  as C[t][q] = sum_e B^T[t][e] x_E[q][e] -> ET[0]
@@ -721,6 +902,9 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
         ZT_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
         if (tc)
             ZT_TRY(tc_edge(p, nrhs, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), w, p->side));
+        else if (sizeof(R) == sizeof(float))
+            ZT_TRY(launch_edge2(p, nrhs, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), w,
+                                p->side));
         else
             ZT_TRY(launch_edge<R>(p, nrhs, x, y, w, p->side, true));
         ZT_CUDA(cudaEventRecord(p->ev_join, p->side));
