@@ -186,9 +186,10 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
 
     t0 = time.perf_counter()
-    plan = ztoep.Plan.from_problem(prob, device=dev)
+    plan = ztoep.Plan.from_problem(prob, device=dev, autotune=0 if args.no_autotune else prob.nrhs)
     torch.cuda.synchronize(dev)
     plan_ms = 1e3 * (time.perf_counter() - t0)
+    tune = plan.tune.as_dict() if plan.tune is not None else None
     V = torch.from_numpy(prob.V.copy()).to(dev)
     X = torch.zeros_like(V)
     N, nrhs = prob.n, prob.nrhs
@@ -279,7 +280,7 @@ def run_ours(args, world, rank, local):
     bp_bytes = plan.info.n_pairs * b * b * 8 + 2 * F * b * nrhs * 8
     bp_us = kt["blockprod"]["avg_us"]
     bp_gbs = bp_bytes / (bp_us / 1e6) / 1e9 if bp_us > 0 else None
-    roofline = {"kernel": "k_edge<float> (B x_T and B^T x_E, one pass over B)", "bound": "hbm",
+    roofline = {"kernel": "k_edge2 (FP32 B x_T and B^T x_E, one pass over B)", "bound": "hbm",
                 "achieved": edge_gbs, "peak": hbm, "unit": "GB/s",
                 "frac": (edge_gbs / hbm) if edge_gbs else None, "traffic": None,
                 "bytes_per_launch": edge_bytes, "avg_launch_us": edge_us,
@@ -356,6 +357,7 @@ def run_ours(args, world, rank, local):
             "blockprod": {"GB/s": bp_gbs, "bytes_per_launch": bp_bytes},
             "product_kernels_us": kt,
             "plan_ms": plan_ms,
+            "autotune": tune,
             "launches_per_step": launches / args.steps,
         }
         print(json.dumps(line), flush=True)
@@ -473,6 +475,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="heuristic launch shapes, smallest embedding")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the solver loops from the host (for profilers; slower)")
     ap.add_argument("--serve", type=int, default=0,

@@ -217,6 +217,55 @@ ZTOEP_API size_t ztoep_footprint(const ztoep_desc_t *desc, int32_t max_nrhs, int
 
 ZTOEP_API void ztoep_plan_destroy(ztoep_plan_t plan);
 
+/* ---- Autotuning (not part of the method: launch and layout choices) ----
+ * The choices a plan's kernels are built with.  0 in a field means the
+ * built-in heuristic.  rad_order: 0 = radix 4 first, 1 = reversed sequence;
+ * fft_channels: channels one CTA of an FP32 FFT pass transforms (1..64, a
+ * power of two; 0 = heuristic), fft_threads: its block size (64/128/256);
+ * bp_split: threads per dot product of the SIMT block product (divides b);
+ * tc_kchunk: complex K per CTA of the tensor-core B x_T product.  lx, ly,
+ * rad_order, bp_split and tc_kchunk change the rounding of the products (all
+ * choices compute the same product exactly in exact arithmetic); they are
+ * fixed for the plan's life, so results stay independent of the batch. */
+typedef struct {
+    int32_t lx, ly;                   /* embedding sizes */
+    int32_t rad_order_x, rad_order_y;
+    int32_t fft_channels_x, fft_threads_x; /* FP32 x passes */
+    int32_t fft_channels_y, fft_threads_y; /* FP32 y passes */
+    int32_t bp_split, bp_ctas_per_sm; /* SIMT block product */
+    int32_t tc_kchunk;                /* tensor-core edge product */
+    int32_t nrhs;                     /* RHS count the choice was timed for */
+    int32_t candidates;               /* configurations timed (0: taken from the cache) */
+    double product_us;                /* FP32 product time with the choice */
+    double default_us;                /* same with the heuristics and the smallest embedding */
+} ztoep_tune_t;
+
+/* Build a plan (same inputs and errors as ztoep_plan) whose embedding sizes,
+ * FFT radix order, FFT-pass geometry, block-product split and tensor-core K
+ * chunk minimise the measured FP32 product time for nrhs right-hand sides
+ * (1..256).  Each candidate is timed with CUDA events on `stream`; embedding
+ * candidates are the three smallest 5-smooth sizes >= 2N-1 per dimension
+ * (within 25% of the smallest, unless desc fixes lx/ly) and each needs its
+ * own plan build, so tuning costs several plan builds and about a hundred
+ * products.  The choice is cached per (GPU name, nx, ny, b, n_edge, lx, ly
+ * of desc, nrhs) in the process and, when the environment variable
+ * ZTOEP_TUNE_CACHE names a file, in that file (one line per key), so a
+ * later call builds the plan once with the cached choice.  tune (may be
+ * NULL) receives the choice.  The device memory of two plans is needed while
+ * tuning. */
+ZTOEP_API ztoep_status_t ztoep_plan_autotune(const ztoep_desc_t *desc, const void *T, const void *B,
+                                             const void *C, int32_t nrhs, void *stream, ztoep_plan_t *out,
+                                             ztoep_tune_t *tune);
+
+/* Build a plan with explicit choices (a ztoep_tune_t from ztoep_plan_autotune,
+ * possibly of another process); desc's lx/ly are replaced by tune's when
+ * nonzero.  ARG if a choice is out of range. */
+ZTOEP_API ztoep_status_t ztoep_plan_tuned(const ztoep_desc_t *desc, const void *T, const void *B, const void *C,
+                                          const ztoep_tune_t *tune, void *stream, ztoep_plan_t *out);
+
+/* The choices of a plan (heuristic fields reported as 0). */
+ZTOEP_API ztoep_status_t ztoep_plan_get_tune(ztoep_plan_t plan, ztoep_tune_t *tune);
+
 ZTOEP_API const char *ztoep_status_string(ztoep_status_t status);
 
 /* ---- Instrumentation (not part of the method) ----

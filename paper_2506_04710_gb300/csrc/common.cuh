@@ -83,11 +83,27 @@ struct Fft1D {
     int rad[12];
 };
 
-Fft1D make_fft1d(int L);
+// Radix sequence for length L: order 0 takes radix 4 first (then 2, 3, 5),
+// order 1 the reverse sequence.
+Fft1D make_fft1d(int L, int order = 0);
 int smooth_size_at_least(int n);
 bool is_smooth(int n);
 
 // ---------------------------------------------------------------- plan
+// Launch and layout choices of a plan; -1 / 0 = the built-in heuristic.  Set
+// when the plan is built (by the autotuner or from its cache) and fixed for the
+// plan's life, so every solve on it sums in the same order whatever its RHS
+// count.  The FFT-pass knobs apply to FP32 products; their values do not
+// change the arithmetic of a line's transform.
+struct TuneParams {
+    int rad_order[2] = {0, 0};  // radix order of the x and y transforms (plan and products)
+    int lib[2] = {-1, -1};      // log2 channels per CTA of the FP32 x / y passes
+    int thr[2] = {0, 0};        // threads per CTA of the FP32 x / y passes
+    int bp_split = 0;           // threads per dot product in the SIMT block product
+    int bp_per_sm = 0;          // block-product CTAs per SM
+    int tc_kchunk = 0;          // K per CTA of the tensor-core B x_T product
+};
+
 struct MatvecWs {  // per-precision matvec workspace, sized for `cap` RHS
     int cap = 0;
     void *xin = nullptr;    // [cap][N] input copy in this precision (public matvec / solver)
@@ -146,6 +162,7 @@ struct ztoep_plan_s {
     int nsm = 0;
     bool masked = false;
     ztoep::Fft1D fx{}, fy{};
+    ztoep::TuneParams tune;
     int2 *pairs = nullptr;          // [npairs] (f, -f); f == -f for self-paired frequencies
     int *rep = nullptr;             // [F] pair index of f if f is the stored one, else -1-pair
     double2 *That64 = nullptr;      // [npairs][b][b]
@@ -187,6 +204,9 @@ namespace ztoep {
     } while (0)
 
 ztoep_status_t dalloc(void **p, size_t bytes, size_t *acc);
+// Build a plan with the given launch/layout choices (ztoep_plan uses the defaults).
+ztoep_status_t plan_create(const ztoep_desc_t *d, const void *T, const void *B, const void *C, cudaStream_t s,
+                           const TuneParams &tp, ztoep_plan_t *out);
 void free_solve_graphs(ztoep_plan_t p);  // cached graphs bake in workspace pointers
 
 // Matvec in one precision on plan-internal buffers: y = Z' x, x/y [nrhs][N].

@@ -664,6 +664,7 @@ static int edge_nsplit(ztoep_plan_t p, int ntile, size_t csize) {
 // K chunk of the tensor-core B x_T product: enough (row tile, K split) CTAs to
 // cover every SM twice, at least 256 complex k per CTA.
 static int tc_edge_kchunk(ztoep_plan_t p) {
+    if (p->tune.tc_kchunk > 0) return std::max(16, (p->tune.tc_kchunk + 15) / 16 * 16);
     const int mt = (p->E + 63) / 64;
     const int want = std::max(1, (2 * p->nsm + mt - 1) / mt);
     int kc = (int)((p->NT + want - 1) / want);
@@ -722,18 +723,30 @@ template <> const double2 *twy_of<double>(ztoep_plan_t p) { return p->twy64; }
 
 static int64_t edge_ldb(int64_t NT) { return (NT + 1023) / 1024 * 1024; }
 
+// Geometry of an FFT pass along dimension dim (0 = x, 1 = y): the heuristic,
+// or the plan's tuned channel batch and thread count for FP32 passes (the
+// batch clamped to what fits in shared memory).
+static PassCfg plan_pass_cfg(ztoep_plan_t p, int dim, int L, int lines, size_t cs) {
+    PassCfg c = pass_cfg(L, p->b, lines, cs, p->nsm);
+    if (cs == 8) {
+        if (p->tune.lib[dim] >= 0) c.lib = std::min(p->tune.lib[dim], pick_lib(L, p->b, cs, 64 * 1024));
+        if (p->tune.thr[dim] > 0) c.threads = p->tune.thr[dim];
+    }
+    return c;
+}
+
 template <typename R>
 static ztoep_status_t forward_passes(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *X1,
                                      cplx_t<R> *Xh, cudaStream_t s) {
     const size_t cs = sizeof(cplx_t<R>);
     const uint8_t *act = p->masked ? p->active : nullptr;
-    const PassCfg cx = pass_cfg(p->lx, p->b, p->ny * nrhs, cs, p->nsm);
+    const PassCfg cx = plan_pass_cfg(p, 0, p->lx, p->ny * nrhs, cs);
     const int ibx = 1 << cx.lib;
     dim3 gx((p->b + ibx - 1) / ibx, p->ny, nrhs);
     ZT_TRY((launch_fft_pass<R>(p->fx, twx_of<R>(p), cx.lib, false, gx,
                                LdXFwd<R>{x, act, p->nx, p->b, ibx, p->N},
                                StX1<R>{X1, p->ny, p->lx, p->b, ibx}, s, cx.threads)));
-    const PassCfg cy = pass_cfg(p->ly, p->b, p->lx * nrhs, cs, p->nsm);
+    const PassCfg cy = plan_pass_cfg(p, 1, p->ly, p->lx * nrhs, cs);
     const int iby = 1 << cy.lib;
     dim3 gy((p->b + iby - 1) / iby, p->lx, nrhs);
     ZT_TRY((launch_fft_pass<R>(p->fy, twy_of<R>(p), cy.lib, false, gy,
@@ -754,11 +767,16 @@ static ztoep_status_t launch_blockprod(ztoep_plan_t p, int nrhs, cplx_t<R> *Xh, 
         // pipelined bulk-copy path
         const int nst = 3 * stage <= budget ? 3 : 2;
         const size_t smem = nst * stage;
-        const int per_sm = std::max<int>(1, std::min<int>(4, (int)((227 * 1024) / (smem + 6 * 1024))));
+        const int fit = std::max<int>(1, std::min<int>(4, (int)((227 * 1024) / (smem + 6 * 1024))));
+        const int per_sm = p->tune.bp_per_sm > 0 ? std::min(p->tune.bp_per_sm, fit) : fit;
         const int grid = std::min(p->npairs, p->nsm * per_sm);
-        int S = 1;  // threads per dot product: from b only (batch-independent sums)
-        for (int c : {8, 4, 2})
-            if (p->b % c == 0 && c * 2 * p->b <= 256) { S = c; break; }
+        int S = 1;  // threads per dot product: from b (or the plan's choice) only, batch-independent sums
+        if (p->tune.bp_split > 0 && p->b % p->tune.bp_split == 0 && p->tune.bp_split <= 8) {
+            S = p->tune.bp_split;
+        } else {
+            for (int c : {8, 4, 2})
+                if (p->b % c == 0 && c * 2 * p->b <= 256) { S = c; break; }
+        }
         static bool attr = false;
         if (!attr) {
             ZT_CUDA(cudaFuncSetAttribute(k_blockprod_tma<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
@@ -917,14 +935,14 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
     } else {
         ZT_TRY(launch_blockprod<R>(p, nrhs, Xh, s));
     }
-    const PassCfg cy = pass_cfg(p->ly, p->b, p->lx * nrhs, cs, p->nsm);
+    const PassCfg cy = plan_pass_cfg(p, 1, p->ly, p->lx * nrhs, cs);
     const int iby = 1 << cy.lib;
     dim3 gy((p->b + iby - 1) / iby, p->lx, nrhs);
     ZT_TRY((launch_fft_pass<R>(p->fy, twy_of<R>(p), cy.lib, true, gy,
                                LdXh<R>{Yh, p->lx, p->b, iby, nrhs},
                                StY1<R>{X1, p->ny, p->lx, p->b, iby}, s, cy.threads)));
     if (p->E > 0) ZT_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
-    const PassCfg cx = pass_cfg(p->lx, p->b, p->ny * nrhs, cs, p->nsm);
+    const PassCfg cx = plan_pass_cfg(p, 0, p->lx, p->ny * nrhs, cs);
     const int ibx = 1 << cx.lib;
     dim3 gx((p->b + ibx - 1) / ibx, p->ny, nrhs);
     const R scale = (R)(1.0 / ((double)p->lx * (double)p->ly));

@@ -33,7 +33,7 @@ int smooth_size_at_least(int n) {
     return L;
 }
 
-Fft1D make_fft1d(int L) {
+Fft1D make_fft1d(int L, int order) {
     Fft1D f{};
     f.L = L;
     int n = L;
@@ -41,6 +41,8 @@ Fft1D make_fft1d(int L) {
     while (n % 2 == 0) { f.rad[f.nst++] = 2; n /= 2; }
     while (n % 3 == 0) { f.rad[f.nst++] = 3; n /= 3; }
     while (n % 5 == 0) { f.rad[f.nst++] = 5; n /= 5; }
+    if (order == 1)
+        for (int i = 0, j = f.nst - 1; i < j; ++i, --j) std::swap(f.rad[i], f.rad[j]);
     return f;
 }
 
@@ -240,14 +242,15 @@ static ztoep_status_t upload_twiddles(int L, double2 **d64, float2 **d32, size_t
 static ztoep_status_t plan_build(ztoep_plan_t p, const ztoep_desc_t *d, const double2 *T, const double2 *B,
                                  const double2 *C, cudaStream_t s) {
     size_t acc = 0;
+    const TuneParams &tp = p->tune;
     p->nx = d->nx; p->ny = d->ny; p->b = d->b; p->E = d->n_edge;
     p->lx = d->lx ? d->lx : smooth_size_at_least(2 * d->nx - 1);
     p->ly = d->ly ? d->ly : smooth_size_at_least(2 * d->ny - 1);
     p->F = p->lx * p->ly;
     p->NT = (int64_t)p->nx * p->ny * p->b;
     p->N = p->NT + p->E;
-    p->fx = make_fft1d(p->lx);
-    p->fy = make_fft1d(p->ly);
+    p->fx = make_fft1d(p->lx, tp.rad_order[0]);
+    p->fy = make_fft1d(p->ly, tp.rad_order[1]);
     ZT_CUDA(cudaGetDevice(&p->device));
     ZT_CUDA(cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device));
     ZT_CUDA(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
@@ -329,15 +332,18 @@ static ztoep_status_t plan_build(ztoep_plan_t p, const ztoep_desc_t *d, const do
     return ZTOEP_OK;
 }
 
-ztoep_status_t ztoep_plan(const ztoep_desc_t *d, const void *T, const void *B, const void *C, void *stream,
-                          ztoep_plan_t *out) {
+}  // extern "C"
+
+namespace ztoep {
+ztoep_status_t plan_create(const ztoep_desc_t *d, const void *T, const void *B, const void *C, cudaStream_t s,
+                           const TuneParams &tp, ztoep_plan_t *out) {
     if (!out) return ZTOEP_ERR_ARG;
     *out = nullptr;
     if (!valid_desc(d) || !T) return ZTOEP_ERR_ARG;
     if (d->n_edge > 0 && (!B || !C)) return ZTOEP_ERR_ARG;
     ztoep_plan_t p = new (std::nothrow) ztoep_plan_s();
     if (!p) return ZTOEP_ERR_NOMEM;
-    cudaStream_t s = (cudaStream_t)stream;
+    p->tune = tp;
     ztoep_status_t st = plan_build(p, d, (const double2 *)T, (const double2 *)B, (const double2 *)C, s);
     if (st != ZTOEP_OK) {
         ztoep_plan_destroy(p);
@@ -345,6 +351,14 @@ ztoep_status_t ztoep_plan(const ztoep_desc_t *d, const void *T, const void *B, c
     }
     *out = p;
     return ZTOEP_OK;
+}
+}  // namespace ztoep
+
+extern "C" {
+
+ztoep_status_t ztoep_plan(const ztoep_desc_t *d, const void *T, const void *B, const void *C, void *stream,
+                          ztoep_plan_t *out) {
+    return plan_create(d, T, B, C, (cudaStream_t)stream, TuneParams{}, out);
 }
 
 ztoep_status_t ztoep_plan_get_info(ztoep_plan_t p, ztoep_plan_info_t *info) {

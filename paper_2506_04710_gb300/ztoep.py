@@ -62,6 +62,17 @@ class PlanInfo(ctypes.Structure):
                 ("resident_bytes", ctypes.c_size_t), ("dense_bytes", ctypes.c_size_t)]
 
 
+class TuneInfo(ctypes.Structure):
+    _fields_ = [("lx", ctypes.c_int32), ("ly", ctypes.c_int32), ("rad_order_x", ctypes.c_int32),
+                ("rad_order_y", ctypes.c_int32), ("fft_channels_x", ctypes.c_int32), ("fft_threads_x", ctypes.c_int32),
+                ("fft_channels_y", ctypes.c_int32), ("fft_threads_y", ctypes.c_int32), ("bp_split", ctypes.c_int32),
+                ("bp_ctas_per_sm", ctypes.c_int32), ("tc_kchunk", ctypes.c_int32), ("nrhs", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("product_us", ctypes.c_double), ("default_us", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class SchedOpts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("workers", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("fake_backend", ctypes.c_int32), ("fake_us", ctypes.c_int64)]
@@ -95,7 +106,8 @@ EXPORTS = ["ztoep_default_opts", "ztoep_plan", "ztoep_matvec", "ztoep_solve", "z
            "ztoep_plan_destroy", "ztoep_status_string", "ztoep_version", "ztoep_launch_count",
            "ztoep_timing_enable", "ztoep_timing_reset", "ztoep_timing_read", "ztoep_edge_product_noalloc",
            "ztoep_sched_create", "ztoep_sched_submit", "ztoep_sched_poll", "ztoep_sched_wait",
-           "ztoep_sched_get_stats", "ztoep_sched_destroy"]
+           "ztoep_sched_get_stats", "ztoep_sched_destroy", "ztoep_plan_autotune", "ztoep_plan_tuned",
+           "ztoep_plan_get_tune"]
 
 K_FFT, K_BLOCKPROD, K_EDGE, K_ARNOLDI, K_MISC, K_TENSOR = range(6)
 
@@ -146,6 +158,14 @@ def lib(path: str | None = None):
     L.ztoep_sched_get_stats.restype = c_i32
     L.ztoep_sched_destroy.argtypes = [c_p]
     L.ztoep_sched_destroy.restype = None
+    L.ztoep_plan_autotune.argtypes = [ctypes.POINTER(Desc), c_p, c_p, c_p, c_i32, c_p, ctypes.POINTER(c_p),
+                                      ctypes.POINTER(TuneInfo)]
+    L.ztoep_plan_autotune.restype = c_i32
+    L.ztoep_plan_tuned.argtypes = [ctypes.POINTER(Desc), c_p, c_p, c_p, ctypes.POINTER(TuneInfo), c_p,
+                                   ctypes.POINTER(c_p)]
+    L.ztoep_plan_tuned.restype = c_i32
+    L.ztoep_plan_get_tune.argtypes = [c_p, ctypes.POINTER(TuneInfo)]
+    L.ztoep_plan_get_tune.restype = c_i32
     L.ztoep_edge_product_noalloc.argtypes = [c_p, c_i32, c_p, c_p, c_p]
     L.ztoep_edge_product_noalloc.restype = c_i32
     L.ztoep_launch_count.argtypes = []
@@ -223,6 +243,27 @@ def ztoep_plan(desc: Desc, T, B, C, stream=None) -> ctypes.c_void_p:
     _check(lib().ztoep_plan(ctypes.byref(desc), _dptr(T), _dptr(B), _dptr(C), _stream_ptr(stream),
                             ctypes.byref(h)), "ztoep_plan")
     return h
+
+
+def ztoep_plan_autotune(desc: Desc, T, B, C, nrhs: int, stream=None) -> tuple[ctypes.c_void_p, TuneInfo]:
+    h = ctypes.c_void_p()
+    t = TuneInfo()
+    _check(lib().ztoep_plan_autotune(ctypes.byref(desc), _dptr(T), _dptr(B), _dptr(C), nrhs, _stream_ptr(stream),
+                                     ctypes.byref(h), ctypes.byref(t)), "ztoep_plan_autotune")
+    return h, t
+
+
+def ztoep_plan_tuned(desc: Desc, T, B, C, tune: TuneInfo, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().ztoep_plan_tuned(ctypes.byref(desc), _dptr(T), _dptr(B), _dptr(C), ctypes.byref(tune),
+                                  _stream_ptr(stream), ctypes.byref(h)), "ztoep_plan_tuned")
+    return h
+
+
+def ztoep_plan_get_tune(plan) -> TuneInfo:
+    t = TuneInfo()
+    _check(lib().ztoep_plan_get_tune(plan, ctypes.byref(t)), "ztoep_plan_get_tune")
+    return t
 
 
 def ztoep_matvec(plan, prec: int, nrhs: int, X, Y, stream=None) -> int:
@@ -403,20 +444,28 @@ def info_array(nrhs: int):
 class Plan:
     """Owns a plan built from a synthetic Problem (or explicit arrays)."""
 
-    def __init__(self, nx, ny, b, n_edge, T, B, C, active=None, lx=0, ly=0, stream=None):
+    def __init__(self, nx, ny, b, n_edge, T, B, C, active=None, lx=0, ly=0, stream=None, autotune: int = 0,
+                 tune: TuneInfo | None = None):
+        """autotune > 0: ztoep_plan_autotune for that many RHS; tune: ztoep_plan_tuned."""
         self.desc, self._keep = make_desc(nx, ny, b, n_edge, active, lx, ly)
-        self.handle = ztoep_plan(self.desc, T, B, C, stream)
+        self.tune = None
+        if autotune:
+            self.handle, self.tune = ztoep_plan_autotune(self.desc, T, B, C, autotune, stream)
+        elif tune is not None:
+            self.handle = ztoep_plan_tuned(self.desc, T, B, C, tune, stream)
+        else:
+            self.handle = ztoep_plan(self.desc, T, B, C, stream)
         self.info = ztoep_plan_get_info(self.handle)
         self.n = int(self.info.n)
 
     @classmethod
-    def from_problem(cls, prob, device="cuda", lx=0, ly=0, stream=None):
+    def from_problem(cls, prob, device="cuda", lx=0, ly=0, stream=None, autotune: int = 0, tune=None):
         import torch
         T = torch.from_numpy(np.ascontiguousarray(prob.T)).to(device)
         B = torch.from_numpy(np.ascontiguousarray(prob.B)).to(device) if prob.n_edge else None
         C = torch.from_numpy(np.ascontiguousarray(prob.C)).to(device) if prob.n_edge else None
         act = prob.active if not prob.active.all() else None
-        p = cls(prob.nx, prob.ny, prob.b, prob.n_edge, T, B, C, act, lx, ly, stream)
+        p = cls(prob.nx, prob.ny, prob.b, prob.n_edge, T, B, C, act, lx, ly, stream, autotune, tune)
         if stream is None:
             torch.cuda.current_stream().synchronize()
         else:

@@ -56,11 +56,32 @@ def test_host_only_calls(lib):
     assert ztoep.ztoep_footprint(bad2, 1, 30) == 0
 
 
-def test_structs_match_header_layout():
+def test_structs_match_header_layout(tmp_path):
+    """The ctypes mirrors have the sizes and field offsets the C compiler gives
+    the header's structs."""
+    import subprocess
     from paper_2506_04710_gb300 import ztoep
-    assert ctypes.sizeof(ztoep.Desc) == 32
-    assert ctypes.sizeof(ztoep.SolveOpts) == 48
-    assert ctypes.sizeof(ztoep.SolveInfo) == 24
+    pairs = {"ztoep_desc_t": ztoep.Desc, "ztoep_solve_opts_t": ztoep.SolveOpts,
+             "ztoep_solve_info_t": ztoep.SolveInfo, "ztoep_plan_info_t": ztoep.PlanInfo,
+             "ztoep_tune_t": ztoep.TuneInfo, "ztoep_sched_opts_t": ztoep.SchedOpts,
+             "ztoep_request_t": ztoep.Request, "ztoep_request_state_t": ztoep.RequestState,
+             "ztoep_sched_stats_t": ztoep.SchedStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ztoep.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
 
 
 def test_no_cpu_fallback_when_library_missing(tmp_path):
