@@ -271,7 +271,8 @@ ZTOEP_API const char *ztoep_status_string(ztoep_status_t status);
 /* ---- Instrumentation (not part of the method) ----
  * Kernel classes: 0 FFT passes, 1 per-frequency block products, 2 edge
  * coupling (one pass over B), 3 Arnoldi/Givens steps, 4 everything else,
- * 5 tensor-core (tcgen05) complex GEMMs. */
+ * 5 tensor-core (tcgen05) complex GEMMs, lock-step kernel, 6 the same GEMMs,
+ * warp-specialised pipelined kernel. */
 
 /* Number of CUDA kernels this library has launched in this process. */
 ZTOEP_API uint64_t ztoep_launch_count(void);

@@ -6,7 +6,8 @@
 namespace ztoep {
 
 // Kernel classes (bit positions of the ztoep_timing_enable mask).
-enum KClass { K_FFT = 0, K_BLOCKPROD = 1, K_EDGE = 2, K_ARNOLDI = 3, K_MISC = 4, K_TENSOR = 5, K_NCLASS = 6 };
+enum KClass { K_FFT = 0, K_BLOCKPROD = 1, K_EDGE = 2, K_ARNOLDI = 3, K_MISC = 4, K_TENSOR = 5, K_TENSOR_PIPE = 6,
+              K_NCLASS = 7 };
 
 // Wraps `n` kernel launches of one class on one stream.
 class KScope {

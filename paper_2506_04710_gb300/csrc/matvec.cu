@@ -874,13 +874,13 @@ static ztoep_status_t tc_edge(ztoep_plan_t p, int nrhs, const float2 *x, float2 
     g1.C = reinterpret_cast<float2 *>(w.Ep); g1.ldc_q = p->E; g1.ldc_m = 1; g1.strideC = 0;
     g1.strideCk = (int64_t)nrhs * p->E;
     g1.M = p->E; g1.K = (int)p->NT; g1.N = nrhs; g1.kchunk = kc; g1.err = p->err;
-    ZT_TRY(launch_cgemm_tc(g1, 1, s));
+    ZT_TRY(launch_cgemm(g1, 1, p->nsm, s));
     CgemmArgs g2{};
     g2.A = p->B32T; g2.lda = p->E; g2.strideA = 0;
     g2.X = x + p->NT; g2.ldx = p->N; g2.strideX = 0;
     g2.C = reinterpret_cast<float2 *>(w.ET); g2.ldc_q = p->NT; g2.ldc_m = 1; g2.strideC = 0; g2.strideCk = 0;
     g2.M = (int)p->NT; g2.K = p->E; g2.N = nrhs; g2.kchunk = 0; g2.err = p->err;
-    ZT_TRY(launch_cgemm_tc(g2, 1, s));
+    ZT_TRY(launch_cgemm(g2, 1, p->nsm, s));
     dim3 gf((p->E + 7) / 8, nrhs);
     KScope ks(K_MISC, s);
     k_edge_finish<float><<<gf, 256, 0, s>>>(x, p->C32, reinterpret_cast<const float2 *>(w.Ep), y, p->NT, p->E,
@@ -897,7 +897,7 @@ static ztoep_status_t tc_blockprod(ztoep_plan_t p, int nrhs, const float2 *Xh, f
     g.X = Xh; g.ldx = p->b; g.strideX = (int64_t)nrhs * p->b;
     g.C = Yh; g.ldc_q = p->b; g.ldc_m = 1; g.strideC = (int64_t)nrhs * p->b; g.strideCk = 0;
     g.M = p->b; g.K = p->b; g.N = nrhs; g.kchunk = 0; g.err = p->err;
-    return launch_cgemm_tc(g, p->F, s);
+    return launch_cgemm(g, p->F, p->nsm, s);
 }
 
 template <typename R> static bool use_tensor(ztoep_plan_t p, int nrhs) {

@@ -25,6 +25,14 @@ struct CgemmArgs {
 size_t cgemm_smem_bytes(int np);
 bool cgemm_fits(int n);  // a GEMM with n right-hand sides fits in shared memory
 ztoep_status_t launch_cgemm_tc(CgemmArgs g, int nprob, cudaStream_t s);
+// Warp-specialised persistent variant (TMA operand loads, double-buffered
+// accumulators); UNSUPPORTED when the operands do not suit TMA.
+ztoep_status_t launch_cgemm_tc2(const CgemmArgs &g, int nprob, int nsm, cudaStream_t s);
+// The pipelined kernel when it applies, else the lock-step one.
+inline ztoep_status_t launch_cgemm(const CgemmArgs &g, int nprob, int nsm, cudaStream_t s) {
+    const ztoep_status_t st = launch_cgemm_tc2(g, nprob, nsm, s);
+    return st == ZTOEP_ERR_UNSUPPORTED ? launch_cgemm_tc(g, nprob, s) : st;
+}
 
 // Number of K splits the launcher uses for a given K and chunk.
 inline int cgemm_splits(int K, int kchunk) {

@@ -273,22 +273,29 @@ def test_timeout_is_enforced_on_device():
 
 
 TC_CASES = [("9x4_b40_e24", 16), ("7x6_b12_e20", 20), ("6x6_b33_e0_gap", 33), ("3x5_b4_e12_pw3", 40),
-            ("4x4_b8_e16", 17)]
+            ("4x4_b8_e16", 17), ("9x4_b40_e24", 100), ("16x8_b32_e200", 24), ("16x8_b32_e200", 72)]
+# shapes only the tensor-core tests use: several 128-row tiles of B and B^T,
+# K split of B x_T into partial sums, RHS in chunks of 64
+TC_EXTRA = {"16x8_b32_e200": dict(nx=16, ny=8, b=32, n_edge=200, seed=23)}
 
 
 @pytest.mark.parametrize("key,nrhs", TC_CASES)
 def test_matvec_mixed_tensor_core_path_vs_oracle(key, nrhs):
     # 16..256 RHS take the tcgen05 3xTF32 path for the block and edge products
-    kw = dict(CASES[key])
+    kw = dict(CASES[key] if key in CASES else TC_EXTRA[key])
     kw.update(rhs="planewave", nrhs=nrhs)
     prob = synth.make_problem(**kw)
     ref = oracle.matvec_dense(oracle.assemble(prob), prob.V)
     plan = ztoep.Plan.from_problem(prob)
     ztoep.ztoep_timing_reset()
-    ztoep.ztoep_timing_enable(1 << ztoep.K_TENSOR)
+    ztoep.ztoep_timing_enable(1 << ztoep.K_TENSOR | 1 << ztoep.K_TENSOR_PIPE)
     got = host(plan.matvec(dev(prob.V), ztoep.ZTOEP_MIXED))
     ztoep.ztoep_timing_enable(0)
-    assert ztoep.ztoep_timing_read(ztoep.K_TENSOR)[0] >= 1  # the tensor-core kernels ran
+    lockstep = ztoep.ztoep_timing_read(ztoep.K_TENSOR)[0]
+    pipelined = ztoep.ztoep_timing_read(ztoep.K_TENSOR_PIPE)[0]
+    assert lockstep + pipelined >= 1  # the tensor-core kernels ran
+    if kw["b"] % 2 == 0 and (kw["nx"] * kw["ny"] * kw["b"] + kw["n_edge"]) % 2 == 0:
+        assert lockstep == 0 and pipelined >= 2  # operands suit TMA: the pipelined kernel for every GEMM
     err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
     assert err.max() <= 2e-6
     plan.close()
