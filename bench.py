@@ -467,6 +467,69 @@ def run_serve(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_product(args, local):
+    """One configuration's FP32 product (the inner-iteration product) timed
+    alone: per-class kernel times and the algorithmic GB/s and tensor flops.
+    Used for kernel profiles of the larger systems."""
+    import numpy as np
+    import torch
+    from paper_2506_04710_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2506_04710_gb300 import synth, ztoep
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    key = args.workload
+    if args.nrhs:
+        cfg = dict(synth.CONFIGS[key])
+        cfg.pop("tol")
+        cfg.update(rhs="planewave", nrhs=args.nrhs)
+        prob = synth.make_problem(seed=0, name=key, **cfg)
+    else:
+        prob, _ = synth.config_problem(key)
+    plan = ztoep.Plan.from_problem(prob, device=dev, autotune=0 if args.no_autotune else prob.nrhs)
+    nr, N, NT, E, b = prob.nrhs, prob.n, prob.n_toep, prob.n_edge, prob.b
+    F = plan.info.lx * plan.info.ly
+    s = torch.cuda.current_stream(dev)
+    x = torch.zeros((nr, N), dtype=torch.complex128, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(max(3, args.warmup)):
+        ztoep.ztoep_matvec(plan.handle, ztoep.ZTOEP_MIXED, nr, x, y, s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(s)
+    for _ in range(args.steps):
+        ztoep.ztoep_matvec(plan.handle, ztoep.ZTOEP_MIXED, nr, x, y, s)
+    e1.record(s)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    names = ["fft", "blockprod", "edge", "arnoldi", "misc", "tensor_lockstep", "tensor_pipe"]
+    ztoep.ztoep_timing_reset()
+    ztoep.ztoep_timing_enable((1 << len(names)) - 1)
+    for _ in range(args.steps):
+        ztoep.ztoep_matvec(plan.handle, ztoep.ZTOEP_MIXED, nr, x, y, s)
+    torch.cuda.synchronize(dev)
+    ztoep.ztoep_timing_enable(0)
+    classes = {}
+    for c, n in enumerate(names):
+        k, t = ztoep.ztoep_timing_read(c)
+        if k:
+            classes[n] = {"launches_per_product": k / args.steps, "us_per_product": 1e3 * t / args.steps}
+    tensor = nr >= 16
+    spec = F * b * b * 8 if tensor else plan.info.n_pairs * b * b * 8
+    bedge = (2 if tensor else 1) * E * NT * 8 + E * E * 8
+    byts = spec + bedge + 2 * NT * nr * 8 + 4 * F * b * nr * 8
+    flops = 8.0 * F * b * b * nr + 16.0 * E * NT * nr
+    pk = peaks()
+    line = {"mode": "product", "workload": key, "nrhs": nr, "n": N, "lx": plan.info.lx, "ly": plan.info.ly,
+            "product_ms": ms, "algorithmic_bytes": byts, "GB/s": byts / ms / 1e6,
+            "frac_of_hbm": byts / ms / 1e6 / pk["hbm_gbs"] if pk.get("hbm_gbs") else None,
+            "complex_flops": flops, "tf32_tflops_3x": 3 * flops / ms / 1e9 if tensor else None,
+            "note": "product_ms includes the complex128 <-> complex64 conversions of the public call",
+            "classes": classes}
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -484,9 +547,16 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
     ap.add_argument("--serve-input-gb", type=float, default=32.0)
+    ap.add_argument("--product-only", action="store_true",
+                    help="time the FP32 product of --workload (a configuration key) alone")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--nrhs", type=int, default=0, help="--product-only: plane-wave RHS count instead of the config's")
     args = ap.parse_args()
     world, rank, local = dist_setup()
-    if args.serve > 0:
+    if args.product_only:
+        if rank == 0:
+            run_product(args, local)
+    elif args.serve > 0:
         run_serve(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)

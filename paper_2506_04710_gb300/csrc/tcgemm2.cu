@@ -14,16 +14,20 @@
 // second one of width 2 rp, so A is read twice per k-step instead of three
 // times.
 //
-// CTA = 10 warps, one CTA per SM, persistent over work items (problem, RHS
+// CTA = 14 warps, one CTA per SM, persistent over work items (problem, RHS
 // chunk of rp <= 64, K split, 128-row tile):
 //   warp 0     TMA producer: A tile (128 rows x 32 floats, 128B swizzle) and
-//              the raw X tile (rp rows x 32 floats) of each k-block into a ring
-//              of NS stages (mbarrier full[s], transaction bytes);
-//   warps 2-5  split A in place into hi and a lo tile, expand and split X into
-//              [Xhi; Xlo] (swizzled), then arrive on ready[s];
+//              the raw X tile (rp rows x 32 floats) of each k-block into a raw
+//              ring of NR stages (mbarrier full[r], transaction bytes); a raw
+//              stage is refilled as soon as it has been converted (rfree[r]),
+//              so up to NR loads are in flight whatever the MMAs are doing;
+//   warps 2-9  split A into hi and lo tiles, expand and split X into
+//              [Xhi; Xlo] (swizzled) in one of NO = 2-3 operand stages (once
+//              the MMAs that last read it are done, ofree[o]), then arrive on
+//              rfree[r] and ready[o];
 //   warp 1     one thread issues the MMAs of a k-block and commits them to
-//              empty[s] (stage free) and, at the end of an item, to accf[b];
-//   warps 6-9  epilogue: tensor memory -> registers -> C, then acce[b]; the
+//              ofree[o] and, at the end of an item, to accf[b];
+//   warps 10-13 epilogue: tensor memory -> registers -> C, then acce[b]; the
 //              accumulator is double-buffered, so an item's epilogue overlaps
 //              the next item's MMAs.
 // Every wait is bounded: a wait that gives up records an error bit, raises an
@@ -45,9 +49,10 @@ namespace ztoep {
 
 namespace {
 
-constexpr int G2_THREADS = 320;
+constexpr int G2_THREADS = 448;  // 14 warps
+constexpr int G2_TW = 8;         // warps converting operands
 constexpr int G2_MAXRP = 64;
-constexpr int G2_MAXST = 6;
+constexpr int G2_MAXRAW = 8;
 constexpr uint32_t G2_WAIT = 1u << 22;
 constexpr size_t G2_SMEM_CAP = 227 * 1024 - 1024;  // per-block limit minus static shared memory
 enum { G2_ERRBIT = 4 };
@@ -58,7 +63,8 @@ struct G2Args {
     int M, K, N;         // complex sizes
     int rp;              // RHS rows per chunk (multiple of 8, <= 64)
     int nchunk, ksplit, mtiles, nprob, kchunk;
-    int nstage;
+    int nraw;            // stages of the raw ring
+    int nop;             // stages of the operand ring (2 or 3)
     uint32_t tmem_cols;
     int *err;
 };
@@ -75,6 +81,18 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *tm,
 struct Item {
     int p, c, s, mt, k0, nkb;
 };
+
+// Round to TF32 (10 mantissa bits), nearest with ties away from zero: add half
+// a TF32 unit to the magnitude bits and clear the 13 low bits (the IEEE
+// layout is sign-magnitude, so this rounds the magnitude; a carry into the
+// exponent is the correct round-up to the next binade).  Integer ops, so the
+// split runs at full issue rate instead of the conversion unit's.
+__device__ __forceinline__ float tf32_near(float v) {
+    return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
+}
+__device__ __forceinline__ float4 tf32n4(float4 v) {
+    return make_float4(tf32_near(v.x), tf32_near(v.y), tf32_near(v.z), tf32_near(v.w));
+}
 
 __device__ __forceinline__ Item decode(const G2Args &g, int it) {
     Item r;
@@ -95,26 +113,31 @@ __device__ __forceinline__ Item decode(const G2Args &g, int it) {
 __global__ void __launch_bounds__(G2_THREADS, 1)
     k_cgemm_tc2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, G2Args g) {
     extern __shared__ __align__(1024) unsigned char g2_smem_raw[];
-    __shared__ __align__(8) uint64_t full[G2_MAXST], ready[G2_MAXST], empty[G2_MAXST], accf[2], acce[2];
+    __shared__ __align__(8) uint64_t full[G2_MAXRAW], rfree[G2_MAXRAW], ready[3], ofree[3], accf[2], acce[2];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     const uint32_t raw = smem_u32(g2_smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char *smem = g2_smem_raw + (base - raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int NS = g.nstage, rp = g.rp;
-    // stage: A hi (16 KB) | A lo (16 KB) | X expanded [4 rp][128 B] | X raw [rp][128 B]
-    const uint32_t stage_bytes = 32768u + 640u * (uint32_t)rp;
-    auto a_hi = [&](int s) { return base + (uint32_t)s * stage_bytes; };
-    auto a_lo = [&](int s) { return a_hi(s) + 16384u; };
-    auto x_exp = [&](int s) { return a_hi(s) + 32768u; };
-    auto x_raw = [&](int s) { return a_hi(s) + 32768u + 512u * (uint32_t)rp; };
+    const int NR = g.nraw, NO = g.nop, rp = g.rp;
+    // operand ring (2 stages): A hi (16 KB) | A lo (16 KB) | X expanded [4 rp][128 B]
+    // raw ring (NR stages):    A as loaded (16 KB, 128B swizzle) | X as loaded [rp][128 B]
+    const uint32_t op_bytes = 32768u + 512u * (uint32_t)rp, raw_bytes = 16384u + 128u * (uint32_t)rp;
+    auto a_hi = [&](int o) { return base + (uint32_t)o * op_bytes; };
+    auto a_lo = [&](int o) { return a_hi(o) + 16384u; };
+    auto x_exp = [&](int o) { return a_hi(o) + 32768u; };
+    auto a_raw = [&](int r) { return base + (uint32_t)NO * op_bytes + (uint32_t)r * raw_bytes; };
+    auto x_raw = [&](int r) { return a_raw(r) + 16384u; };
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NS; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&ready[s], 4);
-            mbar_init(&empty[s], 1);
+        for (int r = 0; r < NR; ++r) {
+            mbar_init(&full[r], 1);
+            mbar_init(&rfree[r], G2_TW);
+        }
+        for (int o = 0; o < NO; ++o) {
+            mbar_init(&ready[o], G2_TW);
+            mbar_init(&ofree[o], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
@@ -141,16 +164,16 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
     };
 
     if (warp == 0) {
-        if (lane == 0) {  // ---------------- producer
-            const uint32_t tx = 128u * 128u + (uint32_t)rp * 128u;
+        if (lane == 0) {  // ---------------- producer: raw ring
+            const uint32_t tx = 16384u + (uint32_t)rp * 128u;
             uint32_t kbg = 0;
             bool ok = true;
             for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
                 const Item w = decode(g, it);
                 for (int kb = 0; kb < w.nkb; ++kb) {
-                    const int s = (int)(kbg % NS);
-                    const uint32_t n = kbg / NS;
-                    if (n > 0 && !mbar_wait_bounded(&empty[s], (n - 1) & 1, G2_WAIT)) {
+                    const int r = (int)(kbg % NR);
+                    const uint32_t n = kbg / NR;
+                    if (n > 0 && !mbar_wait_bounded(&rfree[r], (n - 1) & 1, G2_WAIT)) {
                         ok = false;
                         break;
                     }
@@ -158,23 +181,23 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(&full[s], tx);
+                    mbar_arrive_expect_tx(&full[r], tx);
                     const int kx = 2 * (w.k0 + kb * 16);
-                    tma_load_3d(a_hi(s), &tmA, kx, w.mt * 128, w.p, &full[s]);
-                    tma_load_3d(x_raw(s), &tmX, kx, w.c * rp, w.p, &full[s]);
+                    tma_load_3d(a_raw(r), &tmA, kx, w.mt * 128, w.p, &full[r]);
+                    tma_load_3d(x_raw(r), &tmX, kx, w.c * rp, w.p, &full[r]);
                     ++kbg;
                 }
             }
             if (!ok && !*abort_v) fail();
             // no copy may still be landing when the CTA leaves
-            for (int s = 0; s < NS; ++s) {
-                if (kbg <= (uint32_t)s) continue;
-                const uint32_t cnt = (kbg - (uint32_t)s + NS - 1) / NS;  // copies issued into stage s
-                if (!mbar_wait_bounded(&full[s], (cnt - 1) & 1, G2_WAIT)) fail();
+            for (int r = 0; r < NR; ++r) {
+                if (kbg <= (uint32_t)r) continue;
+                const uint32_t cnt = (kbg - (uint32_t)r + NR - 1) / NR;  // copies issued into stage r
+                if (!mbar_wait_bounded(&full[r], (cnt - 1) & 1, G2_WAIT)) fail();
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {  // ---------------- MMA issuer
+        if (lane == 0) {  // ---------------- MMA issuer: operand ring
             const uint32_t id_wide = idesc_tf32(4 * rp), id_half = idesc_tf32(2 * rp);
             uint32_t kbg = 0, tc = 0;
             bool ok = true;
@@ -189,9 +212,8 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
                 fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * 4 * rp);
                 for (int kb = 0; kb < w.nkb; ++kb) {
-                    const int s = (int)(kbg % NS);
-                    const uint32_t n = kbg / NS;
-                    if (*abort_v || !mbar_wait_bounded(&ready[s], n & 1, G2_WAIT)) {
+                    const int o = (int)(kbg % NO);
+                    if (*abort_v || !mbar_wait_bounded(&ready[o], (kbg / NO) & 1, G2_WAIT)) {
                         ok = false;
                         break;
                     }
@@ -199,11 +221,11 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks) {  // 4 x (K = 8 real = 32 bytes)
                         const uint32_t off = ks * 32;
-                        const uint64_t xb = sdesc(x_exp(s) + off);
-                        mma_tf32(d, sdesc(a_hi(s) + off), xb, id_wide, (kb > 0 || ks > 0) ? 1 : 0);
-                        mma_tf32(d, sdesc(a_lo(s) + off), xb, id_half, 1);
+                        const uint64_t xb = sdesc(x_exp(o) + off);
+                        mma_tf32(d, sdesc(a_hi(o) + off), xb, id_wide, (kb > 0 || ks > 0) ? 1 : 0);
+                        mma_tf32(d, sdesc(a_lo(o) + off), xb, id_half, 1);
                     }
-                    mma_commit(&empty[s]);
+                    mma_commit(&ofree[o]);
                     ++kbg;
                 }
                 if (!ok) break;
@@ -212,49 +234,72 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
             }
             if (!ok && !*abort_v) fail();
         }
-    } else if (warp <= 5) {  // ---------------- operand split / expansion (128 threads)
+    } else if (warp < 2 + G2_TW) {  // ---------------- raw -> operands (G2_TW warps)
+        constexpr int NT = 32 * G2_TW;
         const int t = threadIdx.x - 64;
+        // this thread's (row, 16-byte chunk) pieces of the raw X tile and their
+        // four destinations in the expanded tile: fixed for the whole kernel
+        constexpr int XP = (G2_MAXRP * 8 + NT - 1) / NT;
+        uint32_t xo[XP][4];
+#pragma unroll
+        for (int k = 0; k < XP; ++k) {
+            const int i = t + k * NT, q = i >> 3, ch = i & 7;
+            xo[k][0] = sw128(2 * q, ch);
+            xo[k][1] = sw128(2 * q + 1, ch);
+            xo[k][2] = sw128(2 * rp + 2 * q, ch);
+            xo[k][3] = sw128(2 * rp + 2 * q + 1, ch);
+        }
         uint32_t kbg = 0;
         bool ok = true;
         for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
             const Item w = decode(g, it);
             for (int kb = 0; kb < w.nkb; ++kb) {
-                const int s = (int)(kbg % NS);
-                const uint32_t n = kbg / NS;
-                if (*abort_v || !mbar_wait_bounded(&full[s], n & 1, G2_WAIT)) {
+                const int r = (int)(kbg % NR), o = (int)(kbg % NO);
+                const uint32_t n = kbg / NR, no = kbg / NO;
+                if (*abort_v || !mbar_wait_bounded(&full[r], n & 1, G2_WAIT) ||
+                    (no > 0 && !mbar_wait_bounded(&ofree[o], (no - 1) & 1, G2_WAIT))) {
                     ok = false;
                     break;
                 }
-                float4 *ah = reinterpret_cast<float4 *>(smem + (a_hi(s) - base));
-                float4 *al = reinterpret_cast<float4 *>(smem + (a_lo(s) - base));
-#pragma unroll 4
-                for (int i = t; i < 1024; i += 128) {  // elementwise: the swizzle is irrelevant
-                    const float4 v = ah[i];
-                    const float4 h = tf32x4(v);
+                // A: hi and lo at the loaded tile's offsets (elementwise, so the swizzle carries over)
+                const float4 *ar = reinterpret_cast<const float4 *>(smem + (a_raw(r) - base));
+                float4 *ah = reinterpret_cast<float4 *>(smem + (a_hi(o) - base));
+                float4 *al = reinterpret_cast<float4 *>(smem + (a_lo(o) - base));
+#pragma unroll
+                for (int k = 0; k < 1024 / NT; ++k) {
+                    const int i = t + k * NT;
+                    const float4 v = ar[i];
+                    const float4 h = tf32n4(v);
                     ah[i] = h;
-                    al[i] = tf32x4(sub4(v, h));
+                    al[i] = tf32n4(sub4(v, h));
                 }
-                const float4 *xr = reinterpret_cast<const float4 *>(smem + (x_raw(s) - base));
-                unsigned char *xe = smem + (x_exp(s) - base);
-                for (int i = t; i < rp * 8; i += 128) {
-                    const int q = i >> 3, ch = i & 7;
-                    const float4 v = xr[i];  // (xr0, xi0, xr1, xi1)
-                    const float4 re = make_float4(v.x, -v.y, v.z, -v.w);
-                    const float4 im = make_float4(v.y, v.x, v.w, v.z);
-                    const float4 rh = tf32x4(re), ih = tf32x4(im);
-                    *reinterpret_cast<float4 *>(xe + sw128(2 * q, ch)) = rh;
-                    *reinterpret_cast<float4 *>(xe + sw128(2 * q + 1, ch)) = ih;
-                    *reinterpret_cast<float4 *>(xe + sw128(2 * rp + 2 * q, ch)) = tf32x4(sub4(re, rh));
-                    *reinterpret_cast<float4 *>(xe + sw128(2 * rp + 2 * q + 1, ch)) = tf32x4(sub4(im, ih));
+                const float4 *xr = reinterpret_cast<const float4 *>(smem + (x_raw(r) - base));
+                unsigned char *xe = smem + (x_exp(o) - base);
+#pragma unroll
+                for (int k = 0; k < XP; ++k) {
+                    const int i = t + k * NT;
+                    if (i < rp * 8) {
+                        const float4 v = xr[i];  // (xr0, xi0, xr1, xi1)
+                        const float4 re = make_float4(v.x, -v.y, v.z, -v.w);
+                        const float4 im = make_float4(v.y, v.x, v.w, v.z);
+                        const float4 rh = tf32n4(re), ih = tf32n4(im);
+                        *reinterpret_cast<float4 *>(xe + xo[k][0]) = rh;
+                        *reinterpret_cast<float4 *>(xe + xo[k][1]) = ih;
+                        *reinterpret_cast<float4 *>(xe + xo[k][2]) = tf32n4(sub4(re, rh));
+                        *reinterpret_cast<float4 *>(xe + xo[k][3]) = tf32n4(sub4(im, ih));
+                    }
                 }
                 fence_proxy_async();  // generic-proxy stores -> visible to the tensor core
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&ready[s]);
+                if (lane == 0) {
+                    mbar_arrive(&rfree[r]);  // raw stage read (its values are in the stores above)
+                    mbar_arrive(&ready[o]);
+                }
                 ++kbg;
             }
         }
         if (!ok && !*abort_v) fail();
-    } else {  // ---------------- epilogue (warps 6-9: TMEM lane quarters 2, 3, 0, 1)
+    } else {  // ---------------- epilogue (4 warps: TMEM lane quarters warp % 4)
         const int q4 = warp & 3;
         const uint32_t lane_base = (uint32_t)(32 * q4) << 16;
         uint32_t tc = 0;
@@ -365,16 +410,18 @@ ztoep_status_t launch_cgemm_tc2(const CgemmArgs &a, int nprob, int nsm, cudaStre
     g.ksplit = (a.K + kc - 1) / kc;
     g.mtiles = (a.M + 127) / 128;
     g.nprob = nprob;
-    const size_t stage = 32768 + 640 * (size_t)g.rp;
-    g.nstage = (int)std::min<size_t>(G2_MAXST, (G2_SMEM_CAP - 1024) / stage);
-    if (g.nstage < 2) return ZTOEP_ERR_UNSUPPORTED;
+    const size_t op_bytes = 32768 + 512 * (size_t)g.rp, raw_bytes = 16384 + 128 * (size_t)g.rp;
+    if (G2_SMEM_CAP < 1024 + 2 * op_bytes + 2 * raw_bytes) return ZTOEP_ERR_UNSUPPORTED;
+    // three operand stages when four raw stages still fit beside them
+    g.nop = G2_SMEM_CAP >= 1024 + 3 * op_bytes + 4 * raw_bytes ? 3 : 2;
+    g.nraw = (int)std::min<size_t>(G2_MAXRAW, (G2_SMEM_CAP - 1024 - g.nop * op_bytes) / raw_bytes);
     uint32_t cols = 32;
     while (cols < (uint32_t)(8 * g.rp)) cols <<= 1;
     g.tmem_cols = cols;
     CUtensorMap ma, mx;
     if (!make_map(&ma, a.A, a.K, a.M, a.lda, nprob, a.strideA, 128, true)) return ZTOEP_ERR_UNSUPPORTED;
     if (!make_map(&mx, a.X, a.K, a.N, a.ldx, nprob, a.strideX, g.rp, false)) return ZTOEP_ERR_UNSUPPORTED;
-    const size_t smem = (size_t)g.nstage * stage + 1024;
+    const size_t smem = (size_t)g.nop * op_bytes + (size_t)g.nraw * raw_bytes + 1024;
     static bool attr = false;
     if (!attr) {
         ZT_CUDA(cudaFuncSetAttribute(k_cgemm_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G2_SMEM_CAP));
