@@ -53,6 +53,7 @@ constexpr int G2_THREADS = 448;  // 14 warps
 constexpr int G2_TW = 8;         // warps converting operands
 constexpr int G2_MAXRP = 64;
 constexpr int G2_MAXRAW = 8;
+constexpr int G2_KPR = 2;  // k-blocks per raw stage (one TMA box per operand)
 constexpr uint32_t G2_WAIT = 1u << 22;
 constexpr size_t G2_SMEM_CAP = 227 * 1024 - 1024;  // per-block limit minus static shared memory
 enum { G2_ERRBIT = 4 };
@@ -121,14 +122,17 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
     unsigned char *smem = g2_smem_raw + (base - raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int NR = g.nraw, NO = g.nop, rp = g.rp;
-    // operand ring (2 stages): A hi (16 KB) | A lo (16 KB) | X expanded [4 rp][128 B]
-    // raw ring (NR stages):    A as loaded (16 KB, 128B swizzle) | X as loaded [rp][128 B]
-    const uint32_t op_bytes = 32768u + 512u * (uint32_t)rp, raw_bytes = 16384u + 128u * (uint32_t)rp;
+    // operand ring (NO stages, one k-block each): A hi (16 KB) | A lo (16 KB) |
+    //   X expanded [4 rp][128 B], all 128B-swizzled K-major tiles
+    // raw ring (NR stages, G2_KPR k-blocks each, as loaded, row-major):
+    //   A [128][G2_KPR x 128 B] | X [rp][G2_KPR x 128 B]
+    constexpr uint32_t RW = 128u * G2_KPR;  // bytes of a raw row
+    const uint32_t op_bytes = 32768u + 512u * (uint32_t)rp, raw_bytes = (128u + (uint32_t)rp) * RW;
     auto a_hi = [&](int o) { return base + (uint32_t)o * op_bytes; };
     auto a_lo = [&](int o) { return a_hi(o) + 16384u; };
     auto x_exp = [&](int o) { return a_hi(o) + 32768u; };
     auto a_raw = [&](int r) { return base + (uint32_t)NO * op_bytes + (uint32_t)r * raw_bytes; };
-    auto x_raw = [&](int r) { return a_raw(r) + 16384u; };
+    auto x_raw = [&](int r) { return a_raw(r) + 128u * RW; };
 
     if (threadIdx.x == 0) {
         for (int r = 0; r < NR; ++r) {
@@ -165,12 +169,12 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {  // ---------------- producer: raw ring
-            const uint32_t tx = 16384u + (uint32_t)rp * 128u;
-            uint32_t kbg = 0;
+            const uint32_t tx = raw_bytes;
+            uint32_t kbg = 0;  // raw stages issued
             bool ok = true;
             for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
                 const Item w = decode(g, it);
-                for (int kb = 0; kb < w.nkb; ++kb) {
+                for (int kb = 0; kb < w.nkb; kb += G2_KPR) {
                     const int r = (int)(kbg % NR);
                     const uint32_t n = kbg / NR;
                     if (n > 0 && !mbar_wait_bounded(&rfree[r], (n - 1) & 1, G2_WAIT)) {
@@ -237,65 +241,79 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
     } else if (warp < 2 + G2_TW) {  // ---------------- raw -> operands (G2_TW warps)
         constexpr int NT = 32 * G2_TW;
         const int t = threadIdx.x - 64;
-        // this thread's (row, 16-byte chunk) pieces of the raw X tile and their
-        // four destinations in the expanded tile: fixed for the whole kernel
+        // this thread's (row, 16-byte chunk) pieces of an A and an X k-block:
+        // offsets in the raw row-major tile and in the swizzled operand tile,
+        // fixed for the whole kernel
+        constexpr int AP = 1024 / NT;
         constexpr int XP = (G2_MAXRP * 8 + NT - 1) / NT;
-        uint32_t xo[XP][4];
+        uint32_t ai[AP], ao[AP], xi[XP], xo[XP][4];
+#pragma unroll
+        for (int k = 0; k < AP; ++k) {
+            const int i = t + k * NT, row = i >> 3, ch = i & 7;
+            ai[k] = (uint32_t)row * RW + (uint32_t)ch * 16u;
+            ao[k] = sw128(row, ch);
+        }
 #pragma unroll
         for (int k = 0; k < XP; ++k) {
             const int i = t + k * NT, q = i >> 3, ch = i & 7;
+            xi[k] = (uint32_t)q * RW + (uint32_t)ch * 16u;
             xo[k][0] = sw128(2 * q, ch);
             xo[k][1] = sw128(2 * q + 1, ch);
             xo[k][2] = sw128(2 * rp + 2 * q, ch);
             xo[k][3] = sw128(2 * rp + 2 * q + 1, ch);
         }
-        uint32_t kbg = 0;
+        uint32_t rg = 0, kbg = 0;  // raw stages and k-blocks consumed
         bool ok = true;
         for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
             const Item w = decode(g, it);
-            for (int kb = 0; kb < w.nkb; ++kb) {
-                const int r = (int)(kbg % NR), o = (int)(kbg % NO);
-                const uint32_t n = kbg / NR, no = kbg / NO;
-                if (*abort_v || !mbar_wait_bounded(&full[r], n & 1, G2_WAIT) ||
-                    (no > 0 && !mbar_wait_bounded(&ofree[o], (no - 1) & 1, G2_WAIT))) {
+            for (int kb0 = 0; kb0 < w.nkb && ok; kb0 += G2_KPR) {
+                const int r = (int)(rg % NR);
+                if (*abort_v || !mbar_wait_bounded(&full[r], (rg / NR) & 1, G2_WAIT)) {
                     ok = false;
                     break;
                 }
-                // A: hi and lo at the loaded tile's offsets (elementwise, so the swizzle carries over)
-                const float4 *ar = reinterpret_cast<const float4 *>(smem + (a_raw(r) - base));
-                float4 *ah = reinterpret_cast<float4 *>(smem + (a_hi(o) - base));
-                float4 *al = reinterpret_cast<float4 *>(smem + (a_lo(o) - base));
-#pragma unroll
-                for (int k = 0; k < 1024 / NT; ++k) {
-                    const int i = t + k * NT;
-                    const float4 v = ar[i];
-                    const float4 h = tf32n4(v);
-                    ah[i] = h;
-                    al[i] = tf32n4(sub4(v, h));
-                }
-                const float4 *xr = reinterpret_cast<const float4 *>(smem + (x_raw(r) - base));
-                unsigned char *xe = smem + (x_exp(o) - base);
-#pragma unroll
-                for (int k = 0; k < XP; ++k) {
-                    const int i = t + k * NT;
-                    if (i < rp * 8) {
-                        const float4 v = xr[i];  // (xr0, xi0, xr1, xi1)
-                        const float4 re = make_float4(v.x, -v.y, v.z, -v.w);
-                        const float4 im = make_float4(v.y, v.x, v.w, v.z);
-                        const float4 rh = tf32n4(re), ih = tf32n4(im);
-                        *reinterpret_cast<float4 *>(xe + xo[k][0]) = rh;
-                        *reinterpret_cast<float4 *>(xe + xo[k][1]) = ih;
-                        *reinterpret_cast<float4 *>(xe + xo[k][2]) = tf32n4(sub4(re, rh));
-                        *reinterpret_cast<float4 *>(xe + xo[k][3]) = tf32n4(sub4(im, ih));
+                const unsigned char *ar = smem + (a_raw(r) - base);
+                const unsigned char *xr = smem + (x_raw(r) - base);
+                for (int sub = 0; sub < G2_KPR && kb0 + sub < w.nkb; ++sub) {
+                    const int o = (int)(kbg % NO);
+                    const uint32_t no = kbg / NO;
+                    if (no > 0 && !mbar_wait_bounded(&ofree[o], (no - 1) & 1, G2_WAIT)) {
+                        ok = false;
+                        break;
                     }
+                    unsigned char *ah = smem + (a_hi(o) - base);
+                    unsigned char *al = smem + (a_lo(o) - base);
+                    const uint32_t so = (uint32_t)sub * 128u;
+#pragma unroll
+                    for (int k = 0; k < AP; ++k) {
+                        const float4 v = *reinterpret_cast<const float4 *>(ar + ai[k] + so);
+                        const float4 h = tf32n4(v);
+                        *reinterpret_cast<float4 *>(ah + ao[k]) = h;
+                        *reinterpret_cast<float4 *>(al + ao[k]) = tf32n4(sub4(v, h));
+                    }
+                    unsigned char *xe = smem + (x_exp(o) - base);
+#pragma unroll
+                    for (int k = 0; k < XP; ++k) {
+                        if (t + k * NT < rp * 8) {
+                            const float4 v = *reinterpret_cast<const float4 *>(xr + xi[k] + so);  // (xr0, xi0, xr1, xi1)
+                            const float4 re = make_float4(v.x, -v.y, v.z, -v.w);
+                            const float4 im = make_float4(v.y, v.x, v.w, v.z);
+                            const float4 rh = tf32n4(re), ih = tf32n4(im);
+                            *reinterpret_cast<float4 *>(xe + xo[k][0]) = rh;
+                            *reinterpret_cast<float4 *>(xe + xo[k][1]) = ih;
+                            *reinterpret_cast<float4 *>(xe + xo[k][2]) = tf32n4(sub4(re, rh));
+                            *reinterpret_cast<float4 *>(xe + xo[k][3]) = tf32n4(sub4(im, ih));
+                        }
+                    }
+                    fence_proxy_async();  // generic-proxy stores -> visible to the tensor core
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&ready[o]);
+                    ++kbg;
                 }
-                fence_proxy_async();  // generic-proxy stores -> visible to the tensor core
+                if (!ok) break;
                 __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(&rfree[r]);  // raw stage read (its values are in the stores above)
-                    mbar_arrive(&ready[o]);
-                }
-                ++kbg;
+                if (lane == 0) mbar_arrive(&rfree[r]);  // raw stage read (its values are in the stores above)
+                ++rg;
             }
         }
         if (!ok && !*abort_v) fail();
@@ -373,7 +391,7 @@ bool make_map(CUtensorMap *m, const float2 *base, int K, int rows, int64_t ld, i
     if (!fn) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)(2 * (int64_t)K), (cuuint64_t)rows, (cuuint64_t)nprob};
     const cuuint64_t strides[2] = {(cuuint64_t)(ld * 8), (cuuint64_t)((nprob > 1 ? stride : ld * rows) * 8)};
-    const cuuint32_t box[3] = {32u, (cuuint32_t)box_rows, 1u};
+    const cuuint32_t box[3] = {(cuuint32_t)(32 * G2_KPR), (cuuint32_t)box_rows, 1u};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2 *>(base), dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -410,7 +428,7 @@ ztoep_status_t launch_cgemm_tc2(const CgemmArgs &a, int nprob, int nsm, cudaStre
     g.ksplit = (a.K + kc - 1) / kc;
     g.mtiles = (a.M + 127) / 128;
     g.nprob = nprob;
-    const size_t op_bytes = 32768 + 512 * (size_t)g.rp, raw_bytes = 16384 + 128 * (size_t)g.rp;
+    const size_t op_bytes = 32768 + 512 * (size_t)g.rp, raw_bytes = (128 + (size_t)g.rp) * 128 * G2_KPR;
     if (G2_SMEM_CAP < 1024 + 2 * op_bytes + 2 * raw_bytes) return ZTOEP_ERR_UNSUPPORTED;
     // three operand stages when four raw stages still fit beside them
     g.nop = G2_SMEM_CAP >= 1024 + 3 * op_bytes + 4 * raw_bytes ? 3 : 2;
@@ -419,7 +437,7 @@ ztoep_status_t launch_cgemm_tc2(const CgemmArgs &a, int nprob, int nsm, cudaStre
     while (cols < (uint32_t)(8 * g.rp)) cols <<= 1;
     g.tmem_cols = cols;
     CUtensorMap ma, mx;
-    if (!make_map(&ma, a.A, a.K, a.M, a.lda, nprob, a.strideA, 128, true)) return ZTOEP_ERR_UNSUPPORTED;
+    if (!make_map(&ma, a.A, a.K, a.M, a.lda, nprob, a.strideA, 128, false)) return ZTOEP_ERR_UNSUPPORTED;
     if (!make_map(&mx, a.X, a.K, a.N, a.ldx, nprob, a.strideX, g.rp, false)) return ZTOEP_ERR_UNSUPPORTED;
     const size_t smem = (size_t)g.nop * op_bytes + (size_t)g.nraw * raw_bytes + 1024;
     static bool attr = false;
