@@ -81,6 +81,9 @@ struct Fft1D {
     int L;
     int nst;
     int rad[12];
+    // per stage: the sub-transform length Ns entering it and M = 65536 / Ns + 1,
+    // so that j / Ns == (j * M) >> 16 for every j < 256 (j < L / radix here)
+    int ns[12], mag[12];
 };
 
 // Radix sequence for length L: order 0 takes radix 4 first (then 2, 3, 5),

@@ -74,14 +74,14 @@ template <> __device__ __forceinline__ void dft_small<5, double2>(double2 *a, bo
 // Layout in shared memory: element (pos, ch) at pos*ib + ch, ib = 1 << lib.
 template <int RAD, typename C>
 __device__ __forceinline__ void stockham_stage(const C *__restrict__ src, C *__restrict__ dst, int L,
-                                               int Ns, int lib, const C *__restrict__ tws, bool inv) {
+                                               int Ns, int mag, int lib, const C *__restrict__ tws, bool inv) {
     const int nbf = L / RAD;
     const int span = L / (Ns * RAD);
     const int items = nbf << lib;
     const int mask = (1 << lib) - 1;
     for (int item = threadIdx.x; item < items; item += blockDim.x) {
         const int j = item >> lib, ch = item & mask;
-        const int k = j % Ns;
+        const int k = j - (int)(((unsigned)j * (unsigned)mag) >> 16) * Ns;  // j mod Ns (j < 256)
         C a[RAD];
 #pragma unroll
         for (int r = 0; r < RAD; ++r) a[r] = src[((j + r * nbf) << lib) + ch];
@@ -120,12 +120,12 @@ __global__ void __launch_bounds__(256) k_fft_pass(Fft1D pl, const cplx_t<R> *__r
     C *src = A, *dst = Bf;
     int Ns = 1;
     for (int s = 0; s < pl.nst; ++s) {
-        const int rad = pl.rad[s];
+        const int rad = pl.rad[s], mag = pl.mag[s];
         switch (rad) {
-            case 4: stockham_stage<4>(src, dst, L, Ns, lib, tws, inv != 0); break;
-            case 2: stockham_stage<2>(src, dst, L, Ns, lib, tws, inv != 0); break;
-            case 3: stockham_stage<3>(src, dst, L, Ns, lib, tws, inv != 0); break;
-            default: stockham_stage<5>(src, dst, L, Ns, lib, tws, inv != 0); break;
+            case 4: stockham_stage<4>(src, dst, L, Ns, mag, lib, tws, inv != 0); break;
+            case 2: stockham_stage<2>(src, dst, L, Ns, mag, lib, tws, inv != 0); break;
+            case 3: stockham_stage<3>(src, dst, L, Ns, mag, lib, tws, inv != 0); break;
+            default: stockham_stage<5>(src, dst, L, Ns, mag, lib, tws, inv != 0); break;
         }
         __syncthreads();
         C *t = src; src = dst; dst = t;

@@ -570,47 +570,49 @@ __global__ void __launch_bounds__(256) k_edge2(const float2 *__restrict__ x, con
 }
 
 // y_E[r][e] = sum_tile Ep[tile][r][e] + sum_e' C[e][e'] x_E[r][e'].  A CTA
-// owns 32 edge rows of one RHS: thread (g, l) adds tiles g, g+8, ... of row
-// e0+l (coalesced over l, four accumulators), the 8 group sums are added in
-// order, and each warp forms C x_E for 4 of the rows.
+// owns 8 edge rows of one RHS: thread (g, l), g < 32, adds tiles g, g+32, ...
+// of row e0+l (four accumulators), the 32 group sums are added by a pairwise
+// tree in a fixed order, and warp w forms the C x_E term of row e0+w.
 __global__ void __launch_bounds__(256) k_edge_finish2(const float2 *__restrict__ x, const float2 *__restrict__ Cm,
                                                       const float2 *__restrict__ Ep, float2 *__restrict__ y,
                                                       int64_t NT, int E, int64_t N, int nrhs, int ntile) {
-    __shared__ float2 red[8][32];
-    __shared__ float2 cx[32];
-    const int l = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const int e0 = blockIdx.x * 32, r = blockIdx.y;
+    __shared__ float2 red[32][8];
+    __shared__ float2 cx[8];
+    const int l = threadIdx.x & 7, g = threadIdx.x >> 3;
+    const int e0 = blockIdx.x * 8, r = blockIdx.y;
     const int e = e0 + l;
     float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
     if (e < E) {
+        const float2 *col = Ep + (int64_t)r * E + e;
+        const int64_t ts = (int64_t)nrhs * E;  // stride between tiles
         int t = g;
-        for (; t + 24 < ntile; t += 32) {
-            s0 = s0 + Ep[((int64_t)t * nrhs + r) * E + e];
-            s1 = s1 + Ep[((int64_t)(t + 8) * nrhs + r) * E + e];
-            s2 = s2 + Ep[((int64_t)(t + 16) * nrhs + r) * E + e];
-            s3 = s3 + Ep[((int64_t)(t + 24) * nrhs + r) * E + e];
+        for (; t + 96 < ntile; t += 128) {
+            s0 = s0 + col[(int64_t)t * ts];
+            s1 = s1 + col[(int64_t)(t + 32) * ts];
+            s2 = s2 + col[(int64_t)(t + 64) * ts];
+            s3 = s3 + col[(int64_t)(t + 96) * ts];
         }
-        for (; t < ntile; t += 8) s0 = s0 + Ep[((int64_t)t * nrhs + r) * E + e];
+        for (; t < ntile; t += 32) s0 = s0 + col[(int64_t)t * ts];
     }
     red[g][l] = (s0 + s1) + (s2 + s3);
-    const float2 *xe = x + (int64_t)r * N + NT;
-    for (int k = 0; k < 4; ++k) {
-        const int row = g * 4 + k, er = e0 + row;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    {
+        const int er = e0 + w;
         float2 c = make_float2(0.f, 0.f);
         if (er < E) {
             const float2 *crow = Cm + (int64_t)er * E;
-            for (int j = l; j < E; j += 32) c = cfma(crow[j], xe[j], c);
+            const float2 *xe = x + (int64_t)r * N + NT;
+            for (int j = lane; j < E; j += 32) c = cfma(crow[j], xe[j], c);
         }
         c = warp_sum<float>(c);
-        if (l == 0) cx[row] = c;
+        if (lane == 0) cx[w] = c;
     }
     __syncthreads();
-    if (g == 0 && e < E) {
-        float2 sum = red[0][l];
-#pragma unroll
-        for (int k = 1; k < 8; ++k) sum = sum + red[k][l];
-        y[(int64_t)r * N + NT + e] = sum + cx[l];
+    for (int h = 16; h > 0; h >>= 1) {
+        if (g < h) red[g][l] = red[g][l] + red[g + h][l];
+        __syncthreads();
     }
+    if (threadIdx.x < 8 && e < E) y[(int64_t)r * N + NT + e] = red[0][l] + cx[l];
 }
 
 // ------------------------------------------------------------ conversions
@@ -855,7 +857,7 @@ static ztoep_status_t launch_edge2(ztoep_plan_t p, int nrhs, const float2 *x, fl
             k_edge2<4><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc);
         ZT_CUDA(cudaGetLastError());
     }
-    dim3 gf((p->E + 31) / 32, nrhs);
+    dim3 gf((p->E + 7) / 8, nrhs);
     KScope ks(K_MISC, s);
     k_edge_finish2<<<gf, 256, 0, s>>>(x, p->C32, Ep, y, p->NT, p->E, p->N, nrhs, ntile);
     ZT_CUDA(cudaGetLastError());

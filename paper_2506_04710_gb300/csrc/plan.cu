@@ -43,6 +43,12 @@ Fft1D make_fft1d(int L, int order) {
     while (n % 5 == 0) { f.rad[f.nst++] = 5; n /= 5; }
     if (order == 1)
         for (int i = 0, j = f.nst - 1; i < j; ++i, --j) std::swap(f.rad[i], f.rad[j]);
+    int Ns = 1;
+    for (int s = 0; s < f.nst; ++s) {
+        f.ns[s] = Ns;
+        f.mag[s] = 65536 / Ns + 1;
+        Ns *= f.rad[s];
+    }
     return f;
 }
 
