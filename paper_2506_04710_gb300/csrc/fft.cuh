@@ -100,8 +100,48 @@ __device__ __forceinline__ void stockham_stage(const C *__restrict__ src, C *__r
     }
 }
 
+// FP32 stage on channel pairs: element (pos, 2 c2), (pos, 2 c2 + 1) is one
+// 16-byte value at pos * ib/2 + c2, so each item moves two channels with one
+// load/store per point and shares the twiddle and index arithmetic.
+template <int RAD>
+__device__ __forceinline__ void stockham_stage_v2(const float4 *__restrict__ src, float4 *__restrict__ dst, int L,
+                                                  int Ns, int mag, int lib1, const float2 *__restrict__ tws,
+                                                  bool inv) {
+    const int nbf = L / RAD;
+    const int span = L / (Ns * RAD);
+    const int items = nbf << lib1;
+    const int mask = (1 << lib1) - 1;
+    for (int item = threadIdx.x; item < items; item += blockDim.x) {
+        const int j = item >> lib1, c2 = item & mask;
+        const int k = j - (int)(((unsigned)j * (unsigned)mag) >> 16) * Ns;  // j mod Ns (j < 256)
+        float2 a[RAD], c[RAD];
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) {
+            const float4 v = src[((j + r * nbf) << lib1) + c2];
+            a[r] = make_float2(v.x, v.y);
+            c[r] = make_float2(v.z, v.w);
+        }
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < RAD; ++r) {
+                float2 w = tws[r * k * span];
+                if (inv) w.y = -w.y;
+                a[r] = cmul(a[r], w);
+                c[r] = cmul(c[r], w);
+            }
+        }
+        dft_small<RAD>(a, inv);
+        dft_small<RAD>(c, inv);
+        const int base = (j - k) * RAD + k;
+#pragma unroll
+        for (int q = 0; q < RAD; ++q)
+            dst[((base + q * Ns) << lib1) + c2] = make_float4(a[q].x, a[q].y, c[q].x, c[q].y);
+    }
+}
+
 // Generic pass: load L x ib values, transform along the L axis, store.
-// Shared memory: tw[L] + 2 buffers of L*ib.
+// Shared memory: tw[L] (padded to an even count) + 2 buffers of L*ib.  FP32
+// passes with ib >= 2 move channel pairs (functors' ld2/st2).
 template <typename R, typename Ld, typename St>
 __global__ void __launch_bounds__(256) k_fft_pass(Fft1D pl, const cplx_t<R> *__restrict__ tw, int lib,
                                                   int inv, Ld ld, St st) {
@@ -110,10 +150,36 @@ __global__ void __launch_bounds__(256) k_fft_pass(Fft1D pl, const cplx_t<R> *__r
     C *tws = reinterpret_cast<C *>(zt_smem);
     const int L = pl.L;
     const int ib = 1 << lib;
-    C *A = tws + L;
+    C *A = tws + ((L + 1) & ~1);
     C *Bf = A + (size_t)L * ib;
     for (int t = threadIdx.x; t < L; t += blockDim.x) tws[t] = tw[t];
     const int n = L << lib;
+    if constexpr (sizeof(C) == 8) {
+        if (lib >= 1) {
+            const int lib1 = lib - 1, mask2 = (ib >> 1) - 1, n2 = n >> 1;
+            float4 *A4 = reinterpret_cast<float4 *>(A), *B4 = reinterpret_cast<float4 *>(Bf);
+            for (int idx = threadIdx.x; idx < n2; idx += blockDim.x)
+                A4[idx] = ld.ld2(idx >> lib1, (idx & mask2) << 1);
+            __syncthreads();
+            float4 *src = A4, *dst = B4;
+            int Ns = 1;
+            for (int s = 0; s < pl.nst; ++s) {
+                const int rad = pl.rad[s], mag = pl.mag[s];
+                switch (rad) {
+                    case 4: stockham_stage_v2<4>(src, dst, L, Ns, mag, lib1, tws, inv != 0); break;
+                    case 2: stockham_stage_v2<2>(src, dst, L, Ns, mag, lib1, tws, inv != 0); break;
+                    case 3: stockham_stage_v2<3>(src, dst, L, Ns, mag, lib1, tws, inv != 0); break;
+                    default: stockham_stage_v2<5>(src, dst, L, Ns, mag, lib1, tws, inv != 0); break;
+                }
+                __syncthreads();
+                float4 *t = src; src = dst; dst = t;
+                Ns *= rad;
+            }
+            for (int idx = threadIdx.x; idx < n2; idx += blockDim.x)
+                st.st2(idx >> lib1, (idx & mask2) << 1, src[idx]);
+            return;
+        }
+    }
     const int mask = ib - 1;
     for (int idx = threadIdx.x; idx < n; idx += blockDim.x) A[idx] = ld(idx >> lib, idx & mask);
     __syncthreads();
@@ -139,13 +205,13 @@ __global__ void __launch_bounds__(256) k_fft_pass(Fft1D pl, const cplx_t<R> *__r
 inline int pick_lib(int L, int channels, size_t csize, size_t budget, int cap = 64) {
     int lib = 0;
     while ((2 << lib) <= channels && (2 << lib) <= cap &&
-           (size_t)(L + 2 * (size_t)L * (2 << lib)) * csize <= budget)
+           (size_t)(((L + 1) & ~1) + 2 * (size_t)L * (2 << lib)) * csize <= budget)
         ++lib;
     return lib;
 }
 
 inline size_t fft_smem_bytes(int L, int lib, size_t csize) {
-    return (size_t)(L + 2 * (size_t)L * ((size_t)1 << lib)) * csize;
+    return (size_t)(((L + 1) & ~1) + 2 * (size_t)L * ((size_t)1 << lib)) * csize;
 }
 
 // Pass geometry: the channel batch is shrunk (down to 32-byte chunks per
