@@ -129,6 +129,24 @@ def peaks():
         return {}
 
 
+def profiled_traffic(profile: str, kernel_pattern: str):
+    """DRAM bytes per launch recorded by an ncu capture under profiles/, or None
+    when the kernel's source text has changed since the capture."""
+    import hashlib
+    import re
+    try:
+        text = open(os.path.join(ROOT, "profiles", profile)).read()
+        src = open(os.path.join(ROOT, "paper_2506_04710_gb300", "csrc", "matvec.cu")).read()
+    except OSError:
+        return None
+    t = re.search(r"traffic_bytes_per_launch: (\d+)", text)
+    h = re.search(r"kernel_source_sha256_16: (\w+)", text)
+    m = re.search(kernel_pattern, src, re.S)
+    if not (t and h and m) or hashlib.sha256(m.group(0).encode()).hexdigest()[:16] != h.group(1):
+        return None
+    return int(t.group(1))
+
+
 def oracle_product_seconds(prob, fraction: float):
     """CPU oracle: direct FP64 product on a row sample; returns (sample s, full-product s)."""
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
@@ -282,7 +300,10 @@ def run_ours(args, world, rank, local):
     bp_gbs = bp_bytes / (bp_us / 1e6) / 1e9 if bp_us > 0 else None
     roofline = {"kernel": "k_edge2 (FP32 B x_T and B^T x_E, one pass over B)", "bound": "hbm",
                 "achieved": edge_gbs, "peak": hbm, "unit": "GB/s",
-                "frac": (edge_gbs / hbm) if edge_gbs else None, "traffic": None,
+                "frac": (edge_gbs / hbm) if edge_gbs else None,
+                "traffic": profiled_traffic("k_edge2_c2_32x32_b64.md",
+                                            r"template <int RC>\n__global__ void __launch_bounds__\(256\) k_edge2\(.*?\n}\n"),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/k_edge2_c2_32x32_b64.md",
                 "bytes_per_launch": edge_bytes, "avg_launch_us": edge_us,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                 "timed": f"CUDA events around each k_edge launch over {nmv} FP32 products"}
