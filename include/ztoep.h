@@ -82,11 +82,24 @@ typedef enum {
  *   zero right-hand side there the solution there is exactly zero.
  * lx, ly: circulant embedding sizes; 0 = choose automatically (the smallest
  *   size >= 2n-1 whose prime factors are 2, 3 and 5).  Explicit sizes must be
- *   >= 2n-1, <= 256 and have only those prime factors. */
+ *   >= 2n-1, <= 256 and have only those prime factors.
+ * edge_per_cell: 0 = B is a general dense matrix.  k >= 1 declares the
+ *   perimeter layout: n_edge = 2k(nx + ny) edge unknowns, k per cell side,
+ *   ordered counter-clockwise from the corner (0, 0) (bottom side left to
+ *   right, right side upwards, top side right to left, left side downwards),
+ *   so that each side's block of B is one-level block Toeplitz along its side
+ *   (the side blocks of Sec. II-C, Eqs. submatrixB12/B34): the entry of edge
+ *   unknown (cell c, sub-position s) and element (m, n) depends on c - m (top
+ *   and bottom) or c - n (left and right).  The plan then keeps the 2-D spectra
+ *   of the 4k side generators instead of B and applies B and B^T in the
+ *   frequency domain of the FFT product.  The structure is verified on B at
+ *   plan time (relative 1e-11 of max |B|, columns of absent elements
+ *   excepted); a B that does not have it is rejected with ARG. */
 typedef struct {
     int32_t nx, ny, b, n_edge;
     const uint8_t *active;
     int32_t lx, ly;
+    int32_t edge_per_cell;
 } ztoep_desc_t;
 
 typedef struct {
@@ -129,7 +142,8 @@ ZTOEP_API ztoep_status_t ztoep_default_opts(ztoep_solve_opts_t *opts);
 /* Build a plan: embed the generating blocks in the Lx x Ly block circulant,
  * FFT them over (m, n) in FP64 (Eq. submatrixAA structure), keep the
  * transformed blocks of one frequency of each pair {f, -f} resident in FP64
- * and FP32, and keep B (absent elements' columns zeroed) and C in FP64 and
+ * and FP32, and keep B (absent elements' columns zeroed; or, with
+ * desc->edge_per_cell, the spectra of its side generators) and C in FP64 and
  * FP32.
  *   T: device complex128 [2ny-1][2nx-1][b][b]; T[q+ny-1][p+nx-1] is the
  *      block of offset (p, q) = (m-m', n-n').
@@ -166,7 +180,8 @@ ZTOEP_API ztoep_status_t ztoep_matvec(ztoep_plan_t plan, int32_t prec, int32_t n
  *   capture.  All calls share the array: calls whose work overlaps on the GPU
  *   (other streams, other threads) race and must be serialised by the caller.
  *   No cudaMalloc, cudaFree or allocating library routine is called.
- * Errors: ARG, NOMEM (scratch cap), CUDA, UNSUPPORTED (device index >= 64). */
+ * Errors: ARG, NOMEM (scratch cap), CUDA, UNSUPPORTED (device index >= 64,
+ * or a plan built with desc->edge_per_cell > 0, which keeps no dense B). */
 ZTOEP_API ztoep_status_t ztoep_edge_product_noalloc(ztoep_plan_t plan, int32_t nrhs, const void *X, void *Y,
                                                     void *stream);
 

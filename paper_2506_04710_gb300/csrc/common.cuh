@@ -116,6 +116,8 @@ struct MatvecWs {  // per-precision matvec workspace, sized for `cap` RHS
     void *ET = nullptr;     // [nsplit][cap][NT] B^T x_E partial sums
     void *Ep = nullptr;     // [ntile][cap][E]   B x_T partial sums
     void *Yh = nullptr;     // [F][cap][b] tensor-core block-product output (FP32, >= 16 RHS)
+    void *Fs = nullptr;     // [4k][cap][Lmax] side products B x_T along each side, frequency domain
+    void *Us = nullptr;     // [4k][cap][Lmax] DFTs of the side slices of x_E
     size_t bytes = 0;
 };
 
@@ -176,6 +178,9 @@ struct ztoep_plan_s {
     float2 *C32 = nullptr;
     float2 *That32full = nullptr;   // [F][b][b] every frequency, for the tensor-core product
     float2 *B32T = nullptr;         // [NT][E] transposed B, for the tensor-core B^T x_E
+    int side_k = 0;                 // > 0: perimeter side-Toeplitz B, k edge unknowns per cell side
+    double2 *G64 = nullptr;         // [4k][F][b] 2-D spectra of the side generators (replace B)
+    float2 *G32 = nullptr;
     size_t tc_bytes = 0;
     uint8_t *active = nullptr;      // [ny*nx] device copy, nullptr if all active
     double2 *twx64 = nullptr, *twy64 = nullptr;  // exp(-2 pi i t / L)
@@ -222,6 +227,15 @@ template <typename R> ztoep_status_t ensure_ws(ztoep_plan_t p, int nrhs);
 constexpr int kTcMinRhs = 16;
 constexpr int kTcMaxRhs = 256;
 ztoep_status_t ensure_tensor_data(ztoep_plan_t p, int nrhs, cudaStream_t s);
+// Perimeter side-Toeplitz edge coupling (sides.cu): plan-time generator
+// spectra from B; per product, the steps before and after the block product.
+ztoep_status_t sides_build(ztoep_plan_t p, const double2 *B, cudaStream_t s, size_t *acc);
+template <typename R>
+ztoep_status_t sides_pre(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, const cplx_t<R> *Xh, MatvecWs &w,
+                         cudaStream_t s);
+template <typename R>
+ztoep_status_t sides_post(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *y, cplx_t<R> *Yh, MatvecWs &w,
+                          cudaStream_t s);
 template <typename R> MatvecWs &ws_of(ztoep_plan_t p);
 template <typename R>
 ztoep_status_t run_forward_spectrum(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *Xh,

@@ -749,6 +749,7 @@ static int tc_edge_splits(ztoep_plan_t p) { return cgemm_splits((int)p->NT, tc_e
 
 static void free_ws(MatvecWs &w) {
     cudaFree(w.xin); cudaFree(w.yout); cudaFree(w.X1); cudaFree(w.Xh); cudaFree(w.ET); cudaFree(w.Ep); cudaFree(w.Yh);
+    cudaFree(w.Fs); cudaFree(w.Us);
     w = MatvecWs{};
 }
 
@@ -766,7 +767,11 @@ template <typename R> ztoep_status_t ensure_ws(ztoep_plan_t p, int nrhs) {
     ZT_TRY(dalloc(&w.X1, cs * nrhs * (size_t)p->ny * p->lx * p->b, &acc));
     ZT_TRY(dalloc(&w.Xh, cs * nrhs * (size_t)p->F * p->b, &acc));
     const bool tc = cs == 8 && nrhs >= kTcMinRhs;
-    if (p->E > 0) {
+    if (p->E > 0 && p->side_k > 0) {  // side products: small frequency-domain buffers only
+        const size_t side = cs * (size_t)4 * p->side_k * nrhs * std::max(p->lx, p->ly);
+        ZT_TRY(dalloc(&w.Fs, side, &acc));
+        ZT_TRY(dalloc(&w.Us, side, &acc));
+    } else if (p->E > 0) {
         ZT_TRY(dalloc(&w.ET, cs * (size_t)std::max(nsplit, 1) * nrhs * p->NT, &acc));
         const int parts = std::max(cs == 8 ? edge2_ntile(p) : ntile, tc ? tc_edge_splits(p) : 0);
         ZT_TRY(dalloc(&w.Ep, cs * (size_t)parts * nrhs * p->E, &acc));
@@ -976,7 +981,7 @@ static ztoep_status_t tc_blockprod(ztoep_plan_t p, int nrhs, const float2 *Xh, f
 
 template <typename R> static bool use_tensor(ztoep_plan_t p, int nrhs) {
     if (sizeof(R) != sizeof(float) || nrhs < kTcMinRhs || nrhs > kTcMaxRhs || !cgemm_fits(nrhs)) return false;
-    return p->That32full != nullptr && (p->E == 0 || p->B32T != nullptr);
+    return p->That32full != nullptr && (p->E == 0 || p->side_k > 0 || p->B32T != nullptr);
 }
 
 template <typename R>
@@ -987,9 +992,10 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
     cplx_t<R> *X1 = reinterpret_cast<cplx_t<R> *>(w.X1);
     cplx_t<R> *Xh = reinterpret_cast<cplx_t<R> *>(w.Xh);
     const int ntile = edge_ntile(p, cs);
-    const int nsplit = edge_nsplit(p, ntile, cs);
+    const int nsplit = p->side_k > 0 ? 0 : edge_nsplit(p, ntile, cs);
     const bool tc = use_tensor<R>(p, nrhs) && w.Yh != nullptr;
-    if (p->E > 0) {  // edge branch on the side stream, concurrent with the FFT chain
+    const bool sides = p->E > 0 && p->side_k > 0;
+    if (p->E > 0 && !sides) {  // edge branch on the side stream, concurrent with the FFT chain
         ZT_CUDA(cudaEventRecord(p->ev_fork, s));
         ZT_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
         if (tc)
@@ -1002,6 +1008,7 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
         ZT_CUDA(cudaEventRecord(p->ev_join, p->side));
     }
     ZT_TRY(forward_passes<R>(p, nrhs, x, X1, Xh, s));
+    if (sides) ZT_TRY(sides_pre<R>(p, nrhs, x, Xh, w, s));  // reads X^ before the in-place block product
     cplx_t<R> *Yh = Xh;
     if (tc) {
         Yh = reinterpret_cast<cplx_t<R> *>(w.Yh);
@@ -1009,13 +1016,14 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
     } else {
         ZT_TRY(launch_blockprod<R>(p, nrhs, Xh, s));
     }
+    if (sides) ZT_TRY(sides_post<R>(p, nrhs, x, y, Yh, w, s));  // B^T x_E into Y^, y_E
     const PassCfg cy = plan_pass_cfg(p, 1, p->ly, p->lx * nrhs, cs);
     const int iby = 1 << cy.lib;
     dim3 gy((p->b + iby - 1) / iby, p->lx, nrhs);
     ZT_TRY((launch_fft_pass<R>(p->fy, twy_of<R>(p), cy.lib, true, gy,
                                LdXh<R>{Yh, p->lx, p->b, iby, nrhs},
                                StY1<R>{X1, p->ny, p->lx, p->b, iby}, s, cy.threads)));
-    if (p->E > 0) ZT_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
+    if (p->E > 0 && !sides) ZT_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
     const PassCfg cx = plan_pass_cfg(p, 0, p->lx, p->ny * nrhs, cs);
     const int ibx = 1 << cx.lib;
     dim3 gx((p->b + ibx - 1) / ibx, p->ny, nrhs);
@@ -1093,7 +1101,7 @@ ztoep_status_t ensure_tensor_data(ztoep_plan_t p, int nrhs, cudaStream_t s) {
         k_expand_spectrum32<<<1024, 256, 0, s>>>(p->That32, p->rep, p->That32full, p->F, p->b);
         ZT_CUDA(cudaGetLastError());
     }
-    if (p->E > 0 && !p->B32T) {
+    if (p->E > 0 && p->side_k == 0 && !p->B32T) {
         ZT_TRY(dalloc((void **)&p->B32T, sizeof(float2) * (size_t)p->NT * p->E, &acc));
         dim3 g((unsigned)((p->NT + 31) / 32), (unsigned)((p->E + 31) / 32));
         KScope ks(K_MISC, s);
@@ -1169,6 +1177,7 @@ extern "C" ztoep_status_t ztoep_edge_product_noalloc(ztoep_plan_t p, int32_t nrh
     cudaStream_t s = (cudaStream_t)stream;
     double2 *y = (double2 *)Y;
     const double2 *x = (const double2 *)X;
+    if (p->side_k > 0) return ZTOEP_ERR_UNSUPPORTED;  // no dense B kept: use ztoep_matvec
     if (p->E == 0) {  // no edge unknowns: the edge part of the product is zero
         ZT_CUDA(cudaMemsetAsync(y, 0, sizeof(double2) * (size_t)nrhs * p->N, s));
         return ZTOEP_OK;

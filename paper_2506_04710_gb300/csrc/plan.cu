@@ -138,6 +138,13 @@ static bool valid_desc(const ztoep_desc_t *d) {
     if (d->ly != 0 && (d->ly < 2 * d->ny - 1 || d->ly > 256 || !is_smooth(d->ly))) return false;
     const int lx = d->lx ? d->lx : smooth_size_at_least(2 * d->nx - 1);
     const int ly = d->ly ? d->ly : smooth_size_at_least(2 * d->ny - 1);
+    if (d->edge_per_cell < 0 || d->edge_per_cell > 8) return false;
+    if (d->edge_per_cell > 0) {  // perimeter layout: exact count, no absent elements
+        if ((int64_t)d->n_edge != 2LL * d->edge_per_cell * (d->nx + d->ny)) return false;
+        if (d->active)
+            for (int k = 0; k < d->nx * d->ny; ++k)
+                if (!d->active[k]) return false;
+    }
     return lx <= 256 && ly <= 256;
 }
 
@@ -158,13 +165,16 @@ static int count_pairs(int lx, int ly, std::vector<int2> *pairs, std::vector<int
     return np;
 }
 
-static size_t plan_bytes(int nx, int ny, int b, int E, int lx, int ly) {
+static size_t plan_bytes(int nx, int ny, int b, int E, int lx, int ly, int side_k) {
     const int64_t NT = (int64_t)nx * ny * b;
     const int np = count_pairs(lx, ly, nullptr, nullptr);
     const int64_t ldb = edge_row_stride(NT);
     size_t s = 0;
     s += (size_t)np * b * b * (16 + 8);
-    s += (size_t)E * ldb * (16 + 8);
+    if (side_k > 0)
+        s += (size_t)4 * side_k * lx * ly * b * (16 + 8);  // side generator spectra
+    else
+        s += (size_t)E * ldb * (16 + 8);
     s += (size_t)E * E * (16 + 8);
     s += (size_t)lx * ly * (sizeof(int) + sizeof(int2)) + (size_t)(lx + ly) * 24 + (size_t)nx * ny + 64;
     return s;
@@ -217,7 +227,7 @@ void ztoep_plan_destroy(ztoep_plan_t p) {
     cudaFree(p->pairs); cudaFree(p->rep);
     cudaFree(p->That64); cudaFree(p->That32);
     cudaFree(p->B64); cudaFree(p->B32); cudaFree(p->C64); cudaFree(p->C32);
-    cudaFree(p->That32full); cudaFree(p->B32T);
+    cudaFree(p->That32full); cudaFree(p->B32T); cudaFree(p->G64); cudaFree(p->G32);
     cudaFree(p->active);
     cudaFree(p->twx64); cudaFree(p->twy64); cudaFree(p->twx32); cudaFree(p->twy32);
     cudaFree(p->err);
@@ -316,7 +326,14 @@ static ztoep_status_t plan_build(ztoep_plan_t p, const ztoep_desc_t *d, const do
     }
 
     // edge coupling blocks
-    if (p->E > 0) {
+    if (p->E > 0 && d->edge_per_cell > 0) {  // side generators instead of B
+        p->side_k = d->edge_per_cell;
+        ZT_TRY(sides_build(p, B, s, &acc));
+        ZT_TRY(dalloc((void **)&p->C64, sizeof(double2) * (size_t)p->E * p->E, &acc));
+        ZT_TRY(dalloc((void **)&p->C32, sizeof(float2) * (size_t)p->E * p->E, &acc));
+        ZT_CUDA(cudaMemcpyAsync(p->C64, C, sizeof(double2) * (size_t)p->E * p->E, cudaMemcpyDeviceToDevice, s));
+        ZT_TRY(launch_c128_to_c64(p->C64, p->C32, (int64_t)p->E * p->E, s));
+    } else if (p->E > 0) {
         const int64_t ldb = edge_row_stride(p->NT);
         ZT_TRY(dalloc((void **)&p->B64, sizeof(double2) * (size_t)p->E * ldb, &acc));
         ZT_TRY(dalloc((void **)&p->B32, sizeof(float2) * (size_t)p->E * ldb, &acc));
@@ -383,15 +400,16 @@ size_t ztoep_footprint(const ztoep_desc_t *d, int32_t max_nrhs, int32_t restart)
     const int lx = d->lx ? d->lx : smooth_size_at_least(2 * d->nx - 1);
     const int ly = d->ly ? d->ly : smooth_size_at_least(2 * d->ny - 1);
     const int64_t NT = (int64_t)d->nx * d->ny * d->b, N = NT + d->n_edge;
-    size_t s = plan_bytes(d->nx, d->ny, d->b, d->n_edge, lx, ly);
+    size_t s = plan_bytes(d->nx, d->ny, d->b, d->n_edge, lx, ly, d->edge_per_cell);
     // matvec workspaces (FP32 and FP64): in/out copies, x-pass lines, spectrum, edge partials
     const size_t per_rhs = (size_t)(2 * N + (int64_t)d->ny * lx * d->b + (int64_t)lx * ly * d->b + 8 * NT) * 24;
     s += per_rhs * max_nrhs;
     // Krylov basis and vectors (FP64)
     s += (size_t)max_nrhs * N * 16 * (restart + 8);
-    // tensor-core operands for 16+ RHS: full FP32 spectrum, transposed B, product output
+    // tensor-core operands for 16+ RHS: full FP32 spectrum, transposed B (dense B only), product output
     if (max_nrhs >= kTcMinRhs)
-        s += (size_t)lx * ly * d->b * d->b * 8 + (size_t)NT * d->n_edge * 8 + (size_t)lx * ly * d->b * max_nrhs * 8;
+        s += (size_t)lx * ly * d->b * d->b * 8 + (d->edge_per_cell ? 0 : (size_t)NT * d->n_edge * 8) +
+             (size_t)lx * ly * d->b * max_nrhs * 8;
     return s;
 }
 

@@ -313,7 +313,7 @@ ztoep_status_t ztoep_plan_autotune(const ztoep_desc_t *desc, const void *T, cons
             ztoep_status_t st = try_params(tp, false);
             if (st != ZTOEP_OK) return fail(st);
         }
-    } else if (best->E > 0) {
+    } else if (best->E > 0 && best->side_k == 0) {
         const int mt = (best->E + 63) / 64;
         const int want = std::max(1, (2 * best->nsm + mt - 1) / mt);
         const int kc0 = std::max(256, (int)((best->NT + want - 1) / want + 15) / 16 * 16);

@@ -97,6 +97,7 @@ class Problem:
     pts: np.ndarray
     edge_pts: np.ndarray
     name: str = ""
+    edge_layout: str = "one"
 
     @property
     def n_toep(self) -> int:
@@ -109,6 +110,16 @@ class Problem:
     @property
     def nrhs(self) -> int:
         return self.V.shape[0]
+
+    @property
+    def edge_per_cell(self) -> int:
+        """k when the edge unknowns are k per cell side on the whole perimeter
+        (E = 2k(Nx + Ny), equal spacing a/k from half a spacing after (0, 0)),
+        else 0."""
+        per = 2 * (self.nx + self.ny)
+        if self.n_edge == 0 or self.n_edge % per or self.edge_layout != "one":
+            return 0
+        return self.n_edge // per
 
 
 def basis_points(seed: int, b: int) -> np.ndarray:
@@ -237,7 +248,7 @@ def make_problem(nx: int, ny: int, b: int, n_edge: int, seed: int = 0, rhs: str 
         V = plane_waves(pos, seed, nrhs)
     else:
         raise ValueError(rhs)
-    return Problem(nx, ny, b, n_edge, seed, T, B, C, active, V, pts, edge_pts, name)
+    return Problem(nx, ny, b, n_edge, seed, T, B, C, active, V, pts, edge_pts, name, edge_layout)
 
 
 def manufactured_solution(prob: Problem, nrhs: int, seed: int | None = None) -> np.ndarray:

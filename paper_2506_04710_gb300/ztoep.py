@@ -41,7 +41,7 @@ class ZtoepError(RuntimeError):
 class Desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("b", ctypes.c_int32),
                 ("n_edge", ctypes.c_int32), ("active", ctypes.c_void_p),
-                ("lx", ctypes.c_int32), ("ly", ctypes.c_int32)]
+                ("lx", ctypes.c_int32), ("ly", ctypes.c_int32), ("edge_per_cell", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -208,7 +208,7 @@ def _hptr(a):
     return ctypes.c_void_p(a.ctypes.data)
 
 
-def make_desc(nx, ny, b, n_edge, active=None, lx=0, ly=0):
+def make_desc(nx, ny, b, n_edge, active=None, lx=0, ly=0, edge_per_cell=0):
     """Returns (Desc, keepalive) -- keep the second item alive while the Desc is used."""
     keep = None
     ap = None
@@ -216,7 +216,7 @@ def make_desc(nx, ny, b, n_edge, active=None, lx=0, ly=0):
         keep = np.ascontiguousarray(np.asarray(active, dtype=np.uint8).reshape(-1))
         assert keep.size == nx * ny
         ap = keep.ctypes.data
-    return Desc(nx, ny, b, n_edge, ap, lx, ly), keep
+    return Desc(nx, ny, b, n_edge, ap, lx, ly, edge_per_cell), keep
 
 
 def _check(st, what):
@@ -445,9 +445,10 @@ class Plan:
     """Owns a plan built from a synthetic Problem (or explicit arrays)."""
 
     def __init__(self, nx, ny, b, n_edge, T, B, C, active=None, lx=0, ly=0, stream=None, autotune: int = 0,
-                 tune: TuneInfo | None = None):
-        """autotune > 0: ztoep_plan_autotune for that many RHS; tune: ztoep_plan_tuned."""
-        self.desc, self._keep = make_desc(nx, ny, b, n_edge, active, lx, ly)
+                 tune: TuneInfo | None = None, edge_per_cell: int = 0):
+        """autotune > 0: ztoep_plan_autotune for that many RHS; tune: ztoep_plan_tuned;
+        edge_per_cell > 0: B has the perimeter side-Toeplitz layout (see ztoep.h)."""
+        self.desc, self._keep = make_desc(nx, ny, b, n_edge, active, lx, ly, edge_per_cell)
         self.tune = None
         if autotune:
             self.handle, self.tune = ztoep_plan_autotune(self.desc, T, B, C, autotune, stream)
@@ -459,13 +460,18 @@ class Plan:
         self.n = int(self.info.n)
 
     @classmethod
-    def from_problem(cls, prob, device="cuda", lx=0, ly=0, stream=None, autotune: int = 0, tune=None):
+    def from_problem(cls, prob, device="cuda", lx=0, ly=0, stream=None, autotune: int = 0, tune=None,
+                     structured: bool = False):
+        """structured: declare the problem's perimeter edge layout (prob.edge_per_cell) to the plan."""
         import torch
         T = torch.from_numpy(np.ascontiguousarray(prob.T)).to(device)
         B = torch.from_numpy(np.ascontiguousarray(prob.B)).to(device) if prob.n_edge else None
         C = torch.from_numpy(np.ascontiguousarray(prob.C)).to(device) if prob.n_edge else None
         act = prob.active if not prob.active.all() else None
-        p = cls(prob.nx, prob.ny, prob.b, prob.n_edge, T, B, C, act, lx, ly, stream, autotune, tune)
+        k = prob.edge_per_cell if structured else 0
+        if structured and not k:
+            raise ValueError("the problem's edge layout is not the perimeter side-Toeplitz one")
+        p = cls(prob.nx, prob.ny, prob.b, prob.n_edge, T, B, C, act, lx, ly, stream, autotune, tune, k)
         if stream is None:
             torch.cuda.current_stream().synchronize()
         else:

@@ -309,3 +309,58 @@ def test_oracle_gmres_converges_to_lu_solution():
     x, its, rel = oracle.gmres(prob, prob.V[0], restart=30, tol=1e-12, max_iter=500)
     assert rel <= 1e-12 and its < 500
     assert np.linalg.norm(x - xl) / np.linalg.norm(xl) <= 1e-10
+
+
+# ---------------------------------------------------------------- perimeter side layout
+def _side_edge(nx, ny, k, sg, c, s):
+    """Edge index of (side, cell, sub-position) in the counter-clockwise layout:
+    bottom (left to right), right (upwards), top and left stored in reverse."""
+    lens = (nx, ny, nx, ny)
+    base = (0, k * nx, k * (nx + ny), k * (2 * nx + ny))[sg]
+    if sg < 2:
+        return base + k * c + s
+    return base + k * (lens[sg] - 1 - c) + (k - 1 - s)
+
+
+@pytest.mark.parametrize("nx,ny,k", [(4, 4, 1), (6, 5, 2), (5, 7, 3), (3, 2, 4)])
+def test_perimeter_layout_positions_and_side_toeplitz(nx, ny, k):
+    """The perimeter points of the 'one' layout with E = 2k(nx+ny) sit at
+    (c + (s + 1/2)/k) a along each side, and each side's block of B depends on
+    the element only through c - m (bottom/top) or c - n (right/left): the
+    one-level block-Toeplitz side blocks of Sec. II-C (Eqs. submatrixB12/B34)."""
+    a = synth.PERIOD
+    prob = synth.make_problem(nx, ny, 5, 2 * k * (nx + ny), seed=4)
+    assert prob.edge_per_cell == k
+    for sg in range(4):
+        L = nx if sg % 2 == 0 else ny
+        for c in range(L):
+            for s in range(k):
+                along = (c + (s + 0.5) / k) * a
+                expect = [(along, 0.0), (nx * a, along), (along, ny * a), (0.0, along)][sg]
+                e = _side_edge(nx, ny, k, sg, c, s)
+                assert np.allclose(prob.edge_pts[e], expect, rtol=0, atol=1e-12)
+    B = prob.B.reshape(prob.n_edge, ny, nx, prob.b)  # [e][n][m][i]
+    scale = np.abs(B).max()
+    for sg in range(4):
+        L = nx if sg % 2 == 0 else ny
+        for s in range(k):
+            for c in range(L):
+                for c2 in range(L):
+                    d = c2 - c  # shifting the cell and the element by the same d
+                    e1, e2 = _side_edge(nx, ny, k, sg, c, s), _side_edge(nx, ny, k, sg, c2, s)
+                    if sg % 2 == 0:
+                        lo, hi = max(0, -d), min(nx, nx - d)
+                        if lo < hi:
+                            assert np.max(np.abs(B[e1, :, lo:hi] - B[e2, :, lo + d:hi + d])) <= 1e-12 * scale
+                    else:
+                        lo, hi = max(0, -d), min(ny, ny - d)
+                        if lo < hi:
+                            assert np.max(np.abs(B[e1, lo:hi] - B[e2, lo + d:hi + d])) <= 1e-12 * scale
+
+
+def test_edge_per_cell_only_for_the_full_perimeter_layout():
+    assert synth.make_problem(4, 4, 3, 16).edge_per_cell == 1
+    assert synth.make_problem(4, 4, 3, 15).edge_per_cell == 0
+    assert synth.make_problem(4, 4, 3, 0).edge_per_cell == 0
+    p = synth.make_problem(5, 3, 3, 16, gap_column=2, edge_layout="split")
+    assert p.edge_per_cell == 0
