@@ -203,8 +203,10 @@ def run_ours(args, world, rank, local):
     prob, tol = synth.config_problem(WORKLOAD)
     stream = torch.cuda.current_stream(dev)
 
+    structured = prob.edge_per_cell > 0 and args.structured_edges
     t0 = time.perf_counter()
-    plan = ztoep.Plan.from_problem(prob, device=dev, autotune=0 if args.no_autotune else prob.nrhs)
+    plan = ztoep.Plan.from_problem(prob, device=dev, autotune=0 if args.no_autotune else prob.nrhs,
+                                   structured=structured)
     torch.cuda.synchronize(dev)
     plan_ms = 1e3 * (time.perf_counter() - t0)
     tune = plan.tune.as_dict() if plan.tune is not None else None
@@ -283,7 +285,9 @@ def run_ours(args, world, rank, local):
         n, ms = ztoep.ztoep_timing_read(c)
         kt[name] = {"launches": n, "avg_us": 1e3 * ms / max(1, n)}
     That_bytes = plan.info.n_pairs * b * b * 8
-    mv_bytes = That_bytes + 2 * NT * nrhs * 8 + 4 * F * b * nrhs * 8 + (E * NT + E * E) * 8 + 4 * E * nrhs * 8
+    # edge coupling: dense B read once, or the 4k side-generator spectra read twice (B x_T, B^T x_E)
+    edge_stream = (2 * 4 * prob.edge_per_cell * F * b * 8) if structured else E * NT * 8
+    mv_bytes = That_bytes + 2 * NT * nrhs * 8 + 4 * F * b * nrhs * 8 + edge_stream + E * E * 8 + 4 * E * nrhs * 8
     mv_gbs = mv_bytes / (mv_ms / 1e3) / 1e9
 
     # roofline of the edge-coupling kernel (one pass over B, FP32), the largest
@@ -298,15 +302,28 @@ def run_ours(args, world, rank, local):
     bp_bytes = plan.info.n_pairs * b * b * 8 + 2 * F * b * nrhs * 8
     bp_us = kt["blockprod"]["avg_us"]
     bp_gbs = bp_bytes / (bp_us / 1e6) / 1e9 if bp_us > 0 else None
-    roofline = {"kernel": "k_edge2 (FP32 B x_T and B^T x_E, one pass over B)", "bound": "hbm",
-                "achieved": edge_gbs, "peak": hbm, "unit": "GB/s",
-                "frac": (edge_gbs / hbm) if edge_gbs else None,
-                "traffic": profiled_traffic("k_edge2_c2_32x32_b64.md",
-                                            r"template <int RC>\n__global__ void __launch_bounds__\(256\) k_edge2\(.*?\n}\n"),
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/k_edge2_c2_32x32_b64.md",
-                "bytes_per_launch": edge_bytes, "avg_launch_us": edge_us,
-                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-                "timed": f"CUDA events around each k_edge launch over {nmv} FP32 products"}
+    if structured:  # B is gone: the largest HBM stream is the spectrum in the block product
+        roofline = {"kernel": "k_blockprod_tma (FP32 per-frequency block product, half spectrum)", "bound": "hbm",
+                    "achieved": bp_gbs, "peak": hbm, "unit": "GB/s",
+                    "frac": (bp_gbs / hbm) if bp_gbs else None,
+                    "traffic": profiled_traffic("k_blockprod_tma_c2_32x32_b64.md",
+                                                r"template <typename R, int NST>\n__global__ void __launch_bounds__\(256\) k_blockprod_tma\(.*?\n}\n"),
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                      "profiles/k_blockprod_tma_c2_32x32_b64.md",
+                    "bytes_per_launch": bp_bytes, "avg_launch_us": bp_us,
+                    "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                    "timed": f"CUDA events around each block-product launch over {nmv} FP32 products"}
+    else:
+        roofline = {"kernel": "k_edge2 (FP32 B x_T and B^T x_E, one pass over B)", "bound": "hbm",
+                    "achieved": edge_gbs, "peak": hbm, "unit": "GB/s",
+                    "frac": (edge_gbs / hbm) if edge_gbs else None,
+                    "traffic": profiled_traffic("k_edge2_c2_32x32_b64.md",
+                                                r"template <int RC>\n__global__ void __launch_bounds__\(256\) k_edge2\(.*?\n}\n"),
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                      "profiles/k_edge2_c2_32x32_b64.md",
+                    "bytes_per_launch": edge_bytes, "avg_launch_us": edge_us,
+                    "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                    "timed": f"CUDA events around each k_edge launch over {nmv} FP32 products"}
 
     # ---- FP64 plain path on the same inputs
     o64 = opts(ztoep.ZTOEP_FP64)
@@ -356,10 +373,14 @@ def run_ours(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 products + f64 refinement",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC, "nx": prob.nx, "ny": prob.ny, "b": prob.b, "n_edge": E,
+                       "edge_coupling": (f"perimeter side-Toeplitz, {prob.edge_per_cell} per cell side "
+                                         "(side generator spectra)") if structured else "dense B",
                        "nrhs": nrhs, "tol": tol, "restart": args.restart, "lx": plan.info.lx,
                        "ly": plan.info.ly,
-                       "l2": "inputs larger than L2: FP32 working set per product "
-                             f"{(That_bytes + E * NT * 8) / 1e6:.0f} MB > 129 MB L2",
+                       "l2": "inputs larger than L2: each timed step (one whole solve) streams the plan "
+                             "(FP32 and FP64 spectra, edge data) and the Krylov basis, "
+                             f"{ztoep.ztoep_plan_get_info(plan.handle).resident_bytes / 1e6:.0f} MB resident "
+                             "> 129 MB L2",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -429,8 +450,9 @@ def serve_stream(args, prec_name, n_req, dev):
             time.sleep(wait)
         key = (nx << 40) | (b << 24) | (seed & 0xFFFFFF) | (1 << 62)
         t_sub = time.perf_counter() - t0
-        rid = sched.submit((nx, nx, b, 16 * nx), d["T"], d["B"], d["C"], d["V"], X, opts=o, plan_key=key,
-                           on_device=True)
+        k = 4  # E = 16 Nx on a square array: 4 per cell side (side-generator spectra, no dense B)
+        rid = sched.submit((nx, nx, b, 16 * nx, None, 0, 0, k), d["T"], d["B"], d["C"], d["V"], X, opts=o,
+                           plan_key=key, on_device=True)
         live[rid] = sum(t.numel() * 16 for t in (d["T"], d["B"], d["C"]))
         del d, X
         ids.append((rid, t_arr, nrhs, nx, b))
@@ -507,7 +529,9 @@ def run_product(args, local):
         prob = synth.make_problem(seed=0, name=key, **cfg)
     else:
         prob, _ = synth.config_problem(key)
-    plan = ztoep.Plan.from_problem(prob, device=dev, autotune=0 if args.no_autotune else prob.nrhs)
+    structured = prob.edge_per_cell > 0 and args.structured_edges
+    plan = ztoep.Plan.from_problem(prob, device=dev, autotune=0 if args.no_autotune else prob.nrhs,
+                                   structured=structured)
     nr, N, NT, E, b = prob.nrhs, prob.n, prob.n_toep, prob.n_edge, prob.b
     F = plan.info.lx * plan.info.ly
     s = torch.cuda.current_stream(dev)
@@ -537,11 +561,13 @@ def run_product(args, local):
             classes[n] = {"launches_per_product": k / args.steps, "us_per_product": 1e3 * t / args.steps}
     tensor = nr >= 16
     spec = F * b * b * 8 if tensor else plan.info.n_pairs * b * b * 8
-    bedge = (2 if tensor else 1) * E * NT * 8 + E * E * 8
+    k = prob.edge_per_cell
+    bedge = (2 * 4 * k * F * b * 8 if structured else (2 if tensor else 1) * E * NT * 8) + E * E * 8
     byts = spec + bedge + 2 * NT * nr * 8 + 4 * F * b * nr * 8
-    flops = 8.0 * F * b * b * nr + 16.0 * E * NT * nr
+    flops = 8.0 * F * b * b * nr + (16.0 * 4 * k * F * b * nr if structured else 16.0 * E * NT * nr)
     pk = peaks()
     line = {"mode": "product", "workload": key, "nrhs": nr, "n": N, "lx": plan.info.lx, "ly": plan.info.ly,
+            "edge_coupling": "side generator spectra" if structured else "dense B",
             "product_ms": ms, "algorithmic_bytes": byts, "GB/s": byts / ms / 1e6,
             "frac_of_hbm": byts / ms / 1e6 / pk["hbm_gbs"] if pk.get("hbm_gbs") else None,
             "complex_flops": flops, "tf32_tflops_3x": 3 * flops / ms / 1e9 if tensor else None,
@@ -560,6 +586,9 @@ def main():
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="heuristic launch shapes, smallest embedding")
+    ap.add_argument("--structured-edges", action="store_true",
+                    help="use the side-generator spectra when the edge unknowns have the perimeter "
+                         "side-Toeplitz layout (default: dense B; the serving mode always uses them)")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the solver loops from the host (for profilers; slower)")
     ap.add_argument("--serve", type=int, default=0,

@@ -115,9 +115,9 @@ struct MatvecWs {  // per-precision matvec workspace, sized for `cap` RHS
     void *Xh = nullptr;     // [F][cap][b] spectrum (block product runs in place)
     void *ET = nullptr;     // [nsplit][cap][NT] B^T x_E partial sums
     void *Ep = nullptr;     // [ntile][cap][E]   B x_T partial sums
-    void *Yh = nullptr;     // [F][cap][b] tensor-core block-product output (FP32, >= 16 RHS)
+    void *Yh = nullptr;     // [F][cap][b] out-of-place block-product output (tensor path, side plans)
     void *Fs = nullptr;     // [4k][cap][Lmax] side products B x_T along each side, frequency domain
-    void *Us = nullptr;     // [4k][cap][Lmax] DFTs of the side slices of x_E
+    void *Us = nullptr;     // [cap][4k][Lmax] DFTs of the side slices of x_E
     size_t bytes = 0;
 };
 
@@ -228,14 +228,16 @@ constexpr int kTcMinRhs = 16;
 constexpr int kTcMaxRhs = 256;
 ztoep_status_t ensure_tensor_data(ztoep_plan_t p, int nrhs, cudaStream_t s);
 // Perimeter side-Toeplitz edge coupling (sides.cu): plan-time generator
-// spectra from B; per product, the steps before and after the block product.
+// spectra from B; per product: DFTs of the side slices of x_E (sides_uhat),
+// B x_T from X^ and y_E (sides_edge_rows), and the B^T x_E terms added to Y^
+// after the block product (sides_add).
 ztoep_status_t sides_build(ztoep_plan_t p, const double2 *B, cudaStream_t s, size_t *acc);
 template <typename R>
-ztoep_status_t sides_pre(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, const cplx_t<R> *Xh, MatvecWs &w,
-                         cudaStream_t s);
+ztoep_status_t sides_uhat(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, MatvecWs &w, cudaStream_t s);
 template <typename R>
-ztoep_status_t sides_post(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *y, cplx_t<R> *Yh, MatvecWs &w,
-                          cudaStream_t s);
+ztoep_status_t sides_edge_rows(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, const cplx_t<R> *Xh, cplx_t<R> *y,
+                               MatvecWs &w, cudaStream_t s);
+template <typename R> ztoep_status_t sides_add(ztoep_plan_t p, int nrhs, cplx_t<R> *Yh, MatvecWs &w, cudaStream_t s);
 template <typename R> MatvecWs &ws_of(ztoep_plan_t p);
 template <typename R>
 ztoep_status_t run_forward_spectrum(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *Xh,

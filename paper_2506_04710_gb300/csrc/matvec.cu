@@ -233,7 +233,7 @@ enum { ZT_ERRBIT_BLOCKPROD_WAIT = 1 };
 template <typename R, int NST>
 __global__ void __launch_bounds__(256) k_blockprod_tma(const int2 *__restrict__ pairs, int npairs,
                                                        const cplx_t<R> *__restrict__ That, cplx_t<R> *Xh, int b,
-                                                       int nrhs, int S, int *err) {
+                                                       int nrhs, int S, int *err, cplx_t<R> *Yout) {
     using C = cplx_t<R>;
     extern __shared__ __align__(128) unsigned char zt_smem[];
     __shared__ __align__(8) uint64_t full[NST];
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(256) k_blockprod_tma(const int2 *__restrict__ 
         const bool two = fg.y != fg.x;
         const C *T = stages + (size_t)s * stage_elems;
         const C *xf = T + bb, *xg = xf + rb;
-        C *of = Xh + (size_t)fg.x * rb, *og = Xh + (size_t)fg.y * rb;
+        C *of = Yout + (size_t)fg.x * rb, *og = Yout + (size_t)fg.y * rb;
         const int nout = (two ? 2 : 1) * rb;
         if (S == 1) {
             for (int o = threadIdx.x; o < nout; o += blockDim.x) {
@@ -776,7 +776,7 @@ template <typename R> ztoep_status_t ensure_ws(ztoep_plan_t p, int nrhs) {
         const int parts = std::max(cs == 8 ? edge2_ntile(p) : ntile, tc ? tc_edge_splits(p) : 0);
         ZT_TRY(dalloc(&w.Ep, cs * (size_t)parts * nrhs * p->E, &acc));
     }
-    if (tc) ZT_TRY(dalloc(&w.Yh, cs * nrhs * (size_t)p->F * p->b, &acc));
+    if (tc || p->side_k > 0) ZT_TRY(dalloc(&w.Yh, cs * nrhs * (size_t)p->F * p->b, &acc));
     w.cap = nrhs;
     w.bytes = acc;
     return ZTOEP_OK;
@@ -834,8 +834,21 @@ static ztoep_status_t forward_passes(ztoep_plan_t p, int nrhs, const cplx_t<R> *
     return ZTOEP_OK;
 }
 
+// The pipelined (bulk-copy) block product applies: 16-byte multiples and two
+// stages within 200 KB of shared memory.
+template <typename R> static bool blockprod_pipelined(ztoep_plan_t p, int nrhs) {
+    const size_t cs = sizeof(cplx_t<R>);
+    const size_t tbytes = cs * (size_t)p->b * p->b, xbytes = cs * (size_t)nrhs * p->b;
+    return tbytes % 16 == 0 && xbytes % 16 == 0 && 2 * (tbytes + 2 * xbytes) <= 200 * 1024;
+}
+
+// Block product on the pipelined kernel when it applies (out may differ from
+// Xh there: out-of-place output), else the in-place fallback (UNSUPPORTED if an
+// out-of-place output was asked for).
 template <typename R>
-static ztoep_status_t launch_blockprod(ztoep_plan_t p, int nrhs, cplx_t<R> *Xh, cudaStream_t s) {
+static ztoep_status_t launch_blockprod(ztoep_plan_t p, int nrhs, cplx_t<R> *Xh, cudaStream_t s,
+                                       cplx_t<R> *out = nullptr) {
+    if (!out) out = Xh;
     const size_t cs = sizeof(cplx_t<R>);
     const size_t budget = 200 * 1024;
     const size_t tbytes = cs * (size_t)p->b * p->b;
@@ -863,12 +876,15 @@ static ztoep_status_t launch_blockprod(ztoep_plan_t p, int nrhs, cplx_t<R> *Xh, 
             attr = true;
         }
         if (nst == 3)
-            k_blockprod_tma<R, 3><<<grid, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, p->b, nrhs, S, p->err);
+            k_blockprod_tma<R, 3><<<grid, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, p->b, nrhs, S, p->err,
+                                                          out);
         else
-            k_blockprod_tma<R, 2><<<grid, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, p->b, nrhs, S, p->err);
+            k_blockprod_tma<R, 2><<<grid, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, p->b, nrhs, S, p->err,
+                                                          out);
         ZT_CUDA(cudaGetLastError());
         return ZTOEP_OK;
     }
+    if (out != Xh) return ZTOEP_ERR_UNSUPPORTED;  // the fallback works in place
     if (tbytes + 2 * cs * p->b > budget) return ZTOEP_ERR_UNSUPPORTED;
     const int rch = (int)std::min<size_t>((size_t)nrhs, (budget - tbytes) / (2 * cs * p->b));
     const size_t smem = tbytes + 2 * cs * (size_t)rch * p->b;
@@ -1008,22 +1024,43 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
         ZT_CUDA(cudaEventRecord(p->ev_join, p->side));
     }
     ZT_TRY(forward_passes<R>(p, nrhs, x, X1, Xh, s));
-    if (sides) ZT_TRY(sides_pre<R>(p, nrhs, x, Xh, w, s));  // reads X^ before the in-place block product
     cplx_t<R> *Yh = Xh;
-    if (tc) {
+    bool side_branch = false;
+    if (sides) {
+        // side stream: B x_T from X^ and y_E; main: U, the block product out of
+        // place (X^ stays intact for the side stream), then the B^T x_E terms
+        Yh = reinterpret_cast<cplx_t<R> *>(w.Yh);
+        ZT_TRY(sides_uhat<R>(p, nrhs, x, w, s));
+        if (tc || blockprod_pipelined<R>(p, nrhs)) {
+            ZT_CUDA(cudaEventRecord(p->ev_fork, s));  // X^ ready; the two branches only read it
+            ZT_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+            ZT_TRY(sides_edge_rows<R>(p, nrhs, x, Xh, y, w, p->side));
+            ZT_CUDA(cudaEventRecord(p->ev_join, p->side));
+            if (tc)
+                ZT_TRY(tc_blockprod(p, nrhs, reinterpret_cast<const float2 *>(Xh), reinterpret_cast<float2 *>(Yh), s));
+            else
+                ZT_TRY(launch_blockprod<R>(p, nrhs, Xh, s, Yh));
+            ZT_TRY(sides_add<R>(p, nrhs, Yh, w, s));
+            side_branch = true;
+        } else {
+            ZT_TRY(sides_edge_rows<R>(p, nrhs, x, Xh, y, w, s));  // reads X^ before the in-place product
+            Yh = Xh;
+            ZT_TRY(launch_blockprod<R>(p, nrhs, Xh, s));
+            ZT_TRY(sides_add<R>(p, nrhs, Yh, w, s));
+        }
+    } else if (tc) {
         Yh = reinterpret_cast<cplx_t<R> *>(w.Yh);
         ZT_TRY(tc_blockprod(p, nrhs, reinterpret_cast<const float2 *>(Xh), reinterpret_cast<float2 *>(Yh), s));
     } else {
         ZT_TRY(launch_blockprod<R>(p, nrhs, Xh, s));
     }
-    if (sides) ZT_TRY(sides_post<R>(p, nrhs, x, y, Yh, w, s));  // B^T x_E into Y^, y_E
     const PassCfg cy = plan_pass_cfg(p, 1, p->ly, p->lx * nrhs, cs);
     const int iby = 1 << cy.lib;
     dim3 gy((p->b + iby - 1) / iby, p->lx, nrhs);
     ZT_TRY((launch_fft_pass<R>(p->fy, twy_of<R>(p), cy.lib, true, gy,
                                LdXh<R>{Yh, p->lx, p->b, iby, nrhs},
                                StY1<R>{X1, p->ny, p->lx, p->b, iby}, s, cy.threads)));
-    if (p->E > 0 && !sides) ZT_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
+    if ((p->E > 0 && !sides) || side_branch) ZT_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
     const PassCfg cx = plan_pass_cfg(p, 0, p->lx, p->ny * nrhs, cs);
     const int ibx = 1 << cx.lib;
     dim3 gx((p->b + ibx - 1) / ibx, p->ny, nrhs);

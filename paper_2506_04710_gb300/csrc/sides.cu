@@ -178,7 +178,7 @@ template <typename C> __device__ __forceinline__ C conj_c(C a) {
     return a;
 }
 
-// U[(side*k+s)][r][kk] = sum_{c < len} x_E[r][edge(side, c, s)] w^(kk c), kk < L of the side.
+// U[r][(side*k+s)][kk] = sum_{c < len} x_E[r][edge(side, c, s)] w^(kk c), kk < L of the side.
 // One warp per (side*k+s, r, kk).
 template <typename R>
 __global__ void __launch_bounds__(256) k_side_uhat(const cplx_t<R> *__restrict__ x, cplx_t<R> *__restrict__ U,
@@ -200,77 +200,92 @@ __global__ void __launch_bounds__(256) k_side_uhat(const cplx_t<R> *__restrict__
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
     }
-    if (lane == 0) U[((int64_t)gs * nrhs + r) * lmax + kk] = acc;
+    if (lane == 0) U[((int64_t)r * 4 * sm.k + gs) * lmax + kk] = acc;
 }
 
-// Fs[(side*k+s)][r][kk] = sum_{cross, i} G^[..][f][i] X^[flip][r][i] for one
-// line (side, kk) and a chunk of 32/k RHS: a [k x K] x [K x r] contraction
-// (K = L_cross * b) through shared-memory tiles of SD_KT pairs.  Output slot o
-// (32 slots) is summed by 8 threads, thread g taking pairs g, g+8, ... of each
-// tile; the 8 partial sums are added in a fixed order.  The order depends on
-// k and b only, so a RHS is summed identically alone and in any batch.
-constexpr int SD_KT = 64, SD_SLOTS = 32, SD_G = 8, SD_KMAX = 8;
-
-template <typename R>
+// Fs[(side*k+s)][r][kk] = sum_{cross, i} G^[..][f][i] X^[flip][r][i].  One
+// CTA per (axis, kk, chunk of RQ RHS) serves both sides of the axis (bottom
+// and top share the column kx of X^, right and left the row ky), so X^ is
+// read twice in all.  Each thread walks a fixed strided subset of the
+// K = L_cross * b pairs, two at a time (one for k > 4) with every load issued first, and keeps
+// 2 x KS x RQ sums in registers; the CTA adds the per-thread sums by a warp tree
+// and the 8 warp sums in order.  The order depends on K and blockDim only, so a
+// RHS is summed identically alone and in any batch.
+template <typename R, int KS, int RQ>
 __global__ void __launch_bounds__(256) k_side_dot(const cplx_t<R> *__restrict__ Gh, const cplx_t<R> *__restrict__ Xh,
                                                   cplx_t<R> *__restrict__ Fs, SideMap sm, int b, int lx, int ly,
                                                   int lmax, int nrhs) {
     using C = cplx_t<R>;
-    __shared__ C gs_[SD_KT][SD_KMAX];
-    __shared__ C xs_[SD_KT][SD_SLOTS + 1];
-    __shared__ C red[SD_G][SD_SLOTS];
-    // line -> (side, kk)
-    int line = blockIdx.x, sg = 0;
-    const int lens[4] = {lx, ly, lx, ly};
-    while (line >= lens[sg]) line -= lens[sg++];
-    const int kk = line;
+    constexpr int NO = 2 * KS * RQ, U = KS > 4 ? 1 : 2;
+    __shared__ C red[8][NO];
+    const int ax = blockIdx.y < lx ? 0 : 1;  // 0: kk = kx (sides 0, 2); 1: kk = ky (sides 1, 3)
+    const int kk = ax == 0 ? blockIdx.y : blockIdx.y - lx;
     const int k = sm.k;
-    const int rcc = SD_SLOTS / k;  // RHS per CTA
-    const int r0 = blockIdx.y * rcc;
-    const int rc = min(rcc, nrhs - r0);
-    const int o = threadIdx.x % SD_SLOTS, g = threadIdx.x / SD_SLOTS;
-    const int so = o / rcc, ro = o - so * rcc;
-    const bool live = so < k && ro < rc;
-    const int lcross = (sg & 1) ? lx : ly;
-    const int64_t K = (int64_t)lcross * b;
+    const int r0 = blockIdx.x * RQ;
+    const int rc = min(RQ, nrhs - r0);
+    const int lcross = ax ? lx : ly;
+    const int K = lcross * b;
     const int64_t F = (int64_t)lx * ly;
-    C acc = czero<C>();
-    for (int64_t k0 = 0; k0 < K; k0 += SD_KT) {
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < SD_KT * k; idx += blockDim.x) {  // G^ tile [kp][s]
-            const int s = idx / SD_KT, kp = idx - s * SD_KT;
-            const int64_t kg = k0 + kp;
-            C v = czero<C>();
-            if (kg < K) {
-                const int cross = (int)(kg / b), i = (int)(kg - (int64_t)cross * b);
-                const int64_t f = (sg & 1) ? (int64_t)kk * lx + cross : (int64_t)cross * lx + kk;
-                v = Gh[((int64_t)(sg * k + s) * F + f) * b + i];
-            }
-            gs_[kp][s] = v;
-        }
-        for (int idx = threadIdx.x; idx < SD_KT * rc; idx += blockDim.x) {  // X^ tile [kp][r] at the flipped frequency
-            const int rr = idx / SD_KT, kp = idx - rr * SD_KT;
-            const int64_t kg = k0 + kp;
-            C v = czero<C>();
-            if (kg < K) {
-                const int cross = (int)(kg / b), i = (int)(kg - (int64_t)cross * b);
-                const int64_t f = (sg & 1) ? (int64_t)kk * lx + (lx - cross) % lx
-                                           : (int64_t)((ly - cross) % ly) * lx + kk;
-                v = Xh[(f * nrhs + r0 + rr) * b + i];
-            }
-            xs_[kp][rr] = v;
-        }
-        __syncthreads();
-        if (live)
-            for (int kp = g; kp < SD_KT; kp += SD_G) acc = cfma(gs_[kp][so], xs_[kp][ro], acc);
-    }
-    red[g][o] = acc;
-    __syncthreads();
-    if (g == 0 && live) {
-        C t = red[0][o];
+    const int64_t gstride = F * b;
+    const C *g0 = Gh + (int64_t)ax * k * gstride;        // side ax
+    const C *g1 = Gh + (int64_t)(ax + 2) * k * gstride;  // side ax + 2
+    C acc[2][KS][RQ];
 #pragma unroll
-        for (int gg = 1; gg < SD_G; ++gg) t = t + red[gg][o];
-        Fs[((int64_t)(sg * k + so) * nrhs + r0 + ro) * lmax + kk] = t;
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int s = 0; s < KS; ++s)
+#pragma unroll
+            for (int q = 0; q < RQ; ++q) acc[h][s][q] = czero<C>();
+    for (int kb = threadIdx.x; kb < K; kb += U * blockDim.x) {
+        C xv[U][RQ], gv[U][2][KS];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int kg = kb + u * blockDim.x;
+            const bool ok = kg < K;
+            const int cross = ok ? kg / b : 0, i = ok ? kg - cross * b : 0;
+            const int64_t f = ax ? (int64_t)kk * lx + cross : (int64_t)cross * lx + kk;
+            const int64_t fl = ax ? (int64_t)kk * lx + (lx - cross) % lx : (int64_t)((ly - cross) % ly) * lx + kk;
+#pragma unroll
+            for (int q = 0; q < RQ; ++q) xv[u][q] = (ok && q < rc) ? Xh[(fl * nrhs + r0 + q) * b + i] : czero<C>();
+#pragma unroll
+            for (int s = 0; s < KS; ++s) {
+                const bool sk = ok && s < k;
+                gv[u][0][s] = sk ? g0[(int64_t)s * gstride + f * b + i] : czero<C>();
+                gv[u][1][s] = sk ? g1[(int64_t)s * gstride + f * b + i] : czero<C>();
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int s = 0; s < KS; ++s)
+#pragma unroll
+                    for (int q = 0; q < RQ; ++q) acc[h][s][q] = cfma(gv[u][h][s], xv[u][q], acc[h][s][q]);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int s = 0; s < KS; ++s)
+#pragma unroll
+            for (int q = 0; q < RQ; ++q) {
+                C v = acc[h][s][q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+                    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+                }
+                if (lane == 0) red[w][(h * KS + s) * RQ + q] = v;
+            }
+    __syncthreads();
+    for (int o = threadIdx.x; o < NO; o += blockDim.x) {
+        const int h = o / (KS * RQ), s = (o / RQ) % KS, q = o % RQ;
+        if (s < k && q < rc) {
+            C t = red[0][o];
+            for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) t = t + red[ww][o];
+            Fs[((int64_t)((ax + 2 * h) * k + s) * nrhs + r0 + q) * lmax + kk] = t;
+        }
     }
 }
 
@@ -309,15 +324,19 @@ __global__ void __launch_bounds__(256) k_side_finish(const cplx_t<R> *__restrict
     }
 }
 
-// Y^[f][r][i] += sum_{side,s} G^[side,s][flip][i] U[side,s][r][kk]: thread per
-// (f, i), RHS in chunks of RCH kept in registers so G^ is read once per chunk.
-template <typename R, int RCH>
+// Y^[f][r][i] += sum_{side,s} G^[side,s][flip][i] U[r][side,s][kk]: thread per
+// (f, i); the thread's 4k spectrum values (in chunks of GC) and the offsets of
+// the matching U entries are loaded once and applied to every RHS; the terms
+// are added in (side, s) order whatever GC is (a chunk boundary is a store and
+// reload of the running sum, exact in its precision).
+template <typename R, int GC>
 __global__ void __launch_bounds__(256) k_side_add(const cplx_t<R> *__restrict__ Gh, const cplx_t<R> *__restrict__ U,
                                                   cplx_t<R> *__restrict__ Yh, SideMap sm, int b, int lx, int ly,
                                                   int lmax, int nrhs) {
     using C = cplx_t<R>;
     const int64_t F = (int64_t)lx * ly;
     const int64_t total = F * b;
+    const int ng = 4 * sm.k;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t f = idx / b;
@@ -325,23 +344,25 @@ __global__ void __launch_bounds__(256) k_side_add(const cplx_t<R> *__restrict__ 
         const int ky = (int)(f / lx), kx = (int)(f - (int64_t)ky * lx);
         const int64_t fx = (int64_t)ky * lx + (lx - kx) % lx;    // bottom / top: G^[ky][-kx]
         const int64_t fy = (int64_t)((ly - ky) % ly) * lx + kx;  // right / left: G^[-ky][kx]
-        for (int r0 = 0; r0 < nrhs; r0 += RCH) {
-            const int rc = min(RCH, nrhs - r0);
-            C acc[RCH];
+        for (int g0 = 0; g0 < ng; g0 += GC) {
+            const int gn = min(GC, ng - g0);
+            C gv[GC];
+            int uo[GC];
 #pragma unroll
-            for (int q = 0; q < RCH; ++q) acc[q] = q < rc ? Yh[(f * nrhs + r0 + q) * b + i] : czero<C>();
-            for (int gs = 0; gs < 4 * sm.k; ++gs) {
-                const int sg = gs / sm.k;
-                const C gv = Gh[((int64_t)gs * F + ((sg & 1) ? fy : fx)) * b + i];
-                const int kk = (sg & 1) ? ky : kx;
-                const C *u = U + ((int64_t)gs * nrhs + r0) * lmax + kk;
-#pragma unroll
-                for (int q = 0; q < RCH; ++q)
-                    if (q < rc) acc[q] = cfma(gv, u[(int64_t)q * lmax], acc[q]);
+            for (int j = 0; j < GC; ++j) {
+                const int gs = g0 + (j < gn ? j : 0);
+                const bool odd = (gs / sm.k) & 1;
+                gv[j] = j < gn ? Gh[((int64_t)gs * F + (odd ? fy : fx)) * b + i] : czero<C>();
+                uo[j] = gs * lmax + (odd ? ky : kx);
             }
+            const C *ur = U;
+            for (int r = 0; r < nrhs; ++r, ur += (int64_t)ng * lmax) {
+                C acc = Yh[(f * nrhs + r) * b + i];
 #pragma unroll
-            for (int q = 0; q < RCH; ++q)
-                if (q < rc) Yh[(f * nrhs + r0 + q) * b + i] = acc[q];
+                for (int j = 0; j < GC; ++j)
+                    if (j < gn) acc = cfma(gv[j], ur[uo[j]], acc);
+                Yh[(f * nrhs + r) * b + i] = acc;
+            }
         }
     }
 }
@@ -413,51 +434,65 @@ template <typename R> static const cplx_t<R> *cm_of(ztoep_plan_t p);
 template <> const float2 *cm_of<float>(ztoep_plan_t p) { return p->C32; }
 template <> const double2 *cm_of<double>(ztoep_plan_t p) { return p->C64; }
 
-// Before the block product (X^ intact): side slices of x_E to the frequency
-// domain, B x_T per side in the frequency domain.
+// Side slices of x_E to the frequency domain.
 template <typename R>
-ztoep_status_t sides_pre(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, const cplx_t<R> *Xh, MatvecWs &w,
-                         cudaStream_t s) {
+ztoep_status_t sides_uhat(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, MatvecWs &w, cudaStream_t s) {
     const SideMap sm{p->nx, p->ny, p->side_k};
     const int lmax = std::max(p->lx, p->ly);
-    cplx_t<R> *U = reinterpret_cast<cplx_t<R> *>(w.Us);
-    cplx_t<R> *Fs = reinterpret_cast<cplx_t<R> *>(w.Fs);
     KScope ks(K_EDGE, s);
-    ks.add(1);
-    k_side_uhat<R><<<dim3((lmax + 7) / 8, 4 * sm.k, nrhs), 256, 0, s>>>(x, U, sm, p->N, p->NT, p->lx, p->ly, lmax,
-                                                                         nrhs, tw_x<R>(p), tw_y<R>(p));
-    const int rcc = SD_SLOTS / sm.k;
-    dim3 gd(2 * (p->lx + p->ly), (nrhs + rcc - 1) / rcc);
-    k_side_dot<R><<<gd, 256, 0, s>>>(gh_of<R>(p), Xh, Fs, sm, p->b, p->lx, p->ly, lmax, nrhs);
+    k_side_uhat<R><<<dim3((lmax + 7) / 8, 4 * sm.k, nrhs), 256, 0, s>>>(
+        x, reinterpret_cast<cplx_t<R> *>(w.Us), sm, p->N, p->NT, p->lx, p->ly, lmax, nrhs, tw_x<R>(p), tw_y<R>(p));
     ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
 }
 
-// After the block product: B^T x_E added to Y^, and y_E = B x_T + C x_E.
+// B x_T per side in the frequency domain (reads X^), then y_E = B x_T + C x_E.
 template <typename R>
-ztoep_status_t sides_post(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *y, cplx_t<R> *Yh, MatvecWs &w,
-                          cudaStream_t s) {
+ztoep_status_t sides_edge_rows(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, const cplx_t<R> *Xh, cplx_t<R> *y,
+                               MatvecWs &w, cudaStream_t s) {
     const SideMap sm{p->nx, p->ny, p->side_k};
     const int lmax = std::max(p->lx, p->ly);
-    const cplx_t<R> *U = reinterpret_cast<const cplx_t<R> *>(w.Us);
-    const cplx_t<R> *Fs = reinterpret_cast<const cplx_t<R> *>(w.Fs);
+    cplx_t<R> *Fs = reinterpret_cast<cplx_t<R> *>(w.Fs);
     KScope ks(K_EDGE, s);
     ks.add(1);
-    constexpr int RCH = sizeof(R) == sizeof(float) ? 16 : 8;
-    k_side_add<R, RCH><<<grid1d((int64_t)p->F * p->b, 256, p->nsm), 256, 0, s>>>(gh_of<R>(p), U, Yh, sm, p->b, p->lx,
-                                                                              p->ly, lmax, nrhs);
+    // RHS per CTA: 2 for FP32 with k <= 4, else 1 (registers); RHS chunks of a line are adjacent (G^ from L2)
+    constexpr bool F32 = sizeof(R) == sizeof(float);
+    if (sm.k <= 4) {
+        constexpr int RQ = F32 ? 2 : 1;
+        dim3 gd((nrhs + RQ - 1) / RQ, p->lx + p->ly);
+        k_side_dot<R, 4, RQ><<<gd, 256, 0, s>>>(gh_of<R>(p), Xh, Fs, sm, p->b, p->lx, p->ly, lmax, nrhs);
+    } else {
+        dim3 gd(nrhs, p->lx + p->ly);
+        k_side_dot<R, 8, 1><<<gd, 256, 0, s>>>(gh_of<R>(p), Xh, Fs, sm, p->b, p->lx, p->ly, lmax, nrhs);
+    }
     k_side_finish<R><<<dim3((p->E + 7) / 8, nrhs), 256, 0, s>>>(x, cm_of<R>(p), Fs, y, sm, p->N, p->NT, p->E, p->lx,
                                                                  p->ly, lmax, nrhs, tw_x<R>(p), tw_y<R>(p));
     ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
 }
 
-template ztoep_status_t sides_pre<float>(ztoep_plan_t, int, const float2 *, const float2 *, MatvecWs &, cudaStream_t);
-template ztoep_status_t sides_pre<double>(ztoep_plan_t, int, const double2 *, const double2 *, MatvecWs &,
-                                          cudaStream_t);
-template ztoep_status_t sides_post<float>(ztoep_plan_t, int, const float2 *, float2 *, float2 *, MatvecWs &,
-                                          cudaStream_t);
-template ztoep_status_t sides_post<double>(ztoep_plan_t, int, const double2 *, double2 *, double2 *, MatvecWs &,
-                                           cudaStream_t);
+// B^T x_E terms added to Y^ (after the block product).
+template <typename R>
+ztoep_status_t sides_add(ztoep_plan_t p, int nrhs, cplx_t<R> *Yh, MatvecWs &w, cudaStream_t s) {
+    const SideMap sm{p->nx, p->ny, p->side_k};
+    const int lmax = std::max(p->lx, p->ly);
+    KScope ks(K_EDGE, s);
+    const unsigned g = grid1d((int64_t)p->F * p->b, 256, p->nsm);
+    const cplx_t<R> *U = reinterpret_cast<const cplx_t<R> *>(w.Us);
+    if (nrhs >= 8)  // many RHS: one pass over Y^ per 16 terms
+        k_side_add<R, 16><<<g, 256, 0, s>>>(gh_of<R>(p), U, Yh, sm, p->b, p->lx, p->ly, lmax, nrhs);
+    else  // few RHS: fewer registers, more CTAs resident
+        k_side_add<R, 8><<<g, 256, 0, s>>>(gh_of<R>(p), U, Yh, sm, p->b, p->lx, p->ly, lmax, nrhs);
+    ZT_CUDA(cudaGetLastError());
+    return ZTOEP_OK;
+}
+
+#define ZT_SIDES_INST(R)                                                                                          \
+    template ztoep_status_t sides_uhat<R>(ztoep_plan_t, int, const cplx_t<R> *, MatvecWs &, cudaStream_t);           \
+    template ztoep_status_t sides_edge_rows<R>(ztoep_plan_t, int, const cplx_t<R> *, const cplx_t<R> *, cplx_t<R> *, \
+                                               MatvecWs &, cudaStream_t);                                             \
+    template ztoep_status_t sides_add<R>(ztoep_plan_t, int, cplx_t<R> *, MatvecWs &, cudaStream_t);
+ZT_SIDES_INST(float)
+ZT_SIDES_INST(double)
 
 }  // namespace ztoep
