@@ -29,7 +29,10 @@
 namespace ztoep {
 
 enum { ST_ACTIVE = 0, ST_JLEN = 1, ST_ITERS = 2, ST_STATUS = 3, ST_OUTER = 4, ST_PENDING = 5, ST_REORTH = 6,
-       ST_INNER = 7, ST_RESTARTS = 8, ST_STRIDE = 12 };
+       ST_INNER = 7, ST_RESTARTS = 8, ST_END = 9, ST_STRIDE = 12 };
+// ST_END: the column just finalised ends the cycle; the iteration control
+// turns it into ACTIVE = 0, PENDING = 1 once every kernel of the step is done
+// (the Arnoldi kernels of the step test ACTIVE, so it must not change under them).
 enum { RS_RUNNING = 0, RS_CONVERGED = 1, RS_NONFINITE = 2, RS_MAXITER = 3 };
 enum { NM_VNORM = 0, NM_TARGET = 2, NM_RNORM = 3, NM_W0 = 5, NM_RIN = 6, NM_STRIDE = 8 };
 // Inner (FP32-residual) restarts of one sweep: at most this many, and they stop
@@ -177,22 +180,21 @@ __device__ void reduce_partials(const double2 *part, int nchunk, int pstride, in
     const int kk = threadIdx.x % KP, g = threadIdx.x / KP;
     for (int kb = 0; kb < K; kb += KP) {
         const int k = kb + kk;
-        double2 s0 = make_double2(0, 0), s1 = s0, s2 = s0, s3 = s0;
+        double2 sa[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) sa[q] = make_double2(0, 0);
         if (k < K) {
             int c = g;
-            for (; c + 3 * G < nchunk; c += 4 * G) {
-                const double2 a0 = __ldcg(part + (int64_t)c * pstride + k);
-                const double2 a1 = __ldcg(part + (int64_t)(c + G) * pstride + k);
-                const double2 a2 = __ldcg(part + (int64_t)(c + 2 * G) * pstride + k);
-                const double2 a3 = __ldcg(part + (int64_t)(c + 3 * G) * pstride + k);
-                s0 = s0 + a0;
-                s1 = s1 + a1;
-                s2 = s2 + a2;
-                s3 = s3 + a3;
+            for (; c + 7 * G < nchunk; c += 8 * G) {  // 8 loads in flight
+                double2 av[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) av[q] = __ldcg(part + (int64_t)(c + q * G) * pstride + k);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) sa[q] = sa[q] + av[q];
             }
-            for (; c < nchunk; c += G) s0 = s0 + __ldcg(part + (int64_t)c * pstride + k);
+            for (; c < nchunk; c += G) sa[0] = sa[0] + __ldcg(part + (int64_t)c * pstride + k);
         }
-        red2[threadIdx.x] = (s0 + s1) + (s2 + s3);
+        red2[threadIdx.x] = ((sa[0] + sa[1]) + (sa[2] + sa[3])) + ((sa[4] + sa[5]) + (sa[6] + sa[7]));
         __syncthreads();
         for (int h = G >> 1; h > 0; h >>= 1) {
             if (g < h) red2[threadIdx.x] = red2[threadIdx.x] + red2[threadIdx.x + h * KP];
@@ -340,10 +342,7 @@ __device__ void finalize_column(const GArgs &a, int rr, int j, double2 *hs, doub
         const double res = sqrt(cabs2(gn));
         const bool end =
             !(res > nm[NM_TARGET]) || !(beta > 0) || (j + 1 == m) || (st[ST_ITERS] >= a.ctl->max_iter);
-        if (end) {
-            st[ST_ACTIVE] = 0;
-            st[ST_PENDING] = 1;
-        }
+        if (end) st[ST_END] = 1;
     }
     __syncthreads();
     for (int i = threadIdx.x; i <= j; i += blockDim.x) H[i * m + j] = hs[i];
@@ -404,12 +403,9 @@ __device__ __forceinline__ int first_reorth_rhs(const GArgs &a) {
 
 // Gram-Schmidt dots.
 // PASS 1: w = (product of u_j) / beta_j is formed (from the FP32 or FP64
-//   product) and stored as u_{j+1}; h1_k = <v_k, w> and ||w||.  The last CTA
-//   gets ||w - V h1|| from ||w||^2 - sum |h1_k|^2 (exact for orthonormal v_k up
-//   to rounding of order u ||w||^2 / ||w'||^2, below 4096 u when no second pass
-//   is taken); it either flags the RHS for a second pass or finalises the
-//   Hessenberg column at once, so the update pass needs no reduction.
-// PASS 2 (flagged RHS only): h2_k = <v_k, u_{j+1}>.
+//   product) and stored as u_{j+1}; per-CTA partial sums of <v_k, w> and ||w||^2
+//   (reduced by every CTA of the update kernel, so no CTA waits on a serial tail).
+// PASS 2 (flagged RHS only): h2_k = <v_k, u_{j+1}> (last CTA reduces).
 template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(GArgs a) {
     __shared__ double2 red[64];
     __shared__ double2 tot[130];
@@ -448,50 +444,66 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(GArg
     const int K = j + 1 + (PASS == 1 ? 1 : 0);
     double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
     for (int k0 = 0; k0 < K; k0 += 8) dots_group<ELEM>(a, rr, j, k0, PASS == 1, wv, base, part, red);
+    if (PASS == 1) return;  // the update kernel reduces these partial sums
     if (!last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk)) return;
     reduce_partials(part, a.nchunk, a.pstride, K, tot);
-    double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
-    for (int k = threadIdx.x; k <= j; k += blockDim.x) {
-        const double2 hk = cscale(tot[k], 1.0 / beta[k]);
-        h[k] = hk;
-        tot[k] = hk;
-    }
-    __syncthreads();
-    if (PASS == 2) return;
-    __shared__ double s_wn2;
-    __shared__ int s_again;
-    if (threadIdx.x == 0) {
-        const double w2 = tot[j + 1].x;
-        double hsq = 0;
-        for (int k = 0; k <= j; ++k) hsq += cabs2(tot[k]);
-        const double wn2 = w2 - hsq;
-        const int again = !(wn2 > kReorthEta * kReorthEta * w2);  // strong cancellation (or NaN)
-        st[ST_REORTH] = again;
-        if (again && a.graph) cudaGraphSetConditional(a.h_reorth, 1u);
-        s_wn2 = wn2;
-        s_again = again;
-    }
-    __syncthreads();
-    if (s_again) return;  // second pass first
-    finalize_column(a, rr, j, tot, sqrt(s_wn2));
+    double2 *h = a.h2 + (int64_t)rr * (a.m + 1);
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) h[k] = cscale(tot[k], 1.0 / beta[k]);
 }
 
 // u_{j+1} <- u_{j+1} - sum_k (h_k / beta_k) u_k and its copy for the next
-// product.  PASS 1 needs no reduction; PASS 2 (after a second Gram-Schmidt
-// pass) also forms ||u_{j+1}|| and finalises the Hessenberg column.
+// product.  PASS 1: every CTA first reduces the dots' partial sums (same order
+// everywhere); one extra CTA (blockIdx.x == nchunk) takes the second-pass
+// decision and, without one, finalises the Hessenberg column, alongside the
+// update.  PASS 2 (after a second Gram-Schmidt pass) also forms ||u_{j+1}||
+// and finalises the column.
 template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(GArgs a) {
     __shared__ double red[8];
     __shared__ double2 cf[129];
-    __shared__ double2 tot[1];
+    __shared__ double2 tot[130];
     const int rr = blockIdx.y;
     int *st = a.st + rr * ST_STRIDE;
     if (!st[ST_ACTIVE]) return;
     if (PASS == 2 && !st[ST_REORTH]) return;
     const int j = a.ctl->j;
     const double *beta = a.beta + (int64_t)rr * (a.m + 1);
-    const double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
-    for (int k = threadIdx.x; k <= j; k += blockDim.x) cf[k] = cscale(__ldcg(h + k), 1.0 / beta[k]);
-    __syncthreads();
+    if (PASS == 1) {
+        // every CTA reduces the dots' partial sums in the same fixed order:
+        // tot[k] = <u_k, w> (k <= j), tot[j+1].x = ||w||^2
+        reduce_partials(a.part + (int64_t)rr * a.nchunk * a.pstride, a.nchunk, a.pstride, j + 2, tot);
+        for (int k = threadIdx.x; k <= j; k += blockDim.x) {
+            const double2 hk = cscale(tot[k], 1.0 / beta[k]);  // h_k = <v_k, w>
+            cf[k] = cscale(hk, 1.0 / beta[k]);
+            tot[k] = hk;
+        }
+        __syncthreads();
+        if (blockIdx.x == a.nchunk) {  // one extra CTA: the step decision and Hessenberg column
+            __shared__ double s_wn2;
+            __shared__ int s_again;
+            double2 *h1 = a.h1 + (int64_t)rr * (a.m + 1);
+            for (int k = threadIdx.x; k <= j; k += blockDim.x) h1[k] = tot[k];
+            if (threadIdx.x == 0) {
+                // ||w - V h||^2 = ||w||^2 - sum |h_k|^2 (exact for orthonormal v_k up to
+                // rounding of order u ||w||^2 / ||w'||^2, below 4096 u without a second pass)
+                const double w2 = tot[j + 1].x;
+                double hsq = 0;
+                for (int k = 0; k <= j; ++k) hsq += cabs2(tot[k]);
+                const double wn2 = w2 - hsq;
+                const int again = !(wn2 > kReorthEta * kReorthEta * w2);  // strong cancellation (or NaN)
+                st[ST_REORTH] = again;
+                if (again && a.graph) cudaGraphSetConditional(a.h_reorth, 1u);
+                s_wn2 = wn2;
+                s_again = again;
+            }
+            __syncthreads();
+            if (!s_again) finalize_column(a, rr, j, tot, sqrt(s_wn2));
+            return;
+        }
+    } else {
+        const double2 *h = a.h2 + (int64_t)rr * (a.m + 1);
+        for (int k = threadIdx.x; k <= j; k += blockDim.x) cf[k] = cscale(__ldcg(h + k), 1.0 / beta[k]);
+        __syncthreads();
+    }
     const int64_t base = (int64_t)blockIdx.x * blockDim.x * ELEM;
     double2 *un = basis(a, j + 1, rr);
     double2 wv[ELEM];
@@ -761,8 +773,19 @@ __global__ void k_cycle_begin(GArgs a, cudaGraphConditionalHandle h_iter, int us
     if (use_graph) cudaGraphSetConditional(h_iter, 1u);
 }
 
-// After an Arnoldi step: next iteration while some RHS is still in its cycle.
+// After an Arnoldi step: cycles that ended in this step close (ACTIVE -> 0,
+// PENDING -> 1), then the next iteration runs while some RHS is still in its
+// cycle.
 __global__ void k_iter_ctl(GArgs a, cudaGraphConditionalHandle h_iter, int use_graph) {
+    for (int rr = threadIdx.x; rr < a.nrhs; rr += blockDim.x) {
+        int *st = a.st + rr * ST_STRIDE;
+        if (st[ST_END]) {
+            st[ST_END] = 0;
+            st[ST_ACTIVE] = 0;
+            st[ST_PENDING] = 1;
+        }
+    }
+    __syncthreads();
     const bool any = any_active(a);
     if (threadIdx.x != 0) return;
     SolveCtl *c = a.ctl;
@@ -881,7 +904,7 @@ template <int ELEM> struct Launch {
         ks.add(2);
         if (pass == 1) {
             k_dots<ELEM, 1><<<g, t, 0, s>>>(a);
-            k_upd<ELEM, 1><<<g, t, 0, s>>>(a);
+            k_upd<ELEM, 1><<<dim3(g.x + 1, g.y), t, 0, s>>>(a);  // + the column CTA
         } else {
             k_dots<ELEM, 2><<<g, t, 0, s>>>(a);
             k_upd<ELEM, 2><<<g, t, 0, s>>>(a);
