@@ -236,7 +236,11 @@ ZTOEP_API void ztoep_plan_destroy(ztoep_plan_t plan);
  * The choices a plan's kernels are built with.  0 in a field means the
  * built-in heuristic.  rad_order: 0 = radix 4 first, 1 = reversed sequence;
  * fft_channels: channels one CTA of an FP32 FFT pass transforms (1..64, a
- * power of two; 0 = heuristic), fft_threads: its block size (64/128/256);
+ * power of two; 0 = heuristic), fft_threads: its block size (64/128/256) in
+ * the shared-memory kernel; fft_kernel: 0 = heuristic (the register kernel
+ * where the embedding size has one), 1 = shared-memory Stockham passes,
+ * 2 = register passes (two small DFTs per point held in registers, one
+ * shared-memory exchange; the shared-memory kernel where the size has none);
  * bp_split: threads per dot product of the SIMT block product (divides b);
  * tc_kchunk: complex K per CTA of the tensor-core B x_T product.  lx, ly,
  * rad_order, bp_split and tc_kchunk change the rounding of the products (all
@@ -247,6 +251,7 @@ typedef struct {
     int32_t rad_order_x, rad_order_y;
     int32_t fft_channels_x, fft_threads_x; /* FP32 x passes */
     int32_t fft_channels_y, fft_threads_y; /* FP32 y passes */
+    int32_t fft_kernel_x, fft_kernel_y;    /* FP32 pass kernels (0, 1, 2) */
     int32_t bp_split, bp_ctas_per_sm; /* SIMT block product */
     int32_t tc_kchunk;                /* tensor-core edge product */
     int32_t nrhs;                     /* RHS count the choice was timed for */

@@ -101,7 +101,8 @@ bool is_smooth(int n);
 struct TuneParams {
     int rad_order[2] = {0, 0};  // radix order of the x and y transforms (plan and products)
     int lib[2] = {-1, -1};      // log2 channels per CTA of the FP32 x / y passes
-    int thr[2] = {0, 0};        // threads per CTA of the FP32 x / y passes
+    int thr[2] = {0, 0};        // threads per CTA of the FP32 x / y passes (shared-memory kernel)
+    int fk[2] = {0, 0};         // FP32 x / y pass kernel: 0 register where the length allows, 1 shared memory, 2 register
     int bp_split = 0;           // threads per dot product in the SIMT block product
     int bp_per_sm = 0;          // block-product CTAs per SM
     int tc_kchunk = 0;          // K per CTA of the tensor-core B x_T product
@@ -165,6 +166,7 @@ struct ztoep_plan_s {
     int npairs = 0;
     int device = 0;
     int nsm = 0;
+    int l2_bytes = 0;  // device L2 capacity (cache-hint choices)
     bool masked = false;
     ztoep::Fft1D fx{}, fy{};
     ztoep::TuneParams tune;

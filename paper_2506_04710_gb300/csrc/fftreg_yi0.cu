@@ -1,0 +1,10 @@
+// Register FFT kernels of the inverse y pass (spectrum -> X1, cropped), lengths of
+// part 0 of the size table (each part compiled on its own for build speed).
+#include "fftreg_impl.cuh"
+#include "passes.cuh"
+
+namespace ztoep {
+template ztoep_status_t launch_fft_reg_part<true, LdXh<float>, StY1<float>, 0>(int, const float2 *, dim3, int,
+                                                                   const LdXh<float> &, const StY1<float> &,
+                                                                   cudaStream_t);
+}  // namespace ztoep

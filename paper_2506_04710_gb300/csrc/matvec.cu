@@ -15,157 +15,12 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "fftreg.cuh"
+#include "passes.cuh"
 #include "tma.cuh"
 #include "tcgemm.cuh"
 
 namespace ztoep {
-
-// ------------------------------------------------------------ FFT functors
-// Each maps (position along the transformed axis, channel in the CTA's batch)
-// to global memory; ld2/st2 move the channel pair (ch, ch+1) of FP32 passes
-// as one 16-byte access when it is aligned (two 8-byte ones otherwise).
-__device__ __forceinline__ float4 ld_pair(const float2 *p, bool two) {
-    if (!two) return make_float4(p[0].x, p[0].y, 0.f, 0.f);
-    if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) return *reinterpret_cast<const float4 *>(p);
-    return make_float4(p[0].x, p[0].y, p[1].x, p[1].y);
-}
-__device__ __forceinline__ void st_pair(float2 *p, bool two, float4 v) {
-    if (!two) {
-        p[0] = make_float2(v.x, v.y);
-    } else if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
-        *reinterpret_cast<float4 *>(p) = v;
-    } else {
-        p[0] = make_float2(v.x, v.y);
-        p[1] = make_float2(v.z, v.w);
-    }
-}
-__device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-
-template <typename R> struct LdXFwd {  // x[r][(n*nx+m)*b+i], masked, zero beyond nx
-    const cplx_t<R> *x; const uint8_t *active; int nx, b, ib; int64_t N;
-    __device__ cplx_t<R> operator()(int m, int ch) const {
-        const int n = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
-        if (m >= nx || i >= b) return czero<cplx_t<R>>();
-        const int el = n * nx + m;
-        if (active && !active[el]) return czero<cplx_t<R>>();
-        return x[(int64_t)r * N + (int64_t)el * b + i];
-    }
-    __device__ float4 ld2(int m, int ch) const {
-        const int n = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
-        if (m >= nx || i >= b) return zero4();
-        const int el = n * nx + m;
-        if (active && !active[el]) return zero4();
-        return ld_pair(x + (int64_t)r * N + (int64_t)el * b + i, i + 1 < b);
-    }
-};
-template <typename R> struct StX1 {  // X1[r][n][kx][i]
-    cplx_t<R> *X1; int ny, lx, b, ib;
-    __device__ void operator()(int kx, int ch, cplx_t<R> v) const {
-        const int n = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
-        if (i < b) X1[(((int64_t)r * ny + n) * lx + kx) * b + i] = v;
-    }
-    __device__ void st2(int kx, int ch, float4 v) const {
-        const int n = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
-        if (i < b) st_pair(X1 + (((int64_t)r * ny + n) * lx + kx) * b + i, i + 1 < b, v);
-    }
-};
-template <typename R> struct LdX1 {  // X1[r][n][kx][i], zero beyond ny; grid.y = kx
-    const cplx_t<R> *X1; int ny, lx, b, ib;
-    __device__ cplx_t<R> operator()(int n, int ch) const {
-        const int kx = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
-        if (n >= ny || i >= b) return czero<cplx_t<R>>();
-        return X1[(((int64_t)r * ny + n) * lx + kx) * b + i];
-    }
-    __device__ float4 ld2(int n, int ch) const {
-        const int kx = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
-        if (n >= ny || i >= b) return zero4();
-        return ld_pair(X1 + (((int64_t)r * ny + n) * lx + kx) * b + i, i + 1 < b);
-    }
-};
-template <typename R> struct StXh {  // Xh[f][r][i]
-    cplx_t<R> *Xh; int lx, b, ib, nrhs;
-    __device__ void operator()(int ky, int ch, cplx_t<R> v) const {
-        const int kx = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
-        if (i < b) Xh[(((int64_t)ky * lx + kx) * nrhs + r) * b + i] = v;
-    }
-    __device__ void st2(int ky, int ch, float4 v) const {
-        const int kx = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
-        if (i < b) st_pair(Xh + (((int64_t)ky * lx + kx) * nrhs + r) * b + i, i + 1 < b, v);
-    }
-};
-template <typename R> struct LdXh {
-    const cplx_t<R> *Xh; int lx, b, ib, nrhs;
-    __device__ cplx_t<R> operator()(int ky, int ch) const {
-        const int kx = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
-        if (i >= b) return czero<cplx_t<R>>();
-        return Xh[(((int64_t)ky * lx + kx) * nrhs + r) * b + i];
-    }
-    __device__ float4 ld2(int ky, int ch) const {
-        const int kx = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
-        if (i >= b) return zero4();
-        return ld_pair(Xh + (((int64_t)ky * lx + kx) * nrhs + r) * b + i, i + 1 < b);
-    }
-};
-template <typename R> struct StY1 {  // crop n < ny
-    cplx_t<R> *X1; int ny, lx, b, ib;
-    __device__ void operator()(int n, int ch, cplx_t<R> v) const {
-        const int kx = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
-        if (n < ny && i < b) X1[(((int64_t)r * ny + n) * lx + kx) * b + i] = v;
-    }
-    __device__ void st2(int n, int ch, float4 v) const {
-        const int kx = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
-        if (n < ny && i < b) st_pair(X1 + (((int64_t)r * ny + n) * lx + kx) * b + i, i + 1 < b, v);
-    }
-};
-template <typename R> struct LdY1 {  // grid.y = n
-    const cplx_t<R> *X1; int ny, lx, b, ib;
-    __device__ cplx_t<R> operator()(int kx, int ch) const {
-        const int n = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
-        if (i >= b) return czero<cplx_t<R>>();
-        return X1[(((int64_t)r * ny + n) * lx + kx) * b + i];
-    }
-    __device__ float4 ld2(int kx, int ch) const {
-        const int n = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
-        if (i >= b) return zero4();
-        return ld_pair(X1 + (((int64_t)r * ny + n) * lx + kx) * b + i, i + 1 < b);
-    }
-};
-template <typename R> struct StYOut {  // crop m < nx, scale, + B^T x_E partials, identity on absent elements
-    cplx_t<R> *y; const cplx_t<R> *xin; const cplx_t<R> *ET; const uint8_t *active;
-    int nx, b, ib, nrhs, nsplit; int64_t N, NT; R scale;
-    __device__ void operator()(int m, int ch, cplx_t<R> v) const {
-        const int n = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
-        if (m >= nx || i >= b) return;
-        const int el = n * nx + m;
-        const int64_t t = (int64_t)el * b + i;
-        cplx_t<R> out;
-        if (active && !active[el]) {
-            out = xin[(int64_t)r * N + t];
-        } else {
-            out = cscale(v, scale);
-            for (int s = 0; s < nsplit; ++s) out = out + ET[((int64_t)s * nrhs + r) * NT + t];
-        }
-        y[(int64_t)r * N + t] = out;
-    }
-    __device__ void st2(int m, int ch, float4 v) const {
-        const int n = blockIdx.y, r = blockIdx.z, i = blockIdx.x * ib + ch;
-        if (m >= nx || i >= b) return;
-        const int el = n * nx + m;
-        const int64_t t = (int64_t)el * b + i;
-        const bool two = i + 1 < b;
-        float4 out;
-        if (active && !active[el]) {
-            out = ld_pair(xin + (int64_t)r * N + t, two);
-        } else {
-            out = make_float4(v.x * scale, v.y * scale, v.z * scale, v.w * scale);
-            for (int s = 0; s < nsplit; ++s) {
-                const float4 e = ld_pair(ET + ((int64_t)s * nrhs + r) * NT + t, two);
-                out = make_float4(out.x + e.x, out.y + e.y, out.z + e.z, out.w + e.w);
-            }
-        }
-        st_pair(y + (int64_t)r * N + t, two, out);
-    }
-};
 
 // ------------------------------------------------------------ block product
 // One CTA per frequency pair {f, -f}: T^[f] (b x b, row-major) is staged in
@@ -233,7 +88,7 @@ enum { ZT_ERRBIT_BLOCKPROD_WAIT = 1 };
 template <typename R, int NST>
 __global__ void __launch_bounds__(256) k_blockprod_tma(const int2 *__restrict__ pairs, int npairs,
                                                        const cplx_t<R> *__restrict__ That, cplx_t<R> *Xh, int b,
-                                                       int nrhs, int S, int *err, cplx_t<R> *Yout) {
+                                                       int nrhs, int S, int *err, cplx_t<R> *Yout, int l2hint) {
     using C = cplx_t<R>;
     extern __shared__ __align__(128) unsigned char zt_smem[];
     __shared__ __align__(8) uint64_t full[NST];
@@ -249,13 +104,18 @@ __global__ void __launch_bounds__(256) k_blockprod_tma(const int2 *__restrict__ 
         mbar_fence_init();
     }
     __syncthreads();
+    uint64_t tpol = 0;
+    if (threadIdx.x == 0 && l2hint) tpol = l2hint == 1 ? l2_policy_evict_last() : l2_policy_evict_first();
     auto issue = [&](int it) {  // thread 0
         const int p = blockIdx.x + it * gridDim.x;
         const int s = it % NST;
         const int2 fg = pairs[p];
         C *st = stages + (size_t)s * stage_elems;
         mbar_arrive_expect_tx(&full[s], tbytes + xbytes * (fg.y != fg.x ? 2u : 1u));
-        bulk_g2s(st, That + (size_t)p * bb, tbytes, &full[s]);
+        if (l2hint)
+            bulk_g2s_hint(st, That + (size_t)p * bb, tbytes, &full[s], tpol);
+        else
+            bulk_g2s(st, That + (size_t)p * bb, tbytes, &full[s]);
         bulk_g2s(st + bb, Xh + (size_t)fg.x * rb, xbytes, &full[s]);
         if (fg.y != fg.x) bulk_g2s(st + bb + rb, Xh + (size_t)fg.y * rb, xbytes, &full[s]);
     };
@@ -814,23 +674,45 @@ static PassCfg plan_pass_cfg(ztoep_plan_t p, int dim, int L, int lines, size_t c
     return c;
 }
 
+// FP32 pass kernel of dimension dim: the register kernel when the plan's
+// choice and the length allow it.
+static bool use_reg_pass(ztoep_plan_t p, int dim, int L) {
+    return p->tune.fk[dim] != 1 && reg_fft_shape(L, nullptr);
+}
+
+// One FFT pass along dimension dim (0 = x, 1 = y) over `lines` lines per RHS:
+// mk(ib) builds the load and store functors for a channel batch of ib.
+template <typename R, bool INV, class MkLd, class MkSt>
+static ztoep_status_t fft_pass(ztoep_plan_t p, int dim, int lines, int nrhs, const MkLd &mk_ld, const MkSt &mk_st,
+                               cudaStream_t s) {
+    const size_t cs = sizeof(cplx_t<R>);
+    const int L = dim == 0 ? p->lx : p->ly;
+    if constexpr (sizeof(cplx_t<R>) == 8) {
+        if (use_reg_pass(p, dim, L)) {
+            const int tuned = p->tune.lib[dim] >= 0 ? 1 << p->tune.lib[dim] : 0;
+            const int cpb = reg_fft_cpb(L, p->b, lines * nrhs, p->nsm, tuned);
+            const int ib = 2 * cpb;
+            const dim3 g((p->b + ib - 1) / ib, lines, nrhs);
+            return launch_fft_reg<INV>(L, dim == 0 ? p->twx32 : p->twy32, g, cpb, mk_ld(ib), mk_st(ib), s);
+        }
+    }
+    const PassCfg c = plan_pass_cfg(p, dim, L, lines * nrhs, cs);
+    const int ib = 1 << c.lib;
+    const dim3 g((p->b + ib - 1) / ib, lines, nrhs);
+    return launch_fft_pass<R>(dim == 0 ? p->fx : p->fy, dim == 0 ? twx_of<R>(p) : twy_of<R>(p), c.lib, INV, g,
+                              mk_ld(ib), mk_st(ib), s, c.threads);
+}
+
 template <typename R>
 static ztoep_status_t forward_passes(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *X1,
                                      cplx_t<R> *Xh, cudaStream_t s) {
-    const size_t cs = sizeof(cplx_t<R>);
     const uint8_t *act = p->masked ? p->active : nullptr;
-    const PassCfg cx = plan_pass_cfg(p, 0, p->lx, p->ny * nrhs, cs);
-    const int ibx = 1 << cx.lib;
-    dim3 gx((p->b + ibx - 1) / ibx, p->ny, nrhs);
-    ZT_TRY((launch_fft_pass<R>(p->fx, twx_of<R>(p), cx.lib, false, gx,
-                               LdXFwd<R>{x, act, p->nx, p->b, ibx, p->N},
-                               StX1<R>{X1, p->ny, p->lx, p->b, ibx}, s, cx.threads)));
-    const PassCfg cy = plan_pass_cfg(p, 1, p->ly, p->lx * nrhs, cs);
-    const int iby = 1 << cy.lib;
-    dim3 gy((p->b + iby - 1) / iby, p->lx, nrhs);
-    ZT_TRY((launch_fft_pass<R>(p->fy, twy_of<R>(p), cy.lib, false, gy,
-                               LdX1<R>{X1, p->ny, p->lx, p->b, iby},
-                               StXh<R>{Xh, p->lx, p->b, iby, nrhs}, s, cy.threads)));
+    ZT_TRY((fft_pass<R, false>(
+        p, 0, p->ny, nrhs, [&](int ib) { return LdXFwd<R>{x, act, p->nx, p->b, ib, p->N}; },
+        [&](int ib) { return StX1<R>{X1, p->ny, p->lx, p->b, ib}; }, s)));
+    ZT_TRY((fft_pass<R, false>(
+        p, 1, p->lx, nrhs, [&](int ib) { return LdX1<R>{X1, p->ny, p->lx, p->b, ib}; },
+        [&](int ib) { return StXh<R>{Xh, p->lx, p->b, ib, nrhs}; }, s)));
     return ZTOEP_OK;
 }
 
@@ -875,12 +757,17 @@ static ztoep_status_t launch_blockprod(ztoep_plan_t p, int nrhs, cplx_t<R> *Xh, 
             ZT_CUDA(cudaFuncSetAttribute(k_blockprod_tma<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
             attr = true;
         }
+        // The spectrum is re-read by every product: kept in L2 (evict_last)
+        // when it takes at most 3/4 of it, streamed (evict_first) when it is
+        // over twice its size, so the vectors stay cached instead.
+        const size_t spec = (size_t)p->npairs * tbytes, l2 = (size_t)std::max(p->l2_bytes, 0);
+        const int l2hint = l2 == 0 ? 0 : (4 * spec <= 3 * l2 ? 1 : (spec > 2 * l2 ? 2 : 0));
         if (nst == 3)
             k_blockprod_tma<R, 3><<<grid, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, p->b, nrhs, S, p->err,
-                                                          out);
+                                                          out, l2hint);
         else
             k_blockprod_tma<R, 2><<<grid, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, p->b, nrhs, S, p->err,
-                                                          out);
+                                                          out, l2hint);
         ZT_CUDA(cudaGetLastError());
         return ZTOEP_OK;
     }
@@ -1054,22 +941,20 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
     } else {
         ZT_TRY(launch_blockprod<R>(p, nrhs, Xh, s));
     }
-    const PassCfg cy = plan_pass_cfg(p, 1, p->ly, p->lx * nrhs, cs);
-    const int iby = 1 << cy.lib;
-    dim3 gy((p->b + iby - 1) / iby, p->lx, nrhs);
-    ZT_TRY((launch_fft_pass<R>(p->fy, twy_of<R>(p), cy.lib, true, gy,
-                               LdXh<R>{Yh, p->lx, p->b, iby, nrhs},
-                               StY1<R>{X1, p->ny, p->lx, p->b, iby}, s, cy.threads)));
+    ZT_TRY((fft_pass<R, true>(
+        p, 1, p->lx, nrhs, [&](int ib) { return LdXh<R>{Yh, p->lx, p->b, ib, nrhs}; },
+        [&](int ib) { return StY1<R>{X1, p->ny, p->lx, p->b, ib}; }, s)));
     if ((p->E > 0 && !sides) || side_branch) ZT_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
-    const PassCfg cx = plan_pass_cfg(p, 0, p->lx, p->ny * nrhs, cs);
-    const int ibx = 1 << cx.lib;
-    dim3 gx((p->b + ibx - 1) / ibx, p->ny, nrhs);
     const R scale = (R)(1.0 / ((double)p->lx * (double)p->ly));
-    ZT_TRY((launch_fft_pass<R>(p->fx, twx_of<R>(p), cx.lib, true, gx,
-                               LdY1<R>{X1, p->ny, p->lx, p->b, ibx},
-                               StYOut<R>{y, x, reinterpret_cast<const cplx_t<R> *>(w.ET),
-                                         p->masked ? p->active : nullptr, p->nx, p->b, ibx, nrhs,
-                                         nsplit > 0 ? 1 : 0, p->N, p->NT, scale}, s, cx.threads)));
+    const cplx_t<R> *ET = reinterpret_cast<const cplx_t<R> *>(w.ET);
+    const uint8_t *act = p->masked ? p->active : nullptr;
+    const int ns = nsplit > 0 ? 1 : 0;
+    ZT_TRY((fft_pass<R, true>(
+        p, 0, p->ny, nrhs, [&](int ib) { return LdY1<R>{X1, p->ny, p->lx, p->b, ib}; },
+        [&](int ib) {
+            return StYOut<R>{y, x, ET, act, p->nx, p->b, ib, nrhs, ns, p->N, p->NT, scale};
+        },
+        s)));
     return ZTOEP_OK;
 }
 template ztoep_status_t run_matvec<float>(ztoep_plan_t, int, const float2 *, float2 *, cudaStream_t);

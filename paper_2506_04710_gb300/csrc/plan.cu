@@ -269,6 +269,7 @@ static ztoep_status_t plan_build(ztoep_plan_t p, const ztoep_desc_t *d, const do
     p->fy = make_fft1d(p->ly, tp.rad_order[1]);
     ZT_CUDA(cudaGetDevice(&p->device));
     ZT_CUDA(cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device));
+    ZT_CUDA(cudaDeviceGetAttribute(&p->l2_bytes, cudaDevAttrL2CacheSize, p->device));
     ZT_CUDA(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
     ZT_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
     ZT_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));

@@ -6,8 +6,10 @@
 // candidate, so the choice is never slower than it as measured):
 //   1. embedding sizes: up to 3 x 3 (lx, ly) pairs, one plan build each;
 //   2. radix order of each dimension (a plan rebuild each);
-//   3. on the kept plan: channel batch x threads of the x passes, then of the
-//      y passes, block-product split and CTAs per SM, tensor-core K chunk.
+//   3. on the kept plan: FFT-pass kernel (register or shared memory) and its
+//      channel batch (x threads for the shared-memory kernel) of the x passes,
+//      then of the y passes, block-product split and CTAs per SM, tensor-core
+//      K chunk.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -19,6 +21,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "fftreg.cuh"
 
 namespace ztoep {
 
@@ -47,11 +50,11 @@ void load_file_locked() {
     while (std::fgets(line, sizeof line, f)) {
         char key[512];
         ztoep_tune_t t{};
-        const int n = std::sscanf(line, "%511s %d %d %d %d %d %d %d %d %d %d %d %d %lf %lf", key, &t.lx, &t.ly,
+        const int n = std::sscanf(line, "%511s %d %d %d %d %d %d %d %d %d %d %d %d %d %d %lf %lf", key, &t.lx, &t.ly,
                                   &t.rad_order_x, &t.rad_order_y, &t.fft_channels_x, &t.fft_threads_x, &t.fft_channels_y,
-                                  &t.fft_threads_y, &t.bp_split, &t.bp_ctas_per_sm, &t.tc_kchunk, &t.nrhs,
-                                  &t.product_us, &t.default_us);
-        if (n == 15) g_tune_cache[key] = t;
+                                  &t.fft_threads_y, &t.fft_kernel_x, &t.fft_kernel_y, &t.bp_split, &t.bp_ctas_per_sm,
+                                  &t.tc_kchunk, &t.nrhs, &t.product_us, &t.default_us);
+        if (n == 17) g_tune_cache[key] = t;
     }
     std::fclose(f);
 }
@@ -61,9 +64,9 @@ void append_file_locked(const std::string &key, const ztoep_tune_t &t) {
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %d %.3f %.3f\n", key.c_str(), t.lx, t.ly, t.rad_order_x,
-                 t.rad_order_y, t.fft_channels_x, t.fft_threads_x, t.fft_channels_y, t.fft_threads_y, t.bp_split,
-                 t.bp_ctas_per_sm, t.tc_kchunk, t.nrhs, t.product_us, t.default_us);
+    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %d %d %d %.3f %.3f\n", key.c_str(), t.lx, t.ly, t.rad_order_x,
+                 t.rad_order_y, t.fft_channels_x, t.fft_threads_x, t.fft_channels_y, t.fft_threads_y, t.fft_kernel_x,
+                 t.fft_kernel_y, t.bp_split, t.bp_ctas_per_sm, t.tc_kchunk, t.nrhs, t.product_us, t.default_us);
     std::fclose(f);
 }
 
@@ -95,6 +98,8 @@ TuneParams params_of(const ztoep_tune_t &t) {
     p.lib[1] = t.fft_channels_y > 0 ? ilog2(t.fft_channels_y) : -1;
     p.thr[0] = t.fft_threads_x;
     p.thr[1] = t.fft_threads_y;
+    p.fk[0] = t.fft_kernel_x;
+    p.fk[1] = t.fft_kernel_y;
     p.bp_split = t.bp_split;
     p.bp_per_sm = t.bp_ctas_per_sm;
     p.tc_kchunk = t.tc_kchunk;
@@ -110,6 +115,8 @@ void fill_tune(const ztoep_plan_t p, ztoep_tune_t *t) {
     t->fft_channels_y = p->tune.lib[1] >= 0 ? 1 << p->tune.lib[1] : 0;
     t->fft_threads_x = p->tune.thr[0];
     t->fft_threads_y = p->tune.thr[1];
+    t->fft_kernel_x = p->tune.fk[0];
+    t->fft_kernel_y = p->tune.fk[1];
     t->bp_split = p->tune.bp_split;
     t->bp_ctas_per_sm = p->tune.bp_per_sm;
     t->tc_kchunk = p->tune.tc_kchunk;
@@ -123,7 +130,7 @@ bool valid_tune(const ztoep_tune_t *t) {
            pow2_or_zero(t->fft_channels_y, 64) && (t->fft_threads_x == 0 || t->fft_threads_x == 64 || t->fft_threads_x == 128 ||
                                        t->fft_threads_x == 256) &&
            (t->fft_threads_y == 0 || t->fft_threads_y == 64 || t->fft_threads_y == 128 || t->fft_threads_y == 256) &&
-           in(t->bp_split, 0, 8) && in(t->bp_ctas_per_sm, 0, 4) && t->tc_kchunk >= 0 && t->lx >= 0 && t->ly >= 0;
+           in(t->fft_kernel_x, 0, 2) && in(t->fft_kernel_y, 0, 2) && in(t->bp_split, 0, 8) && in(t->bp_ctas_per_sm, 0, 4) && t->tc_kchunk >= 0 && t->lx >= 0 && t->ly >= 0;
 }
 
 // Mean FP32 product time (us) of `nrhs` RHS on the plan's own buffers.
@@ -287,12 +294,26 @@ ztoep_status_t ztoep_plan_autotune(const ztoep_desc_t *desc, const void *T, cons
     for (int dim = 0; dim < 2; ++dim) {
         const int L = dim == 0 ? best->lx : best->ly;
         const int lines = dim == 0 ? best->ny * nrhs : best->lx * nrhs;
+        const bool reg = reg_fft_shape(L, nullptr);
+        if (reg) {  // register kernel (the heuristic): channel batches 8..64
+            const int h = 2 * reg_fft_cpb(L, best->b, lines, best->nsm, 0);
+            for (int ch = 8; ch <= 64; ch *= 2) {
+                if (ch == h || 2 * reg_fft_cpb(L, best->b, lines, best->nsm, ch) != ch) continue;
+                TuneParams tp = best->tune;
+                tp.fk[dim] = 2;
+                tp.lib[dim] = ilog2(ch);
+                ztoep_status_t st = try_params(tp, false);
+                if (st != ZTOEP_OK) return fail(st);
+            }
+        }
+        // shared-memory kernel: its heuristic, then channel batch x threads around it
         const PassCfg h = pass_cfg(L, best->b, lines, sizeof(float2), best->nsm);
         const int maxlib = pick_lib(L, best->b, sizeof(float2), 64 * 1024);
         for (int lib = std::max(0, h.lib - 1); lib <= std::min(maxlib, h.lib + 1); ++lib)
             for (int thr : {64, 128, 256}) {
-                if (lib == h.lib && thr == h.threads) continue;  // the heuristic itself
+                if (!reg && lib == h.lib && thr == h.threads) continue;  // the heuristic itself
                 TuneParams tp = best->tune;
+                tp.fk[dim] = 1;
                 tp.lib[dim] = lib;
                 tp.thr[dim] = thr;
                 ztoep_status_t st = try_params(tp, false);

@@ -65,7 +65,8 @@ class PlanInfo(ctypes.Structure):
 class TuneInfo(ctypes.Structure):
     _fields_ = [("lx", ctypes.c_int32), ("ly", ctypes.c_int32), ("rad_order_x", ctypes.c_int32),
                 ("rad_order_y", ctypes.c_int32), ("fft_channels_x", ctypes.c_int32), ("fft_threads_x", ctypes.c_int32),
-                ("fft_channels_y", ctypes.c_int32), ("fft_threads_y", ctypes.c_int32), ("bp_split", ctypes.c_int32),
+                ("fft_channels_y", ctypes.c_int32), ("fft_threads_y", ctypes.c_int32), ("fft_kernel_x", ctypes.c_int32),
+                ("fft_kernel_y", ctypes.c_int32), ("bp_split", ctypes.c_int32),
                 ("bp_ctas_per_sm", ctypes.c_int32), ("tc_kchunk", ctypes.c_int32), ("nrhs", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("product_us", ctypes.c_double), ("default_us", ctypes.c_double)]
 
