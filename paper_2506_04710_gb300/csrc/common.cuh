@@ -196,6 +196,7 @@ struct ztoep_plan_s {
     cudaStream_t side = nullptr;    // edge-coupling branch of the matvec
     cudaStream_t cap = nullptr;     // stream used to capture solve graphs
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_et = nullptr;    // edge branch: B^T x_E complete (the rest of the branch may still run)
     std::mutex mu;
 };
 

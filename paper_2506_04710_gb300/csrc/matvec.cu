@@ -821,7 +821,7 @@ static ztoep_status_t launch_edge(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, 
 
 // FP32 edge coupling without E splits (k_edge2): ET holds B^T x_E directly.
 static ztoep_status_t launch_edge2(ztoep_plan_t p, int nrhs, const float2 *x, float2 *y, MatvecWs &w,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, cudaEvent_t et_ready = nullptr) {
     float2 *ET = reinterpret_cast<float2 *>(w.ET);
     float2 *Ep = reinterpret_cast<float2 *>(w.Ep);
     const int ntile = edge2_ntile(p);
@@ -837,6 +837,7 @@ static ztoep_status_t launch_edge2(ztoep_plan_t p, int nrhs, const float2 *x, fl
             k_edge2<4><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc);
         ZT_CUDA(cudaGetLastError());
     }
+    if (et_ready) ZT_CUDA(cudaEventRecord(et_ready, s));  // ET is final; the finish only writes y_E
     dim3 gf((p->E + 7) / 8, nrhs);
     KScope ks(K_MISC, s);
     k_edge_finish2<<<gf, 256, 0, s>>>(x, p->C32, Ep, y, p->NT, p->E, p->N, nrhs, ntile);
@@ -848,7 +849,8 @@ static ztoep_status_t launch_edge2(ztoep_plan_t p, int nrhs, const float2 *x, fl
 //   B x_T    as C[e][q] = sum_t B[e][t] x_T[q][t]   -> K-split partials in Ep
 //   B^T x_E  as C[t][q] = sum_e B^T[t][e] x_E[q][e] -> ET[0]
 // then y_E = sum of the partials + C x_E.
-static ztoep_status_t tc_edge(ztoep_plan_t p, int nrhs, const float2 *x, float2 *y, MatvecWs &w, cudaStream_t s) {
+static ztoep_status_t tc_edge(ztoep_plan_t p, int nrhs, const float2 *x, float2 *y, MatvecWs &w, cudaStream_t s,
+                              cudaEvent_t et_ready = nullptr) {
     const int kc = tc_edge_kchunk(p);
     CgemmArgs g1{};
     g1.A = p->B32; g1.lda = edge_ldb(p->NT); g1.strideA = 0;
@@ -863,6 +865,7 @@ static ztoep_status_t tc_edge(ztoep_plan_t p, int nrhs, const float2 *x, float2 
     g2.C = reinterpret_cast<float2 *>(w.ET); g2.ldc_q = p->NT; g2.ldc_m = 1; g2.strideC = 0; g2.strideCk = 0;
     g2.M = (int)p->NT; g2.K = p->E; g2.N = nrhs; g2.kchunk = 0; g2.err = p->err;
     ZT_TRY(launch_cgemm(g2, 1, p->nsm, s));
+    if (et_ready) ZT_CUDA(cudaEventRecord(et_ready, s));  // ET is final; the finish only writes y_E
     dim3 gf((p->E + 7) / 8, nrhs);
     KScope ks(K_MISC, s);
     k_edge_finish<float><<<gf, 256, 0, s>>>(x, p->C32, reinterpret_cast<const float2 *>(w.Ep), y, p->NT, p->E,
@@ -901,13 +904,16 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
     if (p->E > 0 && !sides) {  // edge branch on the side stream, concurrent with the FFT chain
         ZT_CUDA(cudaEventRecord(p->ev_fork, s));
         ZT_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
-        if (tc)
-            ZT_TRY(tc_edge(p, nrhs, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), w, p->side));
-        else if (sizeof(R) == sizeof(float))
+        if (tc) {
+            ZT_TRY(tc_edge(p, nrhs, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), w, p->side,
+                           p->ev_et));
+        } else if (sizeof(R) == sizeof(float)) {
             ZT_TRY(launch_edge2(p, nrhs, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), w,
-                                p->side));
-        else
+                                p->side, p->ev_et));
+        } else {
             ZT_TRY(launch_edge<R>(p, nrhs, x, y, w, p->side, true));
+            ZT_CUDA(cudaEventRecord(p->ev_et, p->side));
+        }
         ZT_CUDA(cudaEventRecord(p->ev_join, p->side));
     }
     ZT_TRY(forward_passes<R>(p, nrhs, x, X1, Xh, s));
@@ -944,7 +950,9 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
     ZT_TRY((fft_pass<R, true>(
         p, 1, p->lx, nrhs, [&](int ib) { return LdXh<R>{Yh, p->lx, p->b, ib, nrhs}; },
         [&](int ib) { return StY1<R>{X1, p->ny, p->lx, p->b, ib}; }, s)));
-    if ((p->E > 0 && !sides) || side_branch) ZT_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
+    // the last pass adds B^T x_E (dense B): it waits for that term only; the
+    // edge rows y_E (and the side branch) are joined at the end
+    if (p->E > 0 && !sides) ZT_CUDA(cudaStreamWaitEvent(s, p->ev_et, 0));
     const R scale = (R)(1.0 / ((double)p->lx * (double)p->ly));
     const cplx_t<R> *ET = reinterpret_cast<const cplx_t<R> *>(w.ET);
     const uint8_t *act = p->masked ? p->active : nullptr;
@@ -955,6 +963,7 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
             return StYOut<R>{y, x, ET, act, p->nx, p->b, ib, nrhs, ns, p->N, p->NT, scale};
         },
         s)));
+    if ((p->E > 0 && !sides) || side_branch) ZT_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
     return ZTOEP_OK;
 }
 template ztoep_status_t run_matvec<float>(ztoep_plan_t, int, const float2 *, float2 *, cudaStream_t);

@@ -233,6 +233,7 @@ void ztoep_plan_destroy(ztoep_plan_t p) {
     cudaFree(p->err);
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->ev_et) cudaEventDestroy(p->ev_et);
     if (p->side) cudaStreamDestroy(p->side);
     if (p->cap) cudaStreamDestroy(p->cap);
     cudaSetDevice(cur);
@@ -274,6 +275,7 @@ static ztoep_status_t plan_build(ztoep_plan_t p, const ztoep_desc_t *d, const do
     ZT_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
     ZT_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     ZT_CUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+    ZT_CUDA(cudaEventCreateWithFlags(&p->ev_et, cudaEventDisableTiming));
     ZT_TRY(dalloc((void **)&p->err, sizeof(int) * 4, &acc));
     ZT_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int) * 4, s));
 
