@@ -85,6 +85,7 @@ struct GArgs {
     int cap, m, nchunk, pstride, nrhs;
     int mixed;
     int graph;                             // running inside the solve graph
+    int redund;                            // pass-1 partials reduced by every update CTA (else by the dots' last CTA)
     cudaGraphConditionalHandle h_reorth;   // second Gram-Schmidt pass needed by some RHS
 };
 
@@ -348,6 +349,30 @@ __device__ void finalize_column(const GArgs &a, int rr, int j, double2 *hs, doub
     for (int i = threadIdx.x; i <= j; i += blockDim.x) H[i * m + j] = hs[i];
 }
 
+// After the first Gram-Schmidt pass (hs[k] = h_k for k <= j, hs[j+1].x =
+// ||w||^2, shared memory, whole CTA): ||w - V h||^2 = ||w||^2 - sum |h_k|^2
+// (exact for orthonormal v_k up to rounding of order u ||w||^2 / ||w'||^2,
+// below 4096 u when no second pass is taken); strong cancellation (or NaN)
+// asks for the second pass, else the Hessenberg column is finalised now.
+__device__ void column_decision(const GArgs &a, int rr, int j, double2 *hs) {
+    __shared__ double s_wn2;
+    __shared__ int s_again;
+    int *st = a.st + rr * ST_STRIDE;
+    if (threadIdx.x == 0) {
+        const double w2 = hs[j + 1].x;
+        double hsq = 0;
+        for (int k = 0; k <= j; ++k) hsq += cabs2(hs[k]);
+        const double wn2 = w2 - hsq;
+        const int again = !(wn2 > kReorthEta * kReorthEta * w2);
+        st[ST_REORTH] = again;
+        if (again && a.graph) cudaGraphSetConditional(a.h_reorth, 1u);
+        s_wn2 = wn2;
+        s_again = again;
+    }
+    __syncthreads();
+    if (!s_again) finalize_column(a, rr, j, hs, sqrt(s_wn2));
+}
+
 // Partial dot products <u_k, w> for k in [k0, k0+8) (k <= j) plus, when
 // with_norm and k0 + kk == j + 1, ||w||^2 in that slot; CTA totals -> part.
 template <int ELEM>
@@ -403,8 +428,10 @@ __device__ __forceinline__ int first_reorth_rhs(const GArgs &a) {
 
 // Gram-Schmidt dots.
 // PASS 1: w = (product of u_j) / beta_j is formed (from the FP32 or FP64
-//   product) and stored as u_{j+1}; per-CTA partial sums of <v_k, w> and ||w||^2
-//   (reduced by every CTA of the update kernel, so no CTA waits on a serial tail).
+//   product) and stored as u_{j+1}; per-CTA partial sums of <v_k, w> and ||w||^2.
+//   With a.redund every CTA of the update kernel reduces them (no serial tail
+//   on the path); else the last CTA per RHS reduces them, takes the second-pass
+//   decision and finalises the column (column_decision).
 // PASS 2 (flagged RHS only): h2_k = <v_k, u_{j+1}> (last CTA reduces).
 template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(GArgs a) {
     __shared__ double2 red[64];
@@ -444,19 +471,26 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(GArg
     const int K = j + 1 + (PASS == 1 ? 1 : 0);
     double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
     for (int k0 = 0; k0 < K; k0 += 8) dots_group<ELEM>(a, rr, j, k0, PASS == 1, wv, base, part, red);
-    if (PASS == 1) return;  // the update kernel reduces these partial sums
+    if (PASS == 1 && a.redund) return;  // the update kernel reduces these partial sums
     if (!last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk)) return;
     reduce_partials(part, a.nchunk, a.pstride, K, tot);
-    double2 *h = a.h2 + (int64_t)rr * (a.m + 1);
-    for (int k = threadIdx.x; k <= j; k += blockDim.x) h[k] = cscale(tot[k], 1.0 / beta[k]);
+    double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) {
+        const double2 hk = cscale(tot[k], 1.0 / beta[k]);
+        h[k] = hk;
+        tot[k] = hk;
+    }
+    __syncthreads();
+    if (PASS == 2) return;
+    column_decision(a, rr, j, tot);
 }
 
 // u_{j+1} <- u_{j+1} - sum_k (h_k / beta_k) u_k and its copy for the next
-// product.  PASS 1: every CTA first reduces the dots' partial sums (same order
-// everywhere); one extra CTA (blockIdx.x == nchunk) takes the second-pass
-// decision and, without one, finalises the Hessenberg column, alongside the
-// update.  PASS 2 (after a second Gram-Schmidt pass) also forms ||u_{j+1}||
-// and finalises the column.
+// product.  PASS 1 with a.redund: every CTA first reduces the dots' partial
+// sums (same order everywhere, so the same h as the last-CTA reduction); one
+// extra CTA (blockIdx.x == nchunk) takes the second-pass decision and, without
+// one, finalises the Hessenberg column, alongside the update.  PASS 2 (after a
+// second Gram-Schmidt pass) also forms ||u_{j+1}|| and finalises the column.
 template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(GArgs a) {
     __shared__ double red[8];
     __shared__ double2 cf[129];
@@ -467,7 +501,7 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(GArgs
     if (PASS == 2 && !st[ST_REORTH]) return;
     const int j = a.ctl->j;
     const double *beta = a.beta + (int64_t)rr * (a.m + 1);
-    if (PASS == 1) {
+    if (PASS == 1 && a.redund) {
         // every CTA reduces the dots' partial sums in the same fixed order:
         // tot[k] = <u_k, w> (k <= j), tot[j+1].x = ||w||^2
         reduce_partials(a.part + (int64_t)rr * a.nchunk * a.pstride, a.nchunk, a.pstride, j + 2, tot);
@@ -478,29 +512,13 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(GArgs
         }
         __syncthreads();
         if (blockIdx.x == a.nchunk) {  // one extra CTA: the step decision and Hessenberg column
-            __shared__ double s_wn2;
-            __shared__ int s_again;
             double2 *h1 = a.h1 + (int64_t)rr * (a.m + 1);
             for (int k = threadIdx.x; k <= j; k += blockDim.x) h1[k] = tot[k];
-            if (threadIdx.x == 0) {
-                // ||w - V h||^2 = ||w||^2 - sum |h_k|^2 (exact for orthonormal v_k up to
-                // rounding of order u ||w||^2 / ||w'||^2, below 4096 u without a second pass)
-                const double w2 = tot[j + 1].x;
-                double hsq = 0;
-                for (int k = 0; k <= j; ++k) hsq += cabs2(tot[k]);
-                const double wn2 = w2 - hsq;
-                const int again = !(wn2 > kReorthEta * kReorthEta * w2);  // strong cancellation (or NaN)
-                st[ST_REORTH] = again;
-                if (again && a.graph) cudaGraphSetConditional(a.h_reorth, 1u);
-                s_wn2 = wn2;
-                s_again = again;
-            }
-            __syncthreads();
-            if (!s_again) finalize_column(a, rr, j, tot, sqrt(s_wn2));
+            column_decision(a, rr, j, tot);
             return;
         }
-    } else {
-        const double2 *h = a.h2 + (int64_t)rr * (a.m + 1);
+    } else {  // h from the dots' last CTA
+        const double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
         for (int k = threadIdx.x; k <= j; k += blockDim.x) cf[k] = cscale(__ldcg(h + k), 1.0 / beta[k]);
         __syncthreads();
     }
@@ -884,6 +902,10 @@ static GArgs make_args(ztoep_plan_t p, int nrhs, int m, bool mixed, int nchunk) 
     a.nrm = w.nrm; a.beta = w.nrm + (size_t)w.cap * NM_STRIDE; a.st = w.st; a.cnt = w.cnt;
     a.ctl = (SolveCtl *)w.ctl;
     a.N = p->N; a.cap = w.cap; a.m = m; a.nchunk = nchunk; a.pstride = w.m + 2; a.nrhs = nrhs;
+    // Redundant reduction of the pass-1 partials when its L2 traffic (every one
+    // of the nchunk update CTAs reads nchunk partial rows) stays small against
+    // the Arnoldi's own; else the dots' last CTA per RHS reduces once.
+    a.redund = (int64_t)nrhs * nchunk * nchunk <= (1 << 18) ? 1 : 0;
     a.mixed = mixed ? 1 : 0;
     return a;
 }
@@ -904,7 +926,7 @@ template <int ELEM> struct Launch {
         ks.add(2);
         if (pass == 1) {
             k_dots<ELEM, 1><<<g, t, 0, s>>>(a);
-            k_upd<ELEM, 1><<<dim3(g.x + 1, g.y), t, 0, s>>>(a);  // + the column CTA
+            k_upd<ELEM, 1><<<dim3(g.x + (a.redund ? 1 : 0), g.y), t, 0, s>>>(a);  // (+ the column CTA)
         } else {
             k_dots<ELEM, 2><<<g, t, 0, s>>>(a);
             k_upd<ELEM, 2><<<g, t, 0, s>>>(a);
