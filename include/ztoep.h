@@ -298,7 +298,11 @@ ZTOEP_API const char *ztoep_status_string(ztoep_status_t status);
 ZTOEP_API uint64_t ztoep_launch_count(void);
 
 /* Time the launches of the classes whose bit is set in `mask` with a CUDA
- * event pair on the launching stream (0 = off, the default). */
+ * event pair on the launching stream (0 = off, the default).  With
+ * ZTOEP_TIMING_SERIAL also set, a product runs its edge branch on the
+ * launching stream after the FFT chain instead of concurrently on its second
+ * stream, so each timed kernel runs alone (graph captures are unaffected). */
+#define ZTOEP_TIMING_SERIAL (1 << 30)
 ZTOEP_API void ztoep_timing_enable(int32_t mask);
 
 /* Forget accumulated timings (waits for pending events). */

@@ -18,6 +18,7 @@ static thread_local uint64_t *t_capture_sink = nullptr;  // launches recorded in
 void capture_count_begin(uint64_t *sink) { t_capture_sink = sink; }
 void capture_count_end() { t_capture_sink = nullptr; }
 void add_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+bool timing_serial() { return (g_mask.load(std::memory_order_relaxed) & ZTOEP_TIMING_SERIAL) != 0; }
 
 struct Pending {
     int cls;

@@ -33,4 +33,7 @@ void capture_count_begin(uint64_t *sink);
 void capture_count_end();
 void add_launches(uint64_t n);
 
+// ZTOEP_TIMING_SERIAL set: products serialise their branches on one stream.
+bool timing_serial();
+
 }  // namespace ztoep

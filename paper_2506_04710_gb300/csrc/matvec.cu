@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(256) k_blockprod_tma(const int2 *__restrict__ 
                                                        const cplx_t<R> *__restrict__ That, cplx_t<R> *Xh, int b,
                                                        int nrhs, int S, int *err, cplx_t<R> *Yout, int l2hint) {
     using C = cplx_t<R>;
+    pdl_enter();
     extern __shared__ __align__(128) unsigned char zt_smem[];
     __shared__ __align__(8) uint64_t full[NST];
     __shared__ double2 red_raw[256];
@@ -406,6 +407,7 @@ __global__ void __launch_bounds__(256) k_edge2(const float2 *__restrict__ x, con
                                                float2 *__restrict__ ET, float2 *__restrict__ Ep, int64_t NT,
                                                int64_t ldb, int E, int64_t N, int nrhs, int r0, int rc) {
     constexpr int U = E2_U, CPL = E2_CPL, W = E2_W, UNR = 4;
+    pdl_enter();
     // x_E of the current row chunk, later reused for the cross-warp sums
     constexpr int SX = E2_ECH * RC, SR = W * E2_TW * RC;
     __shared__ float2 sh[SX > SR ? SX : SR];
@@ -508,6 +510,7 @@ __global__ void __launch_bounds__(256) k_edge2(const float2 *__restrict__ x, con
 __global__ void __launch_bounds__(256) k_edge_finish2(const float2 *__restrict__ x, const float2 *__restrict__ Cm,
                                                       const float2 *__restrict__ Ep, float2 *__restrict__ y,
                                                       int64_t NT, int E, int64_t N, int nrhs, int ntile) {
+    pdl_enter();
     __shared__ float2 red[32][8];
     __shared__ float2 cx[8];
     const int l = threadIdx.x & 7, g = threadIdx.x >> 3;
@@ -763,12 +766,11 @@ static ztoep_status_t launch_blockprod(ztoep_plan_t p, int nrhs, cplx_t<R> *Xh, 
         const size_t spec = (size_t)p->npairs * tbytes, l2 = (size_t)std::max(p->l2_bytes, 0);
         const int l2hint = l2 == 0 ? 0 : (4 * spec <= 3 * l2 ? 1 : (spec > 2 * l2 ? 2 : 0));
         if (nst == 3)
-            k_blockprod_tma<R, 3><<<grid, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, p->b, nrhs, S, p->err,
-                                                          out, l2hint);
+            ZT_CUDA(launch_pdl(k_blockprod_tma<R, 3>, dim3(grid), dim3(256), smem, s, p->pairs, p->npairs,
+                               that_of<R>(p), Xh, p->b, nrhs, S, p->err, out, l2hint));
         else
-            k_blockprod_tma<R, 2><<<grid, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, p->b, nrhs, S, p->err,
-                                                          out, l2hint);
-        ZT_CUDA(cudaGetLastError());
+            ZT_CUDA(launch_pdl(k_blockprod_tma<R, 2>, dim3(grid), dim3(256), smem, s, p->pairs, p->npairs,
+                               that_of<R>(p), Xh, p->b, nrhs, S, p->err, out, l2hint));
         return ZTOEP_OK;
     }
     if (out != Xh) return ZTOEP_ERR_UNSUPPORTED;  // the fallback works in place
@@ -829,19 +831,19 @@ static ztoep_status_t launch_edge2(ztoep_plan_t p, int nrhs, const float2 *x, fl
     for (int r0 = 0; r0 < nrhs; r0 += 4) {
         const int rc = std::min(4, nrhs - r0);
         KScope ks(K_EDGE, s);
+        const float2 *B32 = p->B32;
         if (rc == 1)
-            k_edge2<1><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc);
+            ZT_CUDA(launch_pdl(k_edge2<1>, dim3(ntile), dim3(256), 0, s, x, B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc));
         else if (rc == 2)
-            k_edge2<2><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc);
+            ZT_CUDA(launch_pdl(k_edge2<2>, dim3(ntile), dim3(256), 0, s, x, B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc));
         else
-            k_edge2<4><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc);
-        ZT_CUDA(cudaGetLastError());
+            ZT_CUDA(launch_pdl(k_edge2<4>, dim3(ntile), dim3(256), 0, s, x, B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc));
     }
     if (et_ready) ZT_CUDA(cudaEventRecord(et_ready, s));  // ET is final; the finish only writes y_E
     dim3 gf((p->E + 7) / 8, nrhs);
     KScope ks(K_MISC, s);
-    k_edge_finish2<<<gf, 256, 0, s>>>(x, p->C32, Ep, y, p->NT, p->E, p->N, nrhs, ntile);
-    ZT_CUDA(cudaGetLastError());
+    const float2 *C32 = p->C32, *Epc = Ep;
+    ZT_CUDA(launch_pdl(k_edge_finish2, gf, dim3(256), 0, s, x, C32, Epc, y, p->NT, p->E, p->N, nrhs, ntile));
     return ZTOEP_OK;
 }
 
@@ -890,6 +892,16 @@ template <typename R> static bool use_tensor(ztoep_plan_t p, int nrhs) {
     return p->That32full != nullptr && (p->E == 0 || p->side_k > 0 || p->B32T != nullptr);
 }
 
+// Stream of the product's concurrent branch: the plan's second stream, or the
+// launching stream itself while instrumentation asks for serial branches
+// (outside graph captures).
+static cudaStream_t branch_stream(ztoep_plan_t p, cudaStream_t s) {
+    if (!timing_serial()) return p->side;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    return cs == cudaStreamCaptureStatusNone ? s : p->side;
+}
+
 template <typename R>
 ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *y, cudaStream_t s) {
     ZT_TRY(ensure_ws<R>(p, nrhs));
@@ -901,20 +913,21 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
     const int nsplit = p->side_k > 0 ? 0 : edge_nsplit(p, ntile, cs);
     const bool tc = use_tensor<R>(p, nrhs) && w.Yh != nullptr;
     const bool sides = p->E > 0 && p->side_k > 0;
+    const cudaStream_t br = branch_stream(p, s);
     if (p->E > 0 && !sides) {  // edge branch on the side stream, concurrent with the FFT chain
         ZT_CUDA(cudaEventRecord(p->ev_fork, s));
-        ZT_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+        ZT_CUDA(cudaStreamWaitEvent(br, p->ev_fork, 0));
         if (tc) {
-            ZT_TRY(tc_edge(p, nrhs, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), w, p->side,
+            ZT_TRY(tc_edge(p, nrhs, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), w, br,
                            p->ev_et));
         } else if (sizeof(R) == sizeof(float)) {
-            ZT_TRY(launch_edge2(p, nrhs, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), w,
-                                p->side, p->ev_et));
+            ZT_TRY(launch_edge2(p, nrhs, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), w, br,
+                                p->ev_et));
         } else {
-            ZT_TRY(launch_edge<R>(p, nrhs, x, y, w, p->side, true));
-            ZT_CUDA(cudaEventRecord(p->ev_et, p->side));
+            ZT_TRY(launch_edge<R>(p, nrhs, x, y, w, br, true));
+            ZT_CUDA(cudaEventRecord(p->ev_et, br));
         }
-        ZT_CUDA(cudaEventRecord(p->ev_join, p->side));
+        ZT_CUDA(cudaEventRecord(p->ev_join, br));
     }
     ZT_TRY(forward_passes<R>(p, nrhs, x, X1, Xh, s));
     cplx_t<R> *Yh = Xh;
@@ -926,9 +939,9 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
         ZT_TRY(sides_uhat<R>(p, nrhs, x, w, s));
         if (tc || blockprod_pipelined<R>(p, nrhs)) {
             ZT_CUDA(cudaEventRecord(p->ev_fork, s));  // X^ ready; the two branches only read it
-            ZT_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
-            ZT_TRY(sides_edge_rows<R>(p, nrhs, x, Xh, y, w, p->side));
-            ZT_CUDA(cudaEventRecord(p->ev_join, p->side));
+            ZT_CUDA(cudaStreamWaitEvent(br, p->ev_fork, 0));
+            ZT_TRY(sides_edge_rows<R>(p, nrhs, x, Xh, y, w, br));
+            ZT_CUDA(cudaEventRecord(p->ev_join, br));
             if (tc)
                 ZT_TRY(tc_blockprod(p, nrhs, reinterpret_cast<const float2 *>(Xh), reinterpret_cast<float2 *>(Yh), s));
             else

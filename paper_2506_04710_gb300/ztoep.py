@@ -111,6 +111,7 @@ EXPORTS = ["ztoep_default_opts", "ztoep_plan", "ztoep_matvec", "ztoep_solve", "z
            "ztoep_plan_get_tune"]
 
 K_FFT, K_BLOCKPROD, K_EDGE, K_ARNOLDI, K_MISC, K_TENSOR, K_TENSOR_PIPE = range(7)
+ZTOEP_TIMING_SERIAL = 1 << 30  # products run their branches one after another while timed
 
 
 def lib(path: str | None = None):
