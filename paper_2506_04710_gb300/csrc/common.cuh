@@ -6,38 +6,10 @@
 
 #include <cstddef>
 #include <mutex>
-#include <utility>
 
 #include "ztoep.h"
 
 namespace ztoep {
-
-// ------------------------------------------------- programmatic dependent launch
-// Kernels on the solver's per-iteration chain are launched with programmatic
-// stream serialisation: the next kernel's launch is prepared while this one
-// drains.  Every such kernel first waits for its predecessor to complete with
-// its memory visible (pdl_enter, the first statement: nothing is read before
-// it).  The dependents are released as the CTAs exit (no early trigger): an
-// early one would park waiting CTAs, with their shared memory, on SMs that
-// the concurrent edge branch needs.  Launched without the attribute, the wait
-// is a no-op.
-__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                              Args &&...args) {
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
-}
 
 // ---------------------------------------------------------------- complex
 template <typename R> struct Cplx;

@@ -146,7 +146,6 @@ template <typename R, typename Ld, typename St>
 __global__ void __launch_bounds__(256) k_fft_pass(Fft1D pl, const cplx_t<R> *__restrict__ tw, int lib,
                                                   int inv, Ld ld, St st) {
     using C = cplx_t<R>;
-    pdl_enter();
     extern __shared__ __align__(16) unsigned char zt_smem[];
     C *tws = reinterpret_cast<C *>(zt_smem);
     const int L = pl.L;
@@ -241,7 +240,8 @@ ztoep_status_t launch_fft_pass(const Fft1D &pl, const cplx_t<R> *tw, int lib, bo
         attr_set = true;
     }
     KScope ks(K_FFT, s);
-    ZT_CUDA(launch_pdl(k_fft_pass<R, Ld, St>, grid, dim3(threads), smem, s, pl, tw, lib, inv ? 1 : 0, ld, st));
+    k_fft_pass<R, Ld, St><<<grid, threads, smem, s>>>(pl, tw, lib, inv ? 1 : 0, ld, st);
+    ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
 }
 

@@ -207,7 +207,6 @@ template <int P, bool INV> struct Dft {
 template <int P1, int P2, bool INV, class Ld, class St>
 __global__ void __launch_bounds__(256) k_fft_reg(const float2 *__restrict__ tw, Ld ld, St st, int cpb) {
     constexpr int T = reg_gcd(P1, P2);
-    pdl_enter();
     extern __shared__ __align__(16) unsigned char zt_smem[];
     float4 *buf = reinterpret_cast<float4 *>(zt_smem);
     const int cp = threadIdx.x % cpb, t = threadIdx.x / cpb;
@@ -253,7 +252,8 @@ static ztoep_status_t launch_reg_shape(const float2 *tw, dim3 grid, int cpb, con
         attr_set = true;
     }
     KScope ks(K_FFT, s);
-    ZT_CUDA(launch_pdl(k_fft_reg<P1, P2, INV, Ld, St>, grid, dim3(cpb * T), smem, s, tw, ld, st, cpb));
+    k_fft_reg<P1, P2, INV, Ld, St><<<grid, cpb * T, smem, s>>>(tw, ld, st, cpb);
+    ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
 }
 

@@ -434,7 +434,6 @@ __device__ __forceinline__ int first_reorth_rhs(const GArgs &a) {
 //   decision and finalises the column (column_decision).
 // PASS 2 (flagged RHS only): h2_k = <v_k, u_{j+1}> (last CTA reduces).
 template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(GArgs a) {
-    pdl_enter();
     __shared__ double2 red[64];
     __shared__ double2 tot[130];
     const int rr = blockIdx.y;
@@ -493,7 +492,6 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(GArg
 // one, finalises the Hessenberg column, alongside the update.  PASS 2 (after a
 // second Gram-Schmidt pass) also forms ||u_{j+1}|| and finalises the column.
 template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(GArgs a) {
-    pdl_enter();
     __shared__ double red[8];
     __shared__ double2 cf[129];
     __shared__ double2 tot[130];
@@ -724,7 +722,6 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // Start of a solve: counters, deadline, x = 0 for a zero guess, and whether the
 // first true residual needs a product (it does not when x = 0).
 __global__ void k_solve_begin(GArgs a, cudaGraphConditionalHandle h_first_product, int use_graph) {
-    pdl_enter();
     SolveCtl *c = a.ctl;
     const int64_t total = (int64_t)a.nrhs * a.N;
     if (c->zero)
@@ -756,7 +753,6 @@ __device__ __forceinline__ bool past_deadline(const SolveCtl *c) {
 // After a true residual: another sweep while some RHS is active, within the
 // sweep cap and the deadline.
 __global__ void k_sweep_ctl(GArgs a, cudaGraphConditionalHandle h_sweep, int use_graph) {
-    pdl_enter();
     const bool any = any_active(a);
     if (threadIdx.x != 0) return;
     SolveCtl *c = a.ctl;
@@ -769,7 +765,6 @@ __global__ void k_sweep_ctl(GArgs a, cudaGraphConditionalHandle h_sweep, int use
 }
 
 __global__ void k_restart_begin(GArgs a, cudaGraphConditionalHandle h_restart, int use_graph) {
-    pdl_enter();
     if (threadIdx.x != 0) return;
     a.ctl->outer_bodies += 1;
     a.ctl->cond_restart = 1;
@@ -778,7 +773,6 @@ __global__ void k_restart_begin(GArgs a, cudaGraphConditionalHandle h_restart, i
 
 // After a restart: another cycle while some RHS started one (MIXED only).
 __global__ void k_restart_ctl(GArgs a, cudaGraphConditionalHandle h_restart, int use_graph) {
-    pdl_enter();
     const bool any = a.mixed && any_active(a);
     if (threadIdx.x != 0) return;
     SolveCtl *c = a.ctl;
@@ -790,7 +784,6 @@ __global__ void k_restart_ctl(GArgs a, cudaGraphConditionalHandle h_restart, int
 }
 
 __global__ void k_cycle_begin(GArgs a, cudaGraphConditionalHandle h_iter, int use_graph) {
-    pdl_enter();
     if (threadIdx.x != 0) return;
     a.ctl->j = 0;
     a.ctl->restart_bodies += 1;
@@ -802,7 +795,6 @@ __global__ void k_cycle_begin(GArgs a, cudaGraphConditionalHandle h_iter, int us
 // PENDING -> 1), then the next iteration runs while some RHS is still in its
 // cycle.
 __global__ void k_iter_ctl(GArgs a, cudaGraphConditionalHandle h_iter, int use_graph) {
-    pdl_enter();
     for (int rr = threadIdx.x; rr < a.nrhs; rr += blockDim.x) {
         int *st = a.st + rr * ST_STRIDE;
         if (st[ST_END]) {
@@ -933,11 +925,11 @@ template <int ELEM> struct Launch {
         KScope ks(K_ARNOLDI, s);
         ks.add(2);
         if (pass == 1) {
-            ZT_CUDA(launch_pdl(k_dots<ELEM, 1>, g, dim3(t), 0, s, a));
-            ZT_CUDA(launch_pdl(k_upd<ELEM, 1>, dim3(g.x + (a.redund ? 1 : 0), g.y), dim3(t), 0, s, a));  // (+ the column CTA)
+            k_dots<ELEM, 1><<<g, t, 0, s>>>(a);
+            k_upd<ELEM, 1><<<dim3(g.x + (a.redund ? 1 : 0), g.y), t, 0, s>>>(a);  // (+ the column CTA)
         } else {
-            ZT_CUDA(launch_pdl(k_dots<ELEM, 2>, g, dim3(t), 0, s, a));
-            ZT_CUDA(launch_pdl(k_upd<ELEM, 2>, g, dim3(t), 0, s, a));
+            k_dots<ELEM, 2><<<g, t, 0, s>>>(a);
+            k_upd<ELEM, 2><<<g, t, 0, s>>>(a);
         }
         return ok();
     }
@@ -993,7 +985,8 @@ struct Ops {
 static ztoep_status_t launch_small(void (*k)(GArgs, cudaGraphConditionalHandle, int), int blocks, const GArgs &a,
                                    cudaGraphConditionalHandle h, cudaStream_t s, int use_graph = 1) {
     KScope ks(K_MISC, s);
-    ZT_CUDA(launch_pdl(k, dim3(blocks), dim3(256), 0, s, a, h, use_graph));
+    k<<<blocks, 256, 0, s>>>(a, h, use_graph);
+    ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
 }
 

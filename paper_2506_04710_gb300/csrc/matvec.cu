@@ -90,7 +90,6 @@ __global__ void __launch_bounds__(256) k_blockprod_tma(const int2 *__restrict__ 
                                                        const cplx_t<R> *__restrict__ That, cplx_t<R> *Xh, int b,
                                                        int nrhs, int S, int *err, cplx_t<R> *Yout, int l2hint) {
     using C = cplx_t<R>;
-    pdl_enter();
     extern __shared__ __align__(128) unsigned char zt_smem[];
     __shared__ __align__(8) uint64_t full[NST];
     __shared__ double2 red_raw[256];
@@ -407,7 +406,6 @@ __global__ void __launch_bounds__(256) k_edge2(const float2 *__restrict__ x, con
                                                float2 *__restrict__ ET, float2 *__restrict__ Ep, int64_t NT,
                                                int64_t ldb, int E, int64_t N, int nrhs, int r0, int rc) {
     constexpr int U = E2_U, CPL = E2_CPL, W = E2_W, UNR = 4;
-    pdl_enter();
     // x_E of the current row chunk, later reused for the cross-warp sums
     constexpr int SX = E2_ECH * RC, SR = W * E2_TW * RC;
     __shared__ float2 sh[SX > SR ? SX : SR];
@@ -510,7 +508,6 @@ __global__ void __launch_bounds__(256) k_edge2(const float2 *__restrict__ x, con
 __global__ void __launch_bounds__(256) k_edge_finish2(const float2 *__restrict__ x, const float2 *__restrict__ Cm,
                                                       const float2 *__restrict__ Ep, float2 *__restrict__ y,
                                                       int64_t NT, int E, int64_t N, int nrhs, int ntile) {
-    pdl_enter();
     __shared__ float2 red[32][8];
     __shared__ float2 cx[8];
     const int l = threadIdx.x & 7, g = threadIdx.x >> 3;
@@ -766,11 +763,12 @@ static ztoep_status_t launch_blockprod(ztoep_plan_t p, int nrhs, cplx_t<R> *Xh, 
         const size_t spec = (size_t)p->npairs * tbytes, l2 = (size_t)std::max(p->l2_bytes, 0);
         const int l2hint = l2 == 0 ? 0 : (4 * spec <= 3 * l2 ? 1 : (spec > 2 * l2 ? 2 : 0));
         if (nst == 3)
-            ZT_CUDA(launch_pdl(k_blockprod_tma<R, 3>, dim3(grid), dim3(256), smem, s, p->pairs, p->npairs,
-                               that_of<R>(p), Xh, p->b, nrhs, S, p->err, out, l2hint));
+            k_blockprod_tma<R, 3><<<grid, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, p->b, nrhs, S, p->err,
+                                                          out, l2hint);
         else
-            ZT_CUDA(launch_pdl(k_blockprod_tma<R, 2>, dim3(grid), dim3(256), smem, s, p->pairs, p->npairs,
-                               that_of<R>(p), Xh, p->b, nrhs, S, p->err, out, l2hint));
+            k_blockprod_tma<R, 2><<<grid, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, p->b, nrhs, S, p->err,
+                                                          out, l2hint);
+        ZT_CUDA(cudaGetLastError());
         return ZTOEP_OK;
     }
     if (out != Xh) return ZTOEP_ERR_UNSUPPORTED;  // the fallback works in place
@@ -831,19 +829,19 @@ static ztoep_status_t launch_edge2(ztoep_plan_t p, int nrhs, const float2 *x, fl
     for (int r0 = 0; r0 < nrhs; r0 += 4) {
         const int rc = std::min(4, nrhs - r0);
         KScope ks(K_EDGE, s);
-        const float2 *B32 = p->B32;
         if (rc == 1)
-            ZT_CUDA(launch_pdl(k_edge2<1>, dim3(ntile), dim3(256), 0, s, x, B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc));
+            k_edge2<1><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc);
         else if (rc == 2)
-            ZT_CUDA(launch_pdl(k_edge2<2>, dim3(ntile), dim3(256), 0, s, x, B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc));
+            k_edge2<2><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc);
         else
-            ZT_CUDA(launch_pdl(k_edge2<4>, dim3(ntile), dim3(256), 0, s, x, B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc));
+            k_edge2<4><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc);
+        ZT_CUDA(cudaGetLastError());
     }
     if (et_ready) ZT_CUDA(cudaEventRecord(et_ready, s));  // ET is final; the finish only writes y_E
     dim3 gf((p->E + 7) / 8, nrhs);
     KScope ks(K_MISC, s);
-    const float2 *C32 = p->C32, *Epc = Ep;
-    ZT_CUDA(launch_pdl(k_edge_finish2, gf, dim3(256), 0, s, x, C32, Epc, y, p->NT, p->E, p->N, nrhs, ntile));
+    k_edge_finish2<<<gf, 256, 0, s>>>(x, p->C32, Ep, y, p->NT, p->E, p->N, nrhs, ntile);
+    ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
 }
 
