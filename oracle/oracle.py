@@ -15,6 +15,10 @@ Every function follows a plain definition from the paper:
   schur_solve   Eqs. solveEqSystem1/2 (Sec. II-D).
   assemble_points  Z[k,l] = G(|r_k - r_l|) + diag, from positions (Sec. II, G).
   gmres         restarted GMRES(m), FP64, matvec from the blocks (Sec. II-D).
+  port_admittance, scattering
+                the port matrices of Sec. IV-B: port currents from delta-port
+                solutions, Y = L I^ L, Z_port = Y^-1, S by the power-wave
+                definition (the paper's reference for S, its Eq. 18).
 """
 from __future__ import annotations
 
@@ -184,3 +188,28 @@ def relres(prob_or_Z, X: np.ndarray, V: np.ndarray) -> np.ndarray:
         ZX = matvec_blocks(prob_or_Z, X)
     V = np.atleast_2d(V)
     return np.linalg.norm(V - ZX, axis=1) / np.linalg.norm(V, axis=1)
+
+
+def port_admittance(I: np.ndarray, ports, edge_len) -> np.ndarray:
+    """Sec. IV-B.  With the excitation matrix V = [e_{i_1}, ..., e_{i_p}] the
+    solution has one column per port; here I[k] (a row) is the solution for
+    the delta excitation at port k.  The port currents I^[a][k] = I[k][i_a]
+    (rows i_1..i_p of the current matrix), and Y = L I^ L with
+    L = diag(1 / l_{i_1}, ..., 1 / l_{i_p}) (l: the ports' edge lengths)."""
+    I = np.atleast_2d(np.asarray(I))
+    ports = np.asarray(ports, dtype=np.int64)
+    Ihat = I[:, ports].T
+    L = np.diag(1.0 / np.asarray(edge_len, dtype=np.float64))
+    return L @ Ihat @ L
+
+
+def scattering(Y: np.ndarray, z0) -> np.ndarray:
+    """Sec. IV-B: the port impedance matrix Z_port = Y^-1 and, with the
+    reference impedances z0, the power-wave scattering matrix
+    S = F (Z_port - G*) (Z_port + G)^-1 F^-1, G = diag(z0),
+    F = diag(1 / (2 sqrt(|Re z0|)))."""
+    Zp = np.linalg.inv(np.asarray(Y, dtype=np.complex128))
+    z0 = np.asarray(z0, dtype=np.complex128)
+    G = np.diag(z0)
+    F = np.diag(1.0 / (2.0 * np.sqrt(np.abs(z0.real))))
+    return F @ (Zp - G.conj()) @ np.linalg.inv(Zp + G) @ np.linalg.inv(F)

@@ -364,3 +364,58 @@ def test_edge_per_cell_only_for_the_full_perimeter_layout():
     assert synth.make_problem(4, 4, 3, 0).edge_per_cell == 0
     p = synth.make_problem(5, 3, 3, 16, gap_column=2, edge_layout="split")
     assert p.edge_per_cell == 0
+
+
+# ---- port matrices (Sec. IV-B)
+
+def test_port_scattering_one_port_closed_form():
+    """One port: S = (1/y - z0) / (1/y + z0) (F cancels for a 1 x 1 matrix)."""
+    for y, z0 in ((0.013 - 0.004j, 50.0), (2.0 + 1.0j, 0.7)):
+        S = oracle.scattering(np.array([[y]]), np.array([z0]))
+        assert S.shape == (1, 1)
+        assert abs(S[0, 0] - (1 / y - z0) / (1 / y + z0)) <= 1e-14
+
+
+def test_port_scattering_terminations():
+    """Matched ports (Z_port = diag(z0)) reflect nothing; near-open ports
+    (Y -> 0) give S -> I; near-short ports (Y -> inf) give S -> -I."""
+    z0 = np.array([50.0, 75.0, 20.0])
+    assert np.max(np.abs(oracle.scattering(np.diag(1 / z0), z0))) <= 1e-14
+    rng = np.random.default_rng(1)
+    Y = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
+    assert np.max(np.abs(oracle.scattering(1e-9 * Y, z0) - np.eye(3))) <= 1e-6
+    assert np.max(np.abs(oracle.scattering(1e9 * Y, z0) + np.eye(3))) <= 1e-6
+
+
+@pytest.mark.parametrize("uniform", [True, False])
+def test_port_scattering_lossless_is_unitary(uniform):
+    """A lossless reciprocal network (Z_port = j X, X real symmetric) has a
+    unitary, and for equal reference impedances symmetric, power-wave S; with
+    unequal real z0 unitarity needs the F scaling."""
+    rng = np.random.default_rng(4)
+    p = 6
+    A = rng.standard_normal((p, p))
+    X = 30.0 * (A + A.T)
+    z0 = np.full(p, 50.0) if uniform else rng.uniform(20.0, 100.0, p)
+    S = oracle.scattering(np.linalg.inv(1j * X), z0)
+    assert np.max(np.abs(S.conj().T @ S - np.eye(p))) <= 1e-10
+    if uniform:
+        assert np.max(np.abs(S - S.T)) <= 1e-10
+
+
+def test_port_admittance_is_the_port_block_of_the_inverse():
+    """Delta-port solutions of the dense system: I^ = (Z^-1) restricted to
+    the port rows and columns, so Y = L (Z^-1)[ports, ports] L, symmetric
+    because the MoM matrix is (Galerkin, Z^T = Z)."""
+    prob = synth.make_problem(4, 3, 5, 8, seed=2)
+    Z = oracle.assemble(prob)
+    ports = np.array([0, 7, 23, 40, prob.n - 1])
+    lens = np.array([0.5, 0.25, 1.0, 0.75, 2.0])
+    V = np.zeros((len(ports), prob.n), complex)
+    V[np.arange(len(ports)), ports] = 1.0
+    I = np.linalg.solve(Z, V.T).T  # row k: solution for port k
+    Y = oracle.port_admittance(I, ports, lens)
+    Zi = np.linalg.inv(Z)
+    L = np.diag(1 / lens)
+    assert np.max(np.abs(Y - L @ Zi[np.ix_(ports, ports)] @ L)) <= 1e-12 * np.max(np.abs(Y))
+    assert np.max(np.abs(Y - Y.T)) <= 1e-12 * np.max(np.abs(Y))
