@@ -225,6 +225,27 @@ ZTOEP_API ztoep_status_t ztoep_plan_spectrum(ztoep_plan_t plan, void *That, void
 
 ZTOEP_API ztoep_status_t ztoep_plan_get_info(ztoep_plan_t plan, ztoep_plan_info_t *info);
 
+/* ---- Port matrices (Sec. IV-B) ----
+ * After a solve with the delta excitations V = [e_{i_1}, ..., e_{i_p}]:
+ *   I      device complex128 [p][n]: row k is the solution for the excitation
+ *          at port k (the layout ztoep_solve writes for p RHS);
+ *   ports  host int32 [p]: the unknown indices i_k (0 <= i_k < n);
+ *   edge_len host double [p]: the ports' edge lengths l_{i_k} (> 0);
+ *   z0     host double [p]: real reference impedances (> 0).
+ * Writes (device complex128 [p][p], row-major):
+ *   Y = L I^ L, I^[a][k] = I[k][i_a] (port currents), L = diag(1 / l_{i_k});
+ *   S = F (Z_port - G)(Z_port + G)^-1 F^-1 with Z_port = Y^-1, G = diag(z0),
+ *       F = diag(1 / (2 sqrt(z0))): the power-wave scattering matrix, formed as
+ *       F (I - G Y)(I + G Y)^-1 F^-1 by FP64 Gauss-Jordan elimination with
+ *       partial pivoting (no inverse of Y).
+ * Stream-ordered; returns after the work completes (it reads back a status
+ * word).  Allocates 2 p^2 complex128 of stream-ordered workspace.  Errors:
+ * ARG (bad sizes or values, Y/S aliasing I or each other), NOMEM,
+ * NONFINITE (a zero or non-finite pivot: I + G Y singular), CUDA. */
+ZTOEP_API ztoep_status_t ztoep_port_matrices(int32_t p, int64_t n, const void *I, const int32_t *ports,
+                                             const double *edge_len, const double *z0, void *Y, void *S,
+                                             void *stream);
+
 /* Device bytes a plan for `desc` plus the workspace of a solve with up to
  * max_nrhs right-hand sides and restart length `restart` would use (for
  * admission control).  0 if the descriptor is invalid. */

@@ -106,6 +106,7 @@ EXPORTS = ["ztoep_default_opts", "ztoep_plan", "ztoep_matvec", "ztoep_solve", "z
            "ztoep_forward_spectrum", "ztoep_plan_spectrum", "ztoep_plan_get_info", "ztoep_footprint",
            "ztoep_plan_destroy", "ztoep_status_string", "ztoep_version", "ztoep_launch_count",
            "ztoep_timing_enable", "ztoep_timing_reset", "ztoep_timing_read", "ztoep_edge_product_noalloc",
+           "ztoep_port_matrices",
            "ztoep_sched_create", "ztoep_sched_submit", "ztoep_sched_poll", "ztoep_sched_wait",
            "ztoep_sched_get_stats", "ztoep_sched_destroy", "ztoep_plan_autotune", "ztoep_plan_tuned",
            "ztoep_plan_get_tune"]
@@ -140,6 +141,8 @@ def lib(path: str | None = None):
     L.ztoep_plan_spectrum.restype = c_i32
     L.ztoep_plan_get_info.argtypes = [c_p, ctypes.POINTER(PlanInfo)]
     L.ztoep_plan_get_info.restype = c_i32
+    L.ztoep_port_matrices.argtypes = [c_i32, ctypes.c_int64, c_p, c_p, c_p, c_p, c_p, c_p, c_p]
+    L.ztoep_port_matrices.restype = c_i32
     L.ztoep_footprint.argtypes = [ctypes.POINTER(Desc), c_i32, c_i32]
     L.ztoep_footprint.restype = ctypes.c_size_t
     L.ztoep_plan_destroy.argtypes = [c_p]
@@ -295,6 +298,30 @@ def ztoep_plan_get_info(plan) -> PlanInfo:
     info = PlanInfo()
     _check(lib().ztoep_plan_get_info(plan, ctypes.byref(info)), "ztoep_plan_get_info")
     return info
+
+
+def ztoep_port_matrices(p: int, n: int, I, ports, edge_len, z0, Y, S, stream=None) -> int:
+    """Argument marshalling for ztoep_port_matrices: I, Y, S device complex128
+    tensors; ports (int32), edge_len and z0 (float64) host numpy arrays."""
+    import numpy as np
+    pa = np.ascontiguousarray(ports, dtype=np.int32)
+    la = np.ascontiguousarray(edge_len, dtype=np.float64)
+    za = np.ascontiguousarray(z0, dtype=np.float64)
+    return lib().ztoep_port_matrices(p, n, _dptr(I), pa.ctypes.data_as(c_p), la.ctypes.data_as(c_p),
+                                     za.ctypes.data_as(c_p), _dptr(Y), _dptr(S), _stream_ptr(stream))
+
+
+def port_matrices(I, ports, edge_len, z0, stream=None):
+    """(Y, S) for the delta-port solutions I ([p][n] complex128 on the
+    device, row k solved for port k); raises ZtoepError on a bad status."""
+    import torch
+    p, n = I.shape
+    Y = torch.empty((p, p), dtype=torch.complex128, device=I.device)
+    S = torch.empty_like(Y)
+    st = ztoep_port_matrices(p, n, I, ports, edge_len, z0, Y, S, stream)
+    if st != 0:
+        raise ZtoepError(st)
+    return Y, S
 
 
 def ztoep_footprint(desc: Desc, max_nrhs: int, restart: int = 30) -> int:
