@@ -597,6 +597,63 @@ def run_many_port(args, local):
     plan.close()
 
 
+def run_far_field(args, local):
+    """Far field of the 32x32 b64 solution on the 64 x 64 array-factor grid
+    (Eqs. farfieldBasis / tensorProd; synthetic per-basis tensor, 2
+    polarisations): the plan's FP64 forward spectrum plus one b-term dot per
+    (direction, polarisation), timed with CUDA events; the oracle's direct sum
+    over the 1024 parts on a sample of directions beside it."""
+    import numpy as np
+    import torch
+    from paper_2506_04710_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2506_04710_gb300 import synth, ztoep
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob, tol = synth.config_problem(WORKLOAD)
+    plan = ztoep.Plan.from_problem(prob, device=dev)
+    V = torch.from_numpy(prob.V.copy()).to(dev)
+    o = ztoep.ztoep_default_opts()
+    o.tol = tol
+    X, _, st = plan.solve(V, opts=o)
+    assert st == 0
+    uv = synth.grid_directions(plan.info.lx, plan.info.ly)
+    Fh = torch.from_numpy(synth.far_field_basis(prob, uv, 2)).to(dev)
+    s = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        F = plan.far_field(X, Fh, synth.K0, 376.73, s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    torch.cuda.synchronize(dev)
+    e0.record(s)
+    for _ in range(reps):
+        F = plan.far_field(X, Fh, synth.K0, 376.73, s)
+    e1.record(s)
+    torch.cuda.synchronize(dev)
+    us = 1e3 * e0.elapsed_time(e1) / reps
+    cpu = None
+    if not args.no_cpu_baseline:
+        sys.path.insert(0, os.path.join(ROOT, "oracle"))
+        import oracle
+        pick = np.arange(0, len(uv), 97)
+        t = time.perf_counter()
+        ref = oracle.far_field(prob, X.cpu().numpy()[:, :prob.n_toep], uv[pick], Fh.cpu().numpy()[pick],
+                               synth.K0, 376.73)
+        dt = time.perf_counter() - t
+        Fg = F.cpu().numpy()[:, pick]
+        cpu = {"directions": int(len(pick)), "seconds": dt, "us_per_direction": 1e6 * dt / len(pick),
+               "max_rel_diff": float(np.max(np.abs(Fg - ref)) / np.max(np.abs(ref))), "kind": "oracle"}
+    nb = prob.n_toep * 16 + plan.info.lx * plan.info.ly * (prob.b * 16 * 3 + 2 * 16 * 2)
+    line = {"metric": "far-field grid time", "mode": "far_field", "value": us, "unit": "us",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"far field of the 32x32 b64 solution on the {plan.info.lx}x{plan.info.ly} "
+                                   "array-factor grid, 2 polarisations, synthetic per-basis tensor",
+                       "directions": int(len(uv)), "parts": prob.nx * prob.ny, "b": prob.b},
+            "algorithmic_bytes": nb, "GB/s": nb / us / 1e3, "oracle_sample": cpu}
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def run_product(args, local):
     """One configuration's FP32 product (the inner-iteration product) timed
     alone: per-class kernel times and the algorithmic GB/s and tensor flops.
@@ -688,6 +745,8 @@ def main():
                     help="time the FP32 product of --workload (a configuration key) alone")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--nrhs", type=int, default=0, help="--product-only: plane-wave RHS count instead of the config's")
+    ap.add_argument("--far-field", action="store_true",
+                    help="far field of the 32x32 b64 solution on the array-factor grid")
     ap.add_argument("--many-port", action="store_true",
                     help="solve every element port of an --ports-nx square array (b=64) and form Y and S")
     ap.add_argument("--ports-nx", type=int, default=32)
@@ -700,6 +759,9 @@ def main():
     elif args.many_port:
         if rank == 0:
             run_many_port(args, local)
+    elif args.far_field:
+        if rank == 0:
+            run_far_field(args, local)
     elif args.serve > 0:
         run_serve(args, world, rank, local)
     elif args.impl == "reference":

@@ -246,6 +246,25 @@ ZTOEP_API ztoep_status_t ztoep_port_matrices(int32_t p, int64_t n, const void *I
                                              const double *edge_len, const double *z0, void *Y, void *S,
                                              void *stream);
 
+/* ---- Far field (Sec. III, Eqs. farfieldBasis and tensorProd) ----
+ * Far field of the element currents on the array-factor grid of the plan's
+ * embedding: direction f = ky*lx + kx has k a u = 2 pi kx / lx and
+ * k a v = 2 pi ky / ly (u = sin th cos ph, v = sin th sin ph, a the element
+ * period), so that the phase of part (m, n) at offset (m a, n a, 0) is
+ * exp(2 pi j (kx m / lx + ky n / ly)).  With the per-basis far-field tensor
+ * Fh of one element (Eq. farfieldBasis),
+ *   F[r][f][t] = -j k eta sum_{active (m,n)} exp(j k r^_f . d_(m,n))
+ *                sum_{i<b} I[r][(n*nx+m)*b+i] Fh[f][t][i]      (Eq. tensorProd),
+ * computed as the plan's FP64 forward spectrum at -f and one b-term dot
+ * product per (f, t, r).  Edge unknowns (other array components) are not
+ * included.
+ *   I: device complex128 [nrhs][N]; Fh: device complex128 [lx*ly][npol][b];
+ *   F: device complex128 [nrhs][lx*ly][npol]; npol 1..16.
+ * Stream-ordered; allocates F b nrhs complex128 of stream-ordered workspace.
+ * Errors: ARG, NOMEM, CUDA. */
+ZTOEP_API ztoep_status_t ztoep_far_field_grid(ztoep_plan_t plan, int32_t nrhs, const void *I, int32_t npol,
+                                              const void *Fh, double k, double eta, void *F, void *stream);
+
 /* Device bytes a plan for `desc` plus the workspace of a solve with up to
  * max_nrhs right-hand sides and restart length `restart` would use (for
  * admission control).  0 if the descriptor is invalid. */

@@ -19,6 +19,8 @@ Every function follows a plain definition from the paper:
                 the port matrices of Sec. IV-B: port currents from delta-port
                 solutions, Y = L I^ L, Z_port = Y^-1, S by the power-wave
                 definition (the paper's reference for S, its Eq. 18).
+  far_field     Eq. tensorProd: F[m][t] = -j k eta sum_p sum_n
+                exp(j k r^_m . d_p) I[n, p] F^[m][t][n] by direct summation.
 """
 from __future__ import annotations
 
@@ -213,3 +215,26 @@ def scattering(Y: np.ndarray, z0) -> np.ndarray:
     G = np.diag(z0)
     F = np.diag(1.0 / (2.0 * np.sqrt(np.abs(z0.real))))
     return F @ (Zp - G.conj()) @ np.linalg.inv(Zp + G) @ np.linalg.inv(F)
+
+
+def far_field(prob, I: np.ndarray, uv: np.ndarray, Fh: np.ndarray, k: float, eta: float) -> np.ndarray:
+    """Eq. tensorProd for the element component: parts p = active elements
+    (m, n) at offsets d_p = (m a, n a, 0), basis coefficients I[r][(n nx + m) b + i],
+    F^ = Fh[M][T][b] (Eq. farfieldBasis), directions (u, v) = (sin th cos ph,
+    sin th sin ph) so that k r^.d_p = k a (u m + v n):
+        F[r][m][t] = -j k eta sum_p exp(j k r^_m.d_p) sum_i I[r][p b + i] Fh[m][t][i].
+    Direct summation over the parts, no FFT.  Returns [nrhs][M][T]."""
+    from paper_2506_04710_gb300.synth import PERIOD
+    I = np.atleast_2d(np.asarray(I))
+    uv = np.asarray(uv, dtype=np.float64)
+    out = np.zeros((I.shape[0], len(uv), Fh.shape[1]), np.complex128)
+    b = prob.b
+    for n in range(prob.ny):
+        for m in range(prob.nx):
+            if not prob.active[n, m]:
+                continue
+            p = n * prob.nx + m
+            ph = np.exp(1j * k * PERIOD * (uv[:, 0] * m + uv[:, 1] * n))  # [M]
+            Ip = I[:, p * b:(p + 1) * b]                                   # [r][b]
+            out += ph[None, :, None] * np.einsum("mti,ri->rmt", Fh, Ip)
+    return -1j * k * eta * out

@@ -347,3 +347,32 @@ def make_problem_device(nx: int, ny: int, b: int, n_edge: int, seed: int, nrhs: 
     ph = kx[:, None] * allpos[None, :, 0] + ky[:, None] * allpos[None, :, 1]
     V = torch.exp(1j * ph.to(torch.complex128))
     return dict(nx=nx, ny=ny, b=b, n_edge=n_edge, T=T.contiguous(), B=B, C=C.contiguous(), V=V.contiguous())
+
+
+def grid_directions(lx: int, ly: int, period: float = PERIOD) -> np.ndarray:
+    """Observation directions (u, v) = (sin th cos ph, sin th sin ph) of the
+    array-factor grid of an lx x ly embedding, in the spectrum's order
+    f = ky lx + kx: u = kx' lambda / (lx a), v = ky' lambda / (ly a), with
+    kx' = kx for kx <= lx / 2 and kx - lx above (so k a u m = 2 pi kx m / lx
+    for every integer m).  Points with u^2 + v^2 > 1 lie outside the visible
+    region; they are kept (evanescent directions) so that the grid is whole."""
+    kx = np.arange(lx)
+    ky = np.arange(ly)
+    kxs = np.where(kx <= lx // 2, kx, kx - lx)
+    kys = np.where(ky <= ly // 2, ky, ky - ly)
+    u = kxs * LAMBDA / (lx * period)
+    v = kys * LAMBDA / (ly * period)
+    U, V = np.meshgrid(u, v)
+    return np.stack([U.reshape(-1), V.reshape(-1)], axis=1)
+
+
+def far_field_basis(prob: "Problem", uv: np.ndarray, npol: int = 2) -> np.ndarray:
+    """Synthetic stand-in for the per-basis far-field integrals of one element
+    (the tensor F^[m][pol][i] of the paper's far-field step; the mesh
+    integrals are not available): a point-like basis at r_i radiates
+    exp(j k r^.r_i) times a smooth polarisation factor, 1 (co) and u v (cross).
+    Returns complex128 [M][npol][b]."""
+    uv = np.asarray(uv, dtype=np.float64)
+    ph = np.exp(1j * K0 * (uv[:, 0:1] * prob.pts[None, :, 0] + uv[:, 1:2] * prob.pts[None, :, 1]))
+    pol = [np.ones(len(uv)), uv[:, 0] * uv[:, 1]] + [uv[:, 0] ** q for q in range(2, npol)]
+    return np.stack([pol[t][:, None] * ph for t in range(npol)], axis=1)

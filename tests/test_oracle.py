@@ -419,3 +419,56 @@ def test_port_admittance_is_the_port_block_of_the_inverse():
     L = np.diag(1 / lens)
     assert np.max(np.abs(Y - L @ Zi[np.ix_(ports, ports)] @ L)) <= 1e-12 * np.max(np.abs(Y))
     assert np.max(np.abs(Y - Y.T)) <= 1e-12 * np.max(np.abs(Y))
+
+
+# ---- far field (Eqs. farfieldBasis / tensorProd)
+
+def test_far_field_single_element_closed_form():
+    """One element at the origin: no phase, F = -j k eta sum_i I_i Fh[m][t][i]."""
+    prob = synth.make_problem(1, 1, 3, 0, seed=6)
+    rng = np.random.default_rng(0)
+    I = rng.standard_normal((2, 3)) + 1j * rng.standard_normal((2, 3))
+    uv = rng.uniform(-1, 1, (5, 2))
+    Fh = rng.standard_normal((5, 2, 3)) + 1j * rng.standard_normal((5, 2, 3))
+    F = oracle.far_field(prob, I, uv, Fh, k=2.0, eta=3.0)
+    ref = -1j * 2.0 * 3.0 * np.einsum("mti,ri->rmt", Fh, I)
+    assert np.max(np.abs(F - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_far_field_shift_theorem():
+    """Moving the currents of element (0, 0) to element (1, 1) multiplies the
+    far field by exp(j k a (u + v)) (the offset d = (a, a, 0))."""
+    prob = synth.make_problem(3, 2, 4, 0, seed=1)
+    rng = np.random.default_rng(3)
+    c = rng.standard_normal(4) + 1j * rng.standard_normal(4)
+    I0 = np.zeros((1, prob.n_toep), complex)
+    I1 = np.zeros((1, prob.n_toep), complex)
+    I0[0, 0:4] = c
+    p = 1 * prob.nx + 1
+    I1[0, 4 * p:4 * p + 4] = c
+    uv = rng.uniform(-1, 1, (7, 2))
+    Fh = synth.far_field_basis(prob, uv)
+    k = synth.K0
+    F0 = oracle.far_field(prob, I0, uv, Fh, k, 1.0)
+    F1 = oracle.far_field(prob, I1, uv, Fh, k, 1.0)
+    ph = np.exp(1j * k * synth.PERIOD * (uv[:, 0] + uv[:, 1]))
+    assert np.max(np.abs(F1 - F0 * ph[None, :, None])) <= 1e-13 * np.max(np.abs(F0))
+
+
+def test_far_field_on_the_grid_is_an_inverse_fft():
+    """On the array-factor grid of an lx x ly embedding the sum over parts is
+    lx ly times numpy's inverse 2-D FFT of the zero-padded element currents
+    (per basis function), contracted with Fh."""
+    prob = synth.make_problem(5, 3, 2, 0, seed=4, gap_column=2)
+    lx, ly = 9, 6
+    rng = np.random.default_rng(5)
+    I = rng.standard_normal((2, prob.n_toep)) + 1j * rng.standard_normal((2, prob.n_toep))
+    uv = synth.grid_directions(lx, ly)
+    Fh = synth.far_field_basis(prob, uv)
+    F = oracle.far_field(prob, I, uv, Fh, synth.K0, 120 * np.pi)
+    grid = I.reshape(2, prob.ny, prob.nx, prob.b) * prob.active[None, :, :, None]
+    pad = np.zeros((2, ly, lx, prob.b), complex)
+    pad[:, :prob.ny, :prob.nx] = grid
+    Xs = np.fft.ifft2(pad, axes=(1, 2)) * (lx * ly)          # [r][ky][kx][i], e^{+j...}
+    ref = -1j * synth.K0 * 120 * np.pi * np.einsum("fti,rfi->rft", Fh, Xs.reshape(2, ly * lx, prob.b))
+    assert np.max(np.abs(F - ref)) <= 1e-11 * np.max(np.abs(ref))
