@@ -246,6 +246,24 @@ ZTOEP_API ztoep_status_t ztoep_port_matrices(int32_t p, int64_t n, const void *I
                                              const double *edge_len, const double *z0, void *Y, void *S,
                                              void *stream);
 
+/* ---- Level-1 solve by the Schur complement (Sec. II-D, Eqs. solveEqSystem1/2) ----
+ * Z = [[A, B^T], [B, C]] solved through solves with A alone:
+ *   A F = B^T, A U = V_T, S = C - B F, I_E = S^-1 (V_E - B U), I_T = U - F I_E.
+ *   plan_A: a plan of the same Toeplitz blocks with n_edge = 0 (ARG otherwise);
+ *   B: device complex128 [n_edge][N_T]; C: device complex128 [n_edge][n_edge];
+ *   V, X: device complex128 [nrhs][N_T + n_edge] (X: output; no initial guess).
+ * The A-solves run ztoep_solve with opts (the n_edge solves for F in chunks of
+ * up to 256 right-hand sides); info (host [nrhs], may be NULL) receives the
+ * solves for U.  The contractions over N_T and n_edge are FP64; S is solved by
+ * FP64 Gauss-Jordan elimination with partial pivoting.  Allocates
+ * (n_edge + 2 nrhs) N_T + n_edge (n_edge + nrhs) complex128 of stream-ordered
+ * workspace and returns after the work completes.  Errors: ARG, NOMEM, CUDA,
+ * NONFINITE (singular S), and NOCONV/TIMEOUT from an A-solve (the solution is
+ * still formed). */
+ZTOEP_API ztoep_status_t ztoep_solve_schur(ztoep_plan_t plan_A, int32_t n_edge, const void *B, const void *C,
+                                           const ztoep_solve_opts_t *opts, int32_t nrhs, const void *V, void *X,
+                                           ztoep_solve_info_t *info, void *stream);
+
 /* ---- Far field (Sec. III, Eqs. farfieldBasis and tensorProd) ----
  * Far field of the element currents on the array-factor grid of the plan's
  * embedding: direction f = ky*lx + kx has k a u = 2 pi kx / lx and

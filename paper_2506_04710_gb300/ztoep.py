@@ -106,7 +106,7 @@ EXPORTS = ["ztoep_default_opts", "ztoep_plan", "ztoep_matvec", "ztoep_solve", "z
            "ztoep_forward_spectrum", "ztoep_plan_spectrum", "ztoep_plan_get_info", "ztoep_footprint",
            "ztoep_plan_destroy", "ztoep_status_string", "ztoep_version", "ztoep_launch_count",
            "ztoep_timing_enable", "ztoep_timing_reset", "ztoep_timing_read", "ztoep_edge_product_noalloc",
-           "ztoep_port_matrices", "ztoep_far_field_grid",
+           "ztoep_port_matrices", "ztoep_far_field_grid", "ztoep_solve_schur",
            "ztoep_sched_create", "ztoep_sched_submit", "ztoep_sched_poll", "ztoep_sched_wait",
            "ztoep_sched_get_stats", "ztoep_sched_destroy", "ztoep_plan_autotune", "ztoep_plan_tuned",
            "ztoep_plan_get_tune"]
@@ -141,6 +141,9 @@ def lib(path: str | None = None):
     L.ztoep_plan_spectrum.restype = c_i32
     L.ztoep_plan_get_info.argtypes = [c_p, ctypes.POINTER(PlanInfo)]
     L.ztoep_plan_get_info.restype = c_i32
+    L.ztoep_solve_schur.argtypes = [c_p, c_i32, c_p, c_p, ctypes.POINTER(SolveOpts), c_i32, c_p, c_p,
+                                    ctypes.POINTER(SolveInfo), c_p]
+    L.ztoep_solve_schur.restype = c_i32
     L.ztoep_far_field_grid.argtypes = [c_p, c_i32, c_p, c_i32, c_p, ctypes.c_double, ctypes.c_double, c_p, c_p]
     L.ztoep_far_field_grid.restype = c_i32
     L.ztoep_port_matrices.argtypes = [c_i32, ctypes.c_int64, c_p, c_p, c_p, c_p, c_p, c_p, c_p]
@@ -311,6 +314,11 @@ def ztoep_port_matrices(p: int, n: int, I, ports, edge_len, z0, Y, S, stream=Non
     za = np.ascontiguousarray(z0, dtype=np.float64)
     return lib().ztoep_port_matrices(p, n, _dptr(I), pa.ctypes.data_as(c_p), la.ctypes.data_as(c_p),
                                      za.ctypes.data_as(c_p), _dptr(Y), _dptr(S), _stream_ptr(stream))
+
+
+def ztoep_solve_schur(plan_A, n_edge: int, B, C, opts: SolveOpts, nrhs: int, V, X, info=None, stream=None) -> int:
+    return lib().ztoep_solve_schur(plan_A, n_edge, _dptr(B), _dptr(C), ctypes.byref(opts), nrhs, _dptr(V), _dptr(X),
+                                   info, _stream_ptr(stream))
 
 
 def ztoep_far_field_grid(plan, nrhs: int, I, npol: int, Fh, k: float, eta: float, F, stream=None) -> int:
