@@ -88,3 +88,35 @@ def test_no_cpu_fallback_when_library_missing(tmp_path):
     from paper_2506_04710_gb300 import ztoep
     with pytest.raises(RuntimeError):
         ztoep.lib(str(tmp_path / "missing.so"))
+
+
+def test_post_solve_entry_points_validate_on_the_host(lib):
+    """Argument checks of the port-matrix, far-field and Schur entry points
+    return ARG before any device work (no GPU needed): bad port indices,
+    lengths, impedances, sizes and missing plans."""
+    import ctypes
+    import numpy as np
+    from paper_2506_04710_gb300 import ztoep
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced on these paths
+    fake2 = ctypes.c_void_p(0x2000)
+    fake3 = ctypes.c_void_p(0x3000)
+    ports = np.array([0, 4, 9], np.int32)
+    ones = np.ones(3)
+    z0 = np.full(3, 50.0)
+
+    def pm(p, n, prt, ln, z):
+        return lib.ztoep_port_matrices(p, n, fake, prt.ctypes.data_as(ctypes.c_void_p),
+                                       ln.ctypes.data_as(ctypes.c_void_p), z.ctypes.data_as(ctypes.c_void_p),
+                                       fake2, fake3, None)
+    assert pm(0, 10, ports, ones, z0) == ztoep.ZTOEP_ERR_ARG
+    assert pm(3, 9, ports, ones, z0) == ztoep.ZTOEP_ERR_ARG                    # port 9 >= n
+    assert pm(3, 10, np.array([0, -1, 9], np.int32), ones, z0) == ztoep.ZTOEP_ERR_ARG
+    assert pm(3, 10, ports, np.array([1.0, np.inf, 1.0]), z0) == ztoep.ZTOEP_ERR_ARG
+    assert pm(3, 10, ports, ones, np.array([50.0, 0.0, 50.0])) == ztoep.ZTOEP_ERR_ARG
+    assert lib.ztoep_port_matrices(3, 10, fake, ports.ctypes.data_as(ctypes.c_void_p),
+                                   ones.ctypes.data_as(ctypes.c_void_p), z0.ctypes.data_as(ctypes.c_void_p),
+                                   fake2, fake2, None) == ztoep.ZTOEP_ERR_ARG  # Y aliases S
+    assert lib.ztoep_far_field_grid(None, 1, fake, 2, fake2, 1.0, 1.0, fake3, None) == ztoep.ZTOEP_ERR_ARG
+    o = ztoep.ztoep_default_opts()
+    assert lib.ztoep_solve_schur(None, 8, fake, fake2, ctypes.byref(o), 1, fake3, ctypes.c_void_p(0x4000),
+                                 None, None) == ztoep.ZTOEP_ERR_ARG
