@@ -155,22 +155,30 @@ ZTOEP_API ztoep_status_t ztoep_default_opts(ztoep_solve_opts_t *opts);
 ZTOEP_API ztoep_status_t ztoep_plan(const ztoep_desc_t *desc, const void *T, const void *B, const void *C,
                           void *stream, ztoep_plan_t *out);
 
-/* Y = Z' X for nrhs right-hand sides (Z' with absent elements masked).
- *   X, Y: device complex128 [nrhs][N], distinct buffers.
+/* Y = Z' X for nrhs right-hand sides (Z' with absent elements masked): the
+ * left-hand side of Z I = V (Sec. II, Eq. MoMMatrixEq) with Z in the block
+ * form of Sec. II-C, Eq. matrixForm, and its element block A applied through
+ * the two-level block-Toeplitz structure of Eq. submatrixAA (circulant
+ * embedding, 2-D FFT over the element indices, per-frequency b x b block
+ * product, inverse FFT, crop; the FFT acceleration of Sec. I), B, B^T and C
+ * applied directly.
+ *   X, Y: device complex128 [nrhs][N]; the two byte ranges must not overlap.
  *   prec: ZTOEP_FP64 computes in FP64; ZTOEP_MIXED rounds X to FP32 and
  *   computes the FFTs and products in FP32 (result widened to FP64).
- * Errors: ARG, NOMEM (workspace), CUDA. */
+ * Errors: ARG (also for overlapping X and Y), NOMEM (workspace), CUDA. */
 ZTOEP_API ztoep_status_t ztoep_matvec(ztoep_plan_t plan, int32_t prec, int32_t nrhs, const void *X, void *Y,
                             void *stream);
 
-/* Edge-coupling part of the FP64 product, allocating nothing (the paper has
- * no counterpart; this is a service for callers that cannot allocate device
- * memory at call time: code inside a CUDA stream capture in global mode,
- * where cudaMalloc is an error, hosts that forbid allocation after start-up,
- * and frameworks whose memory pool owns all device memory).
+/* Edge-coupling part of the FP64 product, allocating nothing.  The paper has
+ * no counterpart: this is a service for callers that cannot allocate device
+ * memory at call time, such as real-time or embedded hosts that forbid
+ * allocation after start-up (an allocation may wait for the whole device or
+ * fail under fragmentation at an unpredictable moment) and frameworks whose
+ * memory pool has already reserved all device memory.
  *   Y[r][t]       = sum_e B[e][t] x_E[r][e]                 (t < N_T; 0 on absent elements)
  *   Y[r][N_T + e] = sum_t B[e][t] x_T[r][t] + sum_e' C[e][e'] x_E[r][e']
- *   X, Y: device complex128 [nrhs][N], distinct.  The plan's device must be
+ *   X, Y: device complex128 [nrhs][N]; the two byte ranges must not overlap
+ *   (ARG otherwise).  The plan's device must be
  *   current.  The partial sums live in a fixed 16 MiB device array that every
  *   device holding this library keeps until the process exits; nrhs is
  *   limited by it (about 4 for a 32x32 array with b = 64 and 512 edge
@@ -185,7 +193,10 @@ ZTOEP_API ztoep_status_t ztoep_matvec(ztoep_plan_t plan, int32_t prec, int32_t n
 ZTOEP_API ztoep_status_t ztoep_edge_product_noalloc(ztoep_plan_t plan, int32_t nrhs, const void *X, void *Y,
                                                     void *stream);
 
-/* Solve Z' X = V for nrhs right-hand sides.
+/* Solve Z' X = V (Sec. II, Eq. MoMMatrixEq; Z' as for ztoep_matvec) for nrhs
+ * right-hand sides by batched restarted GMRES, the iterative solver the paper
+ * names for the second Toeplitz level (Sec. II-D), with the FFT products of
+ * Sec. I inside an FP64 iterative-refinement loop.
  *   V: device complex128 [nrhs][N].
  *   X: device complex128 [nrhs][N]; initial guess on entry, solution on
  *      exit (on NOCONV/TIMEOUT the best iterate).
@@ -377,7 +388,8 @@ ZTOEP_API const char *ztoep_version(void);
  * A scheduler owns worker threads, each with its own CUDA stream.  Submitted
  * requests (any nx, ny, b, n_edge, nrhs) wait in a FIFO queue and are
  * admitted as soon as a worker is free and the device bytes they need fit in
- * the budget (ztoep_footprint of the request, plus the plans kept resident);
+ * the budget (ztoep_footprint of the request, plus, for host inputs, its
+ * device staging copies of T, B and C, plus the plans kept resident);
  * admitted requests run concurrently, so their kernels overlap on the device.
  * Plans (the FFT'd generating blocks, B and C) stay resident under their
  * plan_key and are reused by later requests with the same key; idle ones are

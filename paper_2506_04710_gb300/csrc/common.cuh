@@ -215,6 +215,11 @@ namespace ztoep {
     } while (0)
 
 ztoep_status_t dalloc(void **p, size_t bytes, size_t *acc);
+// True when the byte ranges [a, a + na) and [b, b + nb) share a byte.
+inline bool bytes_overlap(const void *a, size_t na, const void *b, size_t nb) {
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
+}
 // Build a plan with the given launch/layout choices (ztoep_plan uses the defaults).
 ztoep_status_t plan_create(const ztoep_desc_t *d, const void *T, const void *B, const void *C, cudaStream_t s,
                            const TuneParams &tp, ztoep_plan_t *out);

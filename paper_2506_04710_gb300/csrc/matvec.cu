@@ -1058,9 +1058,11 @@ ztoep_status_t ensure_tensor_data(ztoep_plan_t p, int nrhs, cudaStream_t s) {
 
 // ------------------------------------------------------------ allocation-free edge product
 // Some callers cannot allocate device memory when they call into the library:
-// code running inside a CUDA stream capture in global capture mode (where a
-// cudaMalloc is an error), real-time or embedded hosts that forbid allocation
-// after start-up, and frameworks whose memory pool owns every device byte.
+// real-time or embedded hosts that forbid allocation after start-up (an
+// allocation can block for a device-wide synchronisation or fail under
+// fragmentation at an unpredictable moment), and frameworks whose memory pool
+// has already reserved every device byte, so that a cudaMalloc of ours would
+// fail or evict their cache.
 // For them ztoep_edge_product_noalloc computes the edge-coupling part of the
 // FP64 product with its partial sums in the fixed array below instead of the
 // plan's lazily allocated workspace.  The array is 16 MiB, lives on every
@@ -1112,7 +1114,9 @@ static size_t round256(size_t n) { return (n + 255) / 256 * 256; }
 extern "C" ztoep_status_t ztoep_edge_product_noalloc(ztoep_plan_t p, int32_t nrhs, const void *X, void *Y,
                                                      void *stream) {
     using namespace ztoep;
-    if (!p || !X || !Y || nrhs < 1 || X == Y) return ZTOEP_ERR_ARG;
+    if (!p || !X || !Y || nrhs < 1) return ZTOEP_ERR_ARG;
+    const size_t vbytes = sizeof(double2) * (size_t)nrhs * p->N;
+    if (bytes_overlap(X, vbytes, Y, vbytes)) return ZTOEP_ERR_ARG;
     int dev = -1;
     ZT_CUDA(cudaGetDevice(&dev));
     if (dev != p->device) return ZTOEP_ERR_ARG;

@@ -417,7 +417,9 @@ size_t ztoep_footprint(const ztoep_desc_t *d, int32_t max_nrhs, int32_t restart)
 }
 
 ztoep_status_t ztoep_matvec(ztoep_plan_t p, int32_t prec, int32_t nrhs, const void *X, void *Y, void *stream) {
-    if (!p || !X || !Y || nrhs < 1 || X == Y) return ZTOEP_ERR_ARG;
+    if (!p || !X || !Y || nrhs < 1) return ZTOEP_ERR_ARG;
+    const size_t vbytes = sizeof(double2) * (size_t)nrhs * p->N;
+    if (bytes_overlap(X, vbytes, Y, vbytes)) return ZTOEP_ERR_ARG;
     if (prec != ZTOEP_FP64 && prec != ZTOEP_MIXED) return ZTOEP_ERR_ARG;
     std::lock_guard<std::mutex> lk(p->mu);
     cudaStream_t s = (cudaStream_t)stream;

@@ -63,6 +63,10 @@ struct ztoep_sched_s {
     size_t bytes_work = 0, peak = 0;
     int64_t built = 0, reused = 0, evicted = 0;
     uint64_t tick = 0;
+    // Plans evicted under mu, destroyed by a worker after it releases mu:
+    // ztoep_plan_destroy frees device memory, and cudaFree can wait for the
+    // whole device, which must not block the other workers' bookkeeping.
+    std::vector<ztoep_plan_t> doomed;
 
     size_t idle_plan_bytes() const {
         size_t s = 0;
@@ -92,7 +96,7 @@ struct ztoep_sched_s {
                     (victim == plans.end() || it->second.last_use < victim->second.last_use))
                     victim = it;
             if (victim == plans.end()) return false;
-            if (!o.fake_backend) ztoep_plan_destroy(victim->second.plan);
+            if (!o.fake_backend) doomed.push_back(victim->second.plan);
             plans.erase(victim);
             ++evicted;
         }
@@ -149,8 +153,9 @@ struct ztoep_sched_s {
                 const size_t tb = sizeof(double2) * (size_t)(2 * r.desc.ny - 1) * (2 * r.desc.nx - 1) * r.desc.b * r.desc.b;
                 const size_t bb = sizeof(double2) * (size_t)e * nt, cb = sizeof(double2) * (size_t)e * e;
                 void *dT = nullptr, *dB = nullptr, *dC = nullptr;
-                bool ok = cudaMalloc(&dT, tb) == cudaSuccess;
-                if (ok && e > 0) ok = cudaMalloc(&dB, bb) == cudaSuccess && cudaMalloc(&dC, cb) == cudaSuccess;
+                // stream-ordered staging (counted in the request's reserved bytes)
+                bool ok = cudaMallocAsync(&dT, tb, s) == cudaSuccess;
+                if (ok && e > 0) ok = cudaMallocAsync(&dB, bb, s) == cudaSuccess && cudaMallocAsync(&dC, cb, s) == cudaSuccess;
                 if (ok) {
                     cudaMemcpyAsync(dT, r.T, tb, cudaMemcpyHostToDevice, s);
                     if (e > 0) {
@@ -163,9 +168,10 @@ struct ztoep_sched_s {
                     cudaGetLastError();
                     st = ZTOEP_ERR_NOMEM;
                 }
-                cudaFree(dT);
-                cudaFree(dB);
-                cudaFree(dC);
+                if (dT) cudaFreeAsync(dT, s);
+                if (dB) cudaFreeAsync(dB, s);
+                if (dC) cudaFreeAsync(dC, s);
+                cudaStreamSynchronize(s);
             }
         }
         if (!from_cache) {
@@ -211,10 +217,16 @@ struct ztoep_sched_s {
         }
         for (;;) {
             Req *q = nullptr;
+            std::vector<ztoep_plan_t> victims;
             {
                 std::unique_lock<std::mutex> lk(mu);
                 cv_work.wait(lk, [&] { return (stop && queue.empty()) || (!queue.empty() && try_admit(queue.front())); });
-                if (queue.empty()) break;
+                victims.swap(doomed);
+                if (queue.empty()) {
+                    lk.unlock();
+                    for (ztoep_plan_t v : victims) ztoep_plan_destroy(v);
+                    break;
+                }
                 q = queue.front();
                 queue.pop_front();
                 q->state = 1;
@@ -222,6 +234,7 @@ struct ztoep_sched_s {
                 ++in_flight;
                 max_in_flight = std::max(max_in_flight, in_flight);
             }
+            for (ztoep_plan_t v : victims) ztoep_plan_destroy(v);  // outside mu
             run(q, s);
             {
                 std::lock_guard<std::mutex> lk(mu);
@@ -265,8 +278,13 @@ ztoep_status_t ztoep_sched_create(const ztoep_sched_opts_t *o, ztoep_sched_t *ou
 ztoep_status_t ztoep_sched_submit(ztoep_sched_t s, const ztoep_request_t *r, int64_t *id) {
     if (!s || !r || !id || r->nrhs < 1 || !r->T || !r->V || !r->X) return ZTOEP_ERR_ARG;
     if (r->desc.n_edge > 0 && (!r->B || !r->C)) return ZTOEP_ERR_ARG;
-    const size_t fp = ztoep_footprint(&r->desc, r->nrhs, r->opts.restart > 0 ? r->opts.restart : 30);
+    size_t fp = ztoep_footprint(&r->desc, r->nrhs, r->opts.restart > 0 ? r->opts.restart : 30);
     if (fp == 0) return ZTOEP_ERR_ARG;
+    if (!r->inputs_on_device) {  // device staging copies of T, B and C for the plan build
+        const size_t nt = (size_t)r->desc.nx * r->desc.ny * r->desc.b, e = (size_t)r->desc.n_edge;
+        fp += sizeof(double) * 2 *
+              ((size_t)(2 * r->desc.ny - 1) * (2 * r->desc.nx - 1) * r->desc.b * r->desc.b + e * nt + e * e);
+    }
     if (fp > s->o.hbm_budget) return ZTOEP_ERR_NOMEM;
     auto q = std::make_unique<Req>();
     q->r = *r;
@@ -346,6 +364,7 @@ void ztoep_sched_destroy(ztoep_sched_t s) {
     if (!s->o.fake_backend) {
         cudaSetDevice(s->o.device);
         for (auto &kv : s->plans) ztoep_plan_destroy(kv.second.plan);
+        for (ztoep_plan_t v : s->doomed) ztoep_plan_destroy(v);
     }
     delete s;
 }

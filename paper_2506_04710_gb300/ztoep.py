@@ -348,8 +348,8 @@ def ztoep_plan_destroy(plan) -> None:
 
 def ztoep_edge_product_noalloc(plan, nrhs: int, X, Y, stream=None) -> int:
     """Edge-coupling part of the FP64 product with no device allocation (for
-    callers that cannot allocate at call time, e.g. inside a global-mode stream
-    capture); scratch is a fixed 16 MiB device array shared by all calls."""
+    callers that cannot allocate at call time, e.g. hosts that forbid allocation
+    after start-up); scratch is a fixed 16 MiB device array shared by all calls."""
     return lib().ztoep_edge_product_noalloc(plan, nrhs, _dptr(X), _dptr(Y), _stream_ptr(stream))
 
 

@@ -145,3 +145,21 @@ def test_c4_64x64_b96_planewaves_sampled():
     vn = np.linalg.norm(prob.V, axis=1)
     assert np.all(np.abs(r) <= tol * vn[:, None])
     plan.close()
+
+
+@pytest.mark.slow
+def test_c4_64x64_b96_manufactured_both_precisions():
+    """Full-size 64x64 b96 system (the tensor-core edge GEMMs, K split and the
+    128-point passes at full size): V = Z x* by the oracle's direct product
+    from the blocks, then both precisions solve it to 1e-10 and must return x*
+    to 1e-7 (cond(Z) x residual)."""
+    prob, _ = synth.config_problem("c4_64x64_b96")
+    xs = synth.manufactured_solution(prob, 1, seed=64)
+    V = oracle.matvec_blocks(prob, xs)
+    plan = ztoep.Plan.from_problem(prob)
+    for prec in (ztoep.ZTOEP_MIXED, ztoep.ZTOEP_FP64):
+        X, info, st = plan.solve(dev(V), opts=opts(prec, 1e-10))
+        assert st == 0 and info[0]["rel_residual"] <= 1e-10
+        err = np.linalg.norm(X.cpu().numpy() - xs) / np.linalg.norm(xs)
+        assert err <= 1e-7, (prec, err)
+    plan.close()

@@ -1,11 +1,17 @@
 """Serving: requests of different sizes and RHS counts run concurrently
 through the scheduler; each result must be the same as the one of the same
 request solved alone (bitwise: the scheduler runs exactly the same kernels),
-resident plans are reused under their key, and device-side inputs work."""
+resident plans are reused under their key, and device-side inputs work.
+Requests shaped like the large ones of the serving stream (b = 96 with 64 RHS,
+a 32x32 b64 array with 40 RHS, perimeter edge layout through the side spectra)
+are checked against the oracle: residual components on sampled rows from its
+direct product (|r_k| <= tol ||v|| follows from ||r|| <= tol ||v||), and a
+small request solved to 1e-11 against its LU solution."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2506_04710_gb300 import synth, ztoep
 
 pytestmark = pytest.mark.gpu
@@ -78,4 +84,49 @@ def test_device_side_inputs():
     assert np.max(np.abs(d["T"].cpu().numpy() - ph.T)) <= 1e-12 * np.max(np.abs(ph.T))
     assert np.max(np.abs(d["B"].cpu().numpy() - ph.B)) <= 1e-12 * np.max(np.abs(ph.B))
     assert np.max(np.abs(d["V"].cpu().numpy() - ph.V)) <= 1e-12
+    s.close()
+
+
+def sample_rows(prob, count, seed=9):
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(prob.n, size=min(count, prob.n), replace=False)
+    edge = np.arange(prob.n_toep, prob.n)[:: max(1, prob.n_edge // 16)]
+    return np.unique(np.concatenate([rows, edge, [0, prob.n_toep - 1, prob.n - 1]]))
+
+
+def test_stream_shaped_requests_against_oracle():
+    # (nx, b, nrhs, design seed, tol): E = 16 nx, 4 edge unknowns per cell side
+    shapes = [(24, 96, 64, 1001, 1e-8), (32, 64, 40, 1002, 1e-8), (6, 32, 5, 1003, 1e-11)]
+    probs = [synth.make_problem(nx, nx, b, 16 * nx, seed=sd, rhs="planewave", nrhs=r) for nx, b, r, sd, _ in shapes]
+    assert all(p.edge_per_cell == 4 for p in probs)
+    s = ztoep.Scheduler(hbm_budget=48 << 30, workers=3)
+    subs = []
+    for p, (nx, b, r, sd, tol) in zip(probs, shapes):
+        o = opts()
+        o.tol = tol
+        T, B, C, V = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (p.T, p.B, p.C, p.V))
+        X = torch.zeros_like(V)
+        rid = s.submit((nx, nx, b, p.n_edge, None, 0, 0, 4), T, B, C, V, X, opts=o, on_device=True)
+        subs.append((rid, p, o, X))
+    for rid, p, o, X in subs:
+        rc, st, info = s.wait(rid, 300000)
+        assert rc == 0 and st.status == 0
+        Xh = X.cpu().numpy()
+        assert max(i["rel_residual"] for i in info) <= o.tol
+        rows = sample_rows(p, 160)
+        r = p.V[:, rows] - oracle.matvec_rows(p, Xh, rows)
+        vn = np.linalg.norm(p.V, axis=1)
+        assert np.all(np.abs(r) <= o.tol * vn[:, None])
+        # the same request alone on the same layout: bitwise the same result
+        plan = ztoep.Plan.from_problem(p, structured=True)
+        Xa, _, sta = plan.solve(torch.from_numpy(p.V.copy()).cuda(), opts=o)
+        plan.close()
+        assert sta == 0 and torch.equal(X.cpu(), Xa.cpu())
+        if p.n <= 4096:  # small request: the solution against the oracle's LU
+            Z = oracle.assemble(p)
+            xref = oracle.LU(Z).solve(p.V)
+            err = np.linalg.norm(Xh - xref, axis=1) / np.linalg.norm(xref, axis=1)
+            assert err.max() <= 1e-7
+            assert oracle.relres(Z, Xh, p.V).max() <= o.tol
+    assert s.stats().max_in_flight >= 2
     s.close()

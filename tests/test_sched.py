@@ -16,8 +16,11 @@ def dummy():
 
 
 def fp_of(nx, b, e, nrhs):
+    """Bytes a host-input request reserves: the footprint plus the device
+    staging copies of T, B and C for its plan build."""
     d, _ = ztoep.make_desc(nx, nx, b, e)
-    return ztoep.ztoep_footprint(d, nrhs, 30)
+    staging = 16 * ((2 * nx - 1) ** 2 * b * b + e * nx * nx * b + e * e)
+    return ztoep.ztoep_footprint(d, nrhs, 30) + staging
 
 
 def submit(s, nx, b, e, nrhs, key=0):

@@ -1,8 +1,8 @@
 """The allocation-free edge product (for callers that cannot allocate device
-memory at call time, such as code inside a global-mode stream capture or under
-a framework that owns the device memory) must give the same numbers as the
-regular product, call after call, although all calls share one fixed scratch
-array.
+memory at call time, such as hosts that forbid allocation after start-up or a
+framework whose pool has reserved the device memory) must give the same numbers
+as the regular product, call after call, although all calls share one fixed
+scratch array, and must not allocate.
 
 Checked against ztoep_matvec (FP64) through the C-ABI:
   edge rows     Y[:, NT:] = (Z'X)[:, NT:]                       (<= 1e-12, max-norm relative)
@@ -76,6 +76,43 @@ def test_noalloc_full_size_array_and_cap():
     assert ztoep.ztoep_edge_product_noalloc(plan.handle, 8, X8, Y8) == ztoep.ZTOEP_ERR_NOMEM
     torch.cuda.synchronize()
     assert torch.count_nonzero(Y8).item() == 0
+    plan.close()
+
+
+def test_noalloc_allocates_nothing_on_a_fresh_plan():
+    """Free device memory (cudaMemGetInfo) is unchanged across calls on a plan
+    that has never run a product, so no workspace exists yet: the regular
+    product would allocate its partial sums here, this entry point must not."""
+    prob = synth.make_problem(6, 5, 16, 22, seed=17, rhs="planewave", nrhs=2)
+    # first call on this device (scratch address lookup, kernels loaded) on
+    # another plan with the same RHS count, so the same kernels run below
+    wprob = synth.make_problem(4, 3, 8, 10, seed=18, rhs="planewave", nrhs=2)
+    warm = ztoep.Plan.from_problem(wprob)
+    Xw = dev(wprob.V)
+    assert ztoep.ztoep_edge_product_noalloc(warm.handle, 2, Xw, torch.empty_like(Xw)) == ztoep.ZTOEP_OK
+    plan = ztoep.Plan.from_problem(prob)
+    X = dev(prob.V)
+    Y = torch.empty_like(X)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        assert ztoep.ztoep_edge_product_noalloc(plan.handle, prob.nrhs, X, Y) == ztoep.ZTOEP_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    _, edge_ref, full = reference_parts(plan, X, prob.n_toep)
+    assert (Y[:, prob.n_toep:] - edge_ref).abs().max().item() <= TOL * full.abs().max().item()
+    plan.close()
+    warm.close()
+
+
+def test_noalloc_rejects_overlapping_buffers():
+    prob = synth.make_problem(3, 4, 5, 6, seed=4, rhs="planewave", nrhs=2)
+    plan = ztoep.Plan.from_problem(prob)
+    buf = torch.zeros((3, prob.n), dtype=torch.complex128, device="cuda")
+    X, Y = buf[0:2], buf[1:3]  # one RHS row shared
+    assert ztoep.ztoep_edge_product_noalloc(plan.handle, 2, X, Y) == ztoep.ZTOEP_ERR_ARG
+    assert ztoep.ztoep_matvec(plan.handle, ztoep.ZTOEP_FP64, 2, X, Y, None) == ztoep.ZTOEP_ERR_ARG
     plan.close()
 
 
