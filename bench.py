@@ -318,7 +318,8 @@ def run_ours(args, world, rank, local):
     hbm = pk.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    edge_bytes = E * NT * 8 + 2 * NT * 8 * nrhs + E * 8 * nrhs
+    # [B | C] read once (B and C in one pass), x read, B^T x_E and y_E written
+    edge_bytes = E * (NT + E) * 8 + (NT + E) * 8 * nrhs + (NT + E) * 8 * nrhs
     edge_us = kt_alone["edge"]["avg_us"]
     edge_gbs = edge_bytes / (edge_us / 1e6) / 1e9 if edge_us > 0 else None
     bp_bytes = plan.info.n_pairs * b * b * 8 + 2 * F * b * nrhs * 8
@@ -339,16 +340,16 @@ def run_ours(args, world, rank, local):
                     "frac_concurrent": (bp_bytes / (kt["blockprod"]["avg_us"] / 1e6) / 1e9 / hbm)
                     if kt["blockprod"]["avg_us"] > 0 else None}
     else:
-        roofline = {"kernel": "k_edge2 (FP32 B x_T and B^T x_E, one pass over B)", "bound": "hbm",
+        roofline = {"kernel": "k_edge3 (FP32 B x_T + C x_E and B^T x_E, one pass over [B | C])", "bound": "hbm",
                     "achieved": edge_gbs, "peak": hbm, "unit": "GB/s",
                     "frac": (edge_gbs / hbm) if edge_gbs else None,
-                    "traffic": profiled_traffic("k_edge2_c2_32x32_b64.md",
-                                                r"template <int RC>\n__global__ void __launch_bounds__\(256\) k_edge2\(.*?\n}\n"),
+                    "traffic": profiled_traffic("k_edge3_c2_32x32_b64.md",
+                                                r"template <int RC>\n__global__ void __launch_bounds__\(256\) k_edge3\(.*?\n}\n"),
                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                                      "profiles/k_edge2_c2_32x32_b64.md",
+                                      "profiles/k_edge3_c2_32x32_b64.md",
                     "bytes_per_launch": edge_bytes, "avg_launch_us": edge_us,
                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-                    "timed": f"CUDA events around each k_edge launch over {nmv} FP32 products, "
+                    "timed": f"CUDA events around each k_edge3 launch over {nmv} FP32 products, "
                              "branches serialised (the kernel alone)",
                     "frac_concurrent": (edge_bytes / (kt["edge"]["avg_us"] / 1e6) / 1e9 / hbm)
                     if kt["edge"]["avg_us"] > 0 else None}

@@ -214,6 +214,30 @@ ZTOEP_API ztoep_status_t ztoep_edge_product_noalloc(ztoep_plan_t plan, int32_t n
 ZTOEP_API ztoep_status_t ztoep_solve(ztoep_plan_t plan, const ztoep_solve_opts_t *opts, int32_t nrhs,
                            const void *V, void *X, ztoep_solve_info_t *info, void *stream);
 
+/* One solve of `count` independent systems (1..8 plans of any sizes: nx,
+ * ny, b, n_edge may all differ), each member exactly as ztoep_solve would
+ * solve it alone (the same arithmetic, hence bitwise the same result and
+ * info), but as one CUDA graph in which every Arnoldi, residual and update
+ * step is a single launch over all members' RHS and the members' products
+ * run concurrently (a member with no RHS left in a cycle skips its product).
+ * This serves many small or uneven systems (serving, parameter sweeps) whose
+ * separate solves would each be bound by launch latency.
+ *   plans: host array [count] of distinct plans on the current device.
+ *   opts: one set of options for all members (one control loop).
+ *   nrhs: host int32 [count]; V, X: host arrays [count] of device pointers,
+ *   V[i], X[i] complex128 [nrhs[i]][N_i] (X[i]: initial guess in, solution out).
+ *   info: host array [count] of host arrays [nrhs[i]] (entries may be NULL),
+ *   or NULL.
+ * The graph is built for the call and released after it (a few ms of host
+ * time).  Returns the worst per-RHS status after synchronising `stream`.
+ * Errors: ARG (bad counts or pointers, a plan given twice, plans on different
+ * devices), UNSUPPORTED (members whose sizes need different chunk shapes:
+ * systems above 8 x (SM count) x 256 unknowns cannot be grouped with smaller
+ * ones), NOMEM, CUDA; per-RHS NOCONV/TIMEOUT/NONFINITE as ztoep_solve. */
+ZTOEP_API ztoep_status_t ztoep_solve_group(int32_t count, const ztoep_plan_t *plans, const ztoep_solve_opts_t *opts,
+                                           const int32_t *nrhs, const void *const *V, void *const *X,
+                                           ztoep_solve_info_t *const *info, void *stream);
+
 /* ztoep_solve with V and X in HOST memory (pinned or pageable): copies V
  * and the initial guess to the device, solves, copies X back.  The device
  * buffers are the plan's own. */

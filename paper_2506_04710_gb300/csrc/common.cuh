@@ -119,6 +119,8 @@ struct MatvecWs {  // per-precision matvec workspace, sized for `cap` RHS
     void *Yh = nullptr;     // [F][cap][b] out-of-place block-product output (tensor path, side plans)
     void *Fs = nullptr;     // [4k][cap][Lmax] side products B x_T along each side, frequency domain
     void *Us = nullptr;     // [cap][4k][Lmax] DFTs of the side slices of x_E
+    void *Eg = nullptr;     // [ngroups][cap][E] group sums of the FP32 edge-row partials
+    unsigned *cnt = nullptr;  // [ngroups + 1] last-arriver tickets of the FP32 edge kernel
     size_t bytes = 0;
 };
 
@@ -138,11 +140,12 @@ struct SolveWs {  // Krylov workspace, sized for `cap` RHS and restart `m`
     double2 *y = nullptr;      // [cap][m] least-squares solution
     double2 *h1 = nullptr;     // [cap][m+1]
     double2 *h2 = nullptr;     // [cap][m+1]
-    double2 *part = nullptr;   // [cap][nchunk][m+2] per-CTA partial sums
+    double2 *part = nullptr;   // [cap][nchunk + ngroups][m+2] chunk and group partial sums
     double *nrm = nullptr;     // [cap][8] scalars, then [cap][m+1] basis norms
     int *st = nullptr;         // [cap][8] per-RHS state
-    unsigned *cnt = nullptr;   // [cap][4] last-CTA counters
+    unsigned *cnt = nullptr;   // [cap][cstride] last-arriver tickets of the cross-CTA sums
     void *ctl = nullptr;       // device solve control block
+    int cstride = 0;           // reduction tickets per RHS
     int *hst = nullptr;        // host pinned mirror of st (+ control words)
     double *hnrm = nullptr;    // host pinned mirror of nrm
     size_t bytes = 0;
@@ -175,7 +178,7 @@ struct ztoep_plan_s {
     double2 *That64 = nullptr;      // [npairs][b][b]
     float2 *That32 = nullptr;
     double2 *B64 = nullptr;         // [E][NT], absent elements' columns zero
-    float2 *B32 = nullptr;
+    float2 *B32 = nullptr;          // [E][ldb32] = [B | C | 0] (FP32 edge kernel reads one row for y_E)
     double2 *C64 = nullptr;         // [E][E]
     float2 *C32 = nullptr;
     float2 *That32full = nullptr;   // [F][b][b] every frequency, for the tensor-core product

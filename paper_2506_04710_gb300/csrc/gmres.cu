@@ -14,10 +14,13 @@
 // The basis is kept unnormalised: u_k with v_k = u_k / beta_k, so no kernel
 // pass is spent on normalising; every use of v_k folds 1/beta_k into its
 // coefficient.
-// Every kernel is batched over the RHS (grid.y) and each RHS stops on its own
-// flag.  Cross-CTA reductions use the last-CTA-done pattern (atomic ticket,
-// no waiting), so the summation order is fixed and results do not depend on
-// the batch.
+// Every step kernel runs over a work list: the RHS of one or several systems
+// (a group of plans of any sizes, one launch per step for all of them), each
+// RHS cut into chunks whose size depends only on its system.  Each RHS stops
+// on its own flags.  Cross-CTA sums use last-arriver tickets (no waiting) and
+// a fixed summation order, so a RHS is summed identically alone, in a batch
+// and in a group.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -39,16 +42,22 @@ enum { NM_VNORM = 0, NM_TARGET = 2, NM_RNORM = 3, NM_W0 = 5, NM_RIN = 6, NM_STRI
 // early when a restart reduces the inner residual by less than 10%.
 constexpr int kMaxRestarts = 64;
 constexpr double kStagnation = 0.9;
-enum { CNT_STRIDE = 4 };
 // Second Gram-Schmidt pass when ||w'|| < eta ||w||.  The orthogonality lost by
 // one classical pass is about u ||w|| / ||w'||, so eta = 1/64 keeps it below
 // 64 u (~7e-15), far under what the residual targets need, while skipping the
 // pass in the usual case (the stricter 1/sqrt(2) of "twice is enough" asked
 // for it at every step on these systems, doubling the FP64 work).
 constexpr double kReorthEta = 1.0 / 64.0;
+// Chunks per first-level group of the cross-CTA reductions.
+constexpr int kRedGroup = 16;
+// Largest Gram-Schmidt column: j + 2 <= m + 1 with m <= 128.
+constexpr int kMaxK = 130;
+// Systems solved together in one group (one launch per step for all).
+constexpr int kMaxMembers = 8;
 
 // Device-side control of one solve (written by the host before each launch of
-// the solve graph; loop counters advanced by the control kernels).
+// the solve graph; loop counters advanced by the control kernels).  A group
+// of systems shares one.
 struct SolveCtl {
     int j;               // current inner iteration of the running cycle
     int sweeps;          // true-residual evaluations so far
@@ -60,34 +69,77 @@ struct SolveCtl {
     int restart_bodies;  // executions of the restart body
     int reorth_bodies;   // executions of the second Gram-Schmidt pass
     int cond_first, cond_sweep, cond_restart, cond_iter;  // loop decisions (read by the host-driven mode)
+    int reorth_pending;  // the step's second Gram-Schmidt pass (and iteration control) is still to run
+    unsigned tick;       // last-arriver ticket of the update kernel's grid
     double tol, inner_tol;
     long long timeout_ns;
     unsigned long long deadline;  // %globaltimer value, 0 = none
 };
 
+// One system's view of its solve workspace.
 struct GArgs {
     double2 *Vb;       // [(m+1)][cap][N] unnormalised basis u_k
     double2 *w;        // [cap][N] FP64 product output
-    double2 *x;        // [nrhs][N] iterate (caller's buffer)
+    double2 *x;        // [nrhs][N] iterate
     const double2 *v;  // [nrhs][N] right-hand sides
     float2 *x32;       // [cap][N] FP32 copy of the next product input (MIXED)
     const float2 *y32; // [cap][N] FP32 product output (MIXED)
-    double2 *H, *cs, *sn, *g, *y, *h1, *h2, *part;
+    double2 *H, *cs, *sn, *g, *h1, *h2;
+    double2 *part;     // [cap][nchunk + ngroups][pstride] chunk and group partial sums
     double *beta;      // [cap][m+1] ||u_k||
     double2 *xin64;    // [cap][N] FP64 copy of the next product input (FP64)
     double2 *rbuf;     // [cap][N] FP64 residual r of the sweep
     double2 *dbuf;     // [cap][N] correction d of the sweep
     double *nrm;
     int *st;
-    unsigned *cnt;
-    SolveCtl *ctl;
+    unsigned *cnt;     // [cap][cstride] reduction tickets
+    SolveCtl *ctl;     // shared by the group
     int64_t N;
-    int cap, m, nchunk, pstride, nrhs;
+    int cap, m, nchunk, per_cta, ngroups, cstride, pstride, nrhs;
     int mixed;
-    int graph;                             // running inside the solve graph
-    int redund;                            // pass-1 partials reduced by every update CTA (else by the dots' last CTA)
-    cudaGraphConditionalHandle h_reorth;   // second Gram-Schmidt pass needed by some RHS
 };
+
+// A launch's work list: the member systems, all with the same elements per
+// thread (ELEM of the kernel); member i owns (nchunk_i [+ 1]) * nrhs_i
+// consecutive CTAs.
+struct GroupArgs {
+    int n;
+    int graph;                                     // running inside a solve graph
+    cudaGraphConditionalHandle h_iter, h_reorth;   // iteration loop, second Gram-Schmidt pass
+    int prod_if;                                   // the members' iteration products sit in IF nodes
+    cudaGraphConditionalHandle h_prod[kMaxMembers];
+    GArgs m[kMaxMembers];
+};
+
+struct Loc {
+    int mi, rr, cx;
+};
+
+// The CTA's member, RHS and chunk (extra: one more CTA per RHS after its chunks).
+__device__ __forceinline__ Loc locate(const GroupArgs &g, bool extra) {
+    int b = blockIdx.x;
+    for (int i = 0; i < g.n; ++i) {
+        const int per = g.m[i].nchunk + (extra ? 1 : 0);
+        const int cnt = per * g.m[i].nrhs;
+        if (b < cnt) {
+            const int rr = b / per;
+            return {i, rr, b - rr * per};
+        }
+        b -= cnt;
+    }
+    return {-1, 0, 0};
+}
+
+// Element e of this thread in chunk cx: its index, or -1 outside the chunk.
+__device__ __forceinline__ int64_t elem_index(const GArgs &a, int cx, int e) {
+    const int off = e * blockDim.x + threadIdx.x;
+    const int64_t idx = (int64_t)cx * a.per_cta + off;
+    return (off < a.per_cta && idx < a.N) ? idx : -1;
+}
+
+__device__ __forceinline__ double2 *part_rows(const GArgs &a, int rr) {
+    return a.part + (int64_t)rr * (a.nchunk + a.ngroups) * a.pstride;
+}
 
 __device__ __forceinline__ double2 shfl_xor2(double2 v, int o) {
     v.x = __shfl_xor_sync(0xffffffffu, v.x, o);
@@ -124,20 +176,6 @@ __device__ __forceinline__ void warp_rs8(double2 (&v)[8]) {
     v[0] = v[0] + shfl_xor2(v[0], 1);
 }
 
-// CTA totals of 8 values into red[0..8) (red holds >= 8 * warps entries).
-__device__ __forceinline__ void block_sum8(double2 (&v)[8], double2 *red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    warp_rs8(v);
-    if ((lane & 3) == 0) red[warp * 8 + (((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1))] = v[0];
-    __syncthreads();
-    if (threadIdx.x < 8) {
-        double2 s = red[threadIdx.x];
-        for (int w = 1; w < nw; ++w) s = s + red[w * 8 + threadIdx.x];
-        red[threadIdx.x] = s;  // thread t only touches column t
-    }
-    __syncthreads();
-}
-
 // CTA total of one real value (valid in thread 0).
 __device__ __forceinline__ double block_sum1(double v, double *red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -152,101 +190,113 @@ __device__ __forceinline__ double block_sum1(double v, double *red) {
     return s;
 }
 
-// Last-CTA-done ticket for the CTAs of one RHS (no waiting).
-__device__ __forceinline__ bool last_cta(unsigned *cnt, unsigned total) {
-    __shared__ bool s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned t = atomicAdd(cnt, 1u);
-        s_last = (t == total - 1);
-        if (s_last) *cnt = 0;  // reset for the next use; no other CTA touches it in this launch
+// sum_{i < n} src[i * stride] in i order (n <= 16 loads in flight at a time).
+__device__ __forceinline__ double2 ordered_sum(const double2 *src, int n, int64_t stride) {
+    double2 s = make_double2(0, 0);
+    int i = 0;
+    for (; i + 16 <= n; i += 16) {
+        double2 v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = __ldcg(src + (int64_t)(i + q) * stride);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) s = s + v[q];
     }
-    __syncthreads();
-    if (s_last) __threadfence();
-    return s_last;
+    if (i < n) {
+        double2 v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = (i + q < n) ? __ldcg(src + (int64_t)(i + q) * stride) : make_double2(0, 0);
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (i + q < n) s = s + v[q];
+    }
+    return s;
 }
 
-// In the last CTA: out[k] = sum_c part[c][k] for k < K.  The threads form G
-// groups of KP (K rounded up to a power of two, at most blockDim); thread
-// (g, kk) adds chunks g, g+G, g+2G, ... of column kb+kk in four independent
-// accumulators (so several loads are in flight), and the G group sums are then
-// added by a pairwise tree.  The order depends only on nchunk, K and blockDim,
-// never on timing or on the other RHS of the batch.
-__device__ void reduce_partials(const double2 *part, int nchunk, int pstride, int K, double2 *out) {
-    __shared__ double2 red2[256];
-    int KP = 1;
-    while (KP < K && KP < (int)blockDim.x) KP <<= 1;
-    const int G = blockDim.x / KP;
-    const int kk = threadIdx.x % KP, g = threadIdx.x / KP;
-    for (int kb = 0; kb < K; kb += KP) {
-        const int k = kb + kk;
-        double2 sa[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) sa[q] = make_double2(0, 0);
-        if (k < K) {
-            int c = g;
-            for (; c + 7 * G < nchunk; c += 8 * G) {  // 8 loads in flight
-                double2 av[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) av[q] = __ldcg(part + (int64_t)(c + q * G) * pstride + k);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) sa[q] = sa[q] + av[q];
-            }
-            for (; c < nchunk; c += G) sa[0] = sa[0] + __ldcg(part + (int64_t)c * pstride + k);
-        }
-        red2[threadIdx.x] = ((sa[0] + sa[1]) + (sa[2] + sa[3])) + ((sa[4] + sa[5]) + (sa[6] + sa[7]));
-        __syncthreads();
-        for (int h = G >> 1; h > 0; h >>= 1) {
-            if (g < h) red2[threadIdx.x] = red2[threadIdx.x] + red2[threadIdx.x + h * KP];
-            __syncthreads();
-        }
-        if (threadIdx.x < KP && kb + (int)threadIdx.x < K) out[kb + threadIdx.x] = red2[threadIdx.x];
-        __syncthreads();
-    }
+// Cross-CTA sum of one RHS's partial rows (chunk cx has written row cx,
+// columns 0..K-1).  The last CTA to finish in each group of kRedGroup chunks
+// adds the group's rows in chunk order into a group row; the last group to
+// finish adds the group rows in group order into tot[0..K) (shared memory).
+// Returns true in that one CTA (all threads).  The tickets are last-arriver
+// counters that reset themselves; nothing waits.  The order depends only on
+// nchunk and K.
+__device__ bool reduce_rows(const GArgs &a, int rr, int cx, int K, double2 *tot) {
+    __shared__ unsigned s_t;
+    double2 *rows = part_rows(a, rr);
+    unsigned *cnt = a.cnt + (int64_t)rr * a.cstride;
+    const int g = cx / kRedGroup, g0 = g * kRedGroup;
+    const int gs = min(kRedGroup, a.nchunk - g0);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_t = atomicAdd(cnt + g, 1u);
+    __syncthreads();
+    if (s_t != (unsigned)gs - 1) return false;
+    __threadfence();
+    if (threadIdx.x == 0) cnt[g] = 0u;  // no other CTA of this launch touches it again
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+        rows[(int64_t)(a.nchunk + g) * a.pstride + k] = ordered_sum(rows + (int64_t)g0 * a.pstride + k, gs, a.pstride);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_t = atomicAdd(cnt + a.ngroups, 1u);
+    __syncthreads();
+    if (s_t != (unsigned)a.ngroups - 1) return false;
+    __threadfence();
+    if (threadIdx.x == 0) cnt[a.ngroups] = 0u;
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+        tot[k] = ordered_sum(rows + (int64_t)a.nchunk * a.pstride + k, a.ngroups, a.pstride);
+    __syncthreads();
+    return true;
 }
 
 __device__ __forceinline__ double2 *basis(const GArgs &a, int k, int rr) {
     return a.Vb + ((int64_t)k * a.cap + rr) * a.N;
 }
 
+// acc - c * u with four fused multiply-adds
+__device__ __forceinline__ double2 cfms(double2 c, double2 u, double2 acc) {
+    acc.x = fma(-c.x, u.x, acc.x);
+    acc.x = fma(c.y, u.y, acc.x);
+    acc.y = fma(-c.x, u.y, acc.y);
+    acc.y = fma(-c.y, u.x, acc.y);
+    return acc;
+}
+
 // ---------------------------------------------------------------- norms
-template <int ELEM> __global__ void __launch_bounds__(256) k_vnorm(GArgs a) {
+template <int ELEM> __global__ void __launch_bounds__(256) k_vnorm(const __grid_constant__ GroupArgs g) {
     __shared__ double red[8];
     __shared__ double2 tot[1];
-    const int rr = blockIdx.y;
-    const int64_t base = (int64_t)blockIdx.x * blockDim.x * ELEM;
+    const Loc L = locate(g, false);
+    if (L.mi < 0) return;
+    const GArgs &a = g.m[L.mi];
+    const int rr = L.rr;
     double acc = 0;
 #pragma unroll
     for (int e = 0; e < ELEM; ++e) {
-        const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
-        if (idx < a.N) acc += cabs2(a.v[(int64_t)rr * a.N + idx]);
+        const int64_t idx = elem_index(a, L.cx, e);
+        if (idx >= 0) acc += cabs2(a.v[(int64_t)rr * a.N + idx]);
     }
     acc = block_sum1(acc, red);
-    double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * a.pstride] = make_double2(acc, 0);
-    if (last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk)) {
-        reduce_partials(part, a.nchunk, a.pstride, 1, tot);
-        if (threadIdx.x == 0) a.nrm[rr * NM_STRIDE + NM_VNORM] = sqrt(tot[0].x);
-    }
+    if (threadIdx.x == 0) part_rows(a, rr)[(int64_t)L.cx * a.pstride] = make_double2(acc, 0);
+    if (reduce_rows(a, rr, L.cx, 1, tot) && threadIdx.x == 0) a.nrm[rr * NM_STRIDE + NM_VNORM] = sqrt(tot[0].x);
 }
 
 // u_0 = v - Z'x (w holds Z'x) or v (zero guess), its FP32 copy, ||u_0||, stop
 // test and the start of a cycle.
-template <int ELEM> __global__ void __launch_bounds__(256) k_residual(GArgs a, int first) {
+template <int ELEM> __global__ void __launch_bounds__(256) k_residual(const __grid_constant__ GroupArgs g, int first) {
     __shared__ double red[8];
     __shared__ double2 tot[1];
-    const int rr = blockIdx.y;
+    const Loc L = locate(g, false);
+    if (L.mi < 0) return;
+    const GArgs &a = g.m[L.mi];
+    const int rr = L.rr;
     int *st = a.st + rr * ST_STRIDE;
     if (st[ST_STATUS] != RS_RUNNING) return;
     const int zero = first && a.ctl->zero;
-    const int64_t base = (int64_t)blockIdx.x * blockDim.x * ELEM;
     double2 *u0 = basis(a, 0, rr);
     double acc = 0;
 #pragma unroll
     for (int e = 0; e < ELEM; ++e) {
-        const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
-        if (idx < a.N) {
+        const int64_t idx = elem_index(a, L.cx, e);
+        if (idx >= 0) {
             const int64_t o = (int64_t)rr * a.N + idx;
             const double2 t = zero ? a.v[o] : a.v[o] - a.w[o];
             u0[idx] = t;
@@ -260,10 +310,8 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_residual(GArgs a, i
         }
     }
     acc = block_sum1(acc, red);
-    double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * a.pstride] = make_double2(acc, 0);
-    if (!last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk)) return;
-    reduce_partials(part, a.nchunk, a.pstride, 1, tot);
+    if (threadIdx.x == 0) part_rows(a, rr)[(int64_t)L.cx * a.pstride] = make_double2(acc, 0);
+    if (!reduce_rows(a, rr, L.cx, 1, tot)) return;
     if (threadIdx.x != 0) return;
     double *nm = a.nrm + rr * NM_STRIDE;
     const double vn = nm[NM_VNORM], rn = sqrt(tot[0].x);
@@ -288,9 +336,9 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_residual(GArgs a, i
         a.beta[(int64_t)rr * (a.m + 1)] = rn;
         const double floor_abs = 0.5 * a.ctl->tol * vn;
         nm[NM_TARGET] = a.mixed ? fmax(a.ctl->inner_tol * rn, floor_abs) : floor_abs;
-        double2 *g = a.g + (int64_t)rr * (a.m + 1);
-        g[0] = make_double2(rn, 0);
-        for (int i = 1; i <= a.m; ++i) g[i] = make_double2(0, 0);
+        double2 *gg = a.g + (int64_t)rr * (a.m + 1);
+        gg[0] = make_double2(rn, 0);
+        for (int i = 1; i <= a.m; ++i) gg[i] = make_double2(0, 0);
     }
 }
 
@@ -365,7 +413,6 @@ __device__ void column_decision(const GArgs &a, int rr, int j, double2 *hs) {
         const double wn2 = w2 - hsq;
         const int again = !(wn2 > kReorthEta * kReorthEta * w2);
         st[ST_REORTH] = again;
-        if (again && a.graph) cudaGraphSetConditional(a.h_reorth, 1u);
         s_wn2 = wn2;
         s_again = again;
     }
@@ -374,10 +421,13 @@ __device__ void column_decision(const GArgs &a, int rr, int j, double2 *hs) {
 }
 
 // Partial dot products <u_k, w> for k in [k0, k0+8) (k <= j) plus, when
-// with_norm and k0 + kk == j + 1, ||w||^2 in that slot; CTA totals -> part.
+// with_norm and k0 + kk == j + 1, ||w||^2 in that slot: per-thread sums,
+// then one warp reduce-scatter; the warp's 8 totals go to wred[warp][k0..].
+// No block barrier here: the warps are added once after all groups.
 template <int ELEM>
-__device__ __forceinline__ void dots_group(const GArgs &a, int rr, int j, int k0, bool with_norm,
-                                           const double2 (&wv)[ELEM], int64_t base, double2 *part, double2 *red) {
+__device__ __forceinline__ void dots_group(const GArgs &a, int rr, int j, int k0, int K, bool with_norm,
+                                           const double2 (&wv)[ELEM], const int64_t (&ix)[ELEM],
+                                           double2 (*wred)[kMaxK]) {
     double2 acc[8];
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) acc[kk] = make_double2(0, 0);
@@ -386,11 +436,10 @@ __device__ __forceinline__ void dots_group(const GArgs &a, int rr, int j, int k0
         const int64_t vstride = (int64_t)a.cap * a.N;
 #pragma unroll
         for (int e = 0; e < ELEM; ++e) {
-            const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
-            if (idx < a.N) {
+            if (ix[e] >= 0) {
                 double2 uv[8];
 #pragma unroll
-                for (int kk = 0; kk < 8; ++kk) uv[kk] = u0[kk * vstride + idx];
+                for (int kk = 0; kk < 8; ++kk) uv[kk] = u0[kk * vstride + ix[e]];
 #pragma unroll
                 for (int kk = 0; kk < 8; ++kk) acc[kk] = cfmac(uv[kk], wv[e], acc[kk]);
             }
@@ -402,57 +451,52 @@ __device__ __forceinline__ void dots_group(const GArgs &a, int rr, int j, int k0
             if (k <= j) {
                 const double2 *uk = basis(a, k, rr);
 #pragma unroll
-                for (int e = 0; e < ELEM; ++e) {
-                    const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
-                    if (idx < a.N) acc[kk] = cfmac(uk[idx], wv[e], acc[kk]);
-                }
+                for (int e = 0; e < ELEM; ++e)
+                    if (ix[e] >= 0) acc[kk] = cfmac(uk[ix[e]], wv[e], acc[kk]);
             } else if (with_norm && k == j + 1) {
 #pragma unroll
                 for (int e = 0; e < ELEM; ++e) acc[kk].x += cabs2(wv[e]);
             }
         }
     }
-    block_sum8(acc, red);
-    const int K = j + 1 + (with_norm ? 1 : 0);
-    if (threadIdx.x < 8 && k0 + (int)threadIdx.x < K)
-        part[(int64_t)blockIdx.x * a.pstride + k0 + threadIdx.x] = red[threadIdx.x];
-    __syncthreads();
-}
-
-// Lowest RHS index that asked for a second Gram-Schmidt pass (-1 if none).
-__device__ __forceinline__ int first_reorth_rhs(const GArgs &a) {
-    for (int rr = 0; rr < a.nrhs; ++rr)
-        if (a.st[rr * ST_STRIDE + ST_ACTIVE] && a.st[rr * ST_STRIDE + ST_REORTH]) return rr;
-    return -1;
+    warp_rs8(acc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if ((lane & 3) == 0) {
+        const int kk = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        if (k0 + kk < K) wred[warp][k0 + kk] = acc[0];
+    }
 }
 
 // Gram-Schmidt dots.
 // PASS 1: w = (product of u_j) / beta_j is formed (from the FP32 or FP64
-//   product) and stored as u_{j+1}; per-CTA partial sums of <v_k, w> and ||w||^2.
-//   With a.redund every CTA of the update kernel reduces them (no serial tail
-//   on the path); else the last CTA per RHS reduces them, takes the second-pass
-//   decision and finalises the column (column_decision).
-// PASS 2 (flagged RHS only): h2_k = <v_k, u_{j+1}> (last CTA reduces).
-template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(GArgs a) {
-    __shared__ double2 red[64];
-    __shared__ double2 tot[130];
-    const int rr = blockIdx.y;
-    int *st = a.st + rr * ST_STRIDE;
+//   product) and stored as u_{j+1}; the CTA's sums of <u_k, w> (k <= j) and
+//   ||w||^2 are reduced across the RHS's chunks; the last CTA stores
+//   h1_k = <v_k, w> and h1_{j+1} = ||w||^2.
+// PASS 2 (flagged RHS only): h2_k = <v_k, u_{j+1}>.
+template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(const __grid_constant__ GroupArgs g) {
+    __shared__ double2 wred[8][kMaxK];
+    __shared__ double2 tot[kMaxK];
+    const Loc L = locate(g, false);
+    if (L.mi < 0) return;
+    const GArgs &a = g.m[L.mi];
+    const int rr = L.rr;
+    const int *st = a.st + rr * ST_STRIDE;
     if (!st[ST_ACTIVE]) return;
     if (PASS == 2 && !st[ST_REORTH]) return;
     const int j = a.ctl->j;
-    const int64_t base = (int64_t)blockIdx.x * blockDim.x * ELEM;
+    if (j >= a.m) return;
     const double *beta = a.beta + (int64_t)rr * (a.m + 1);
     double2 *un = basis(a, j + 1, rr);
     double2 wv[ELEM];
+    int64_t ix[ELEM];
     const double sc = 1.0 / beta[j];
 #pragma unroll
     for (int e = 0; e < ELEM; ++e) {
-        const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
+        ix[e] = elem_index(a, L.cx, e);
         wv[e] = make_double2(0, 0);
-        if (idx < a.N) {
+        if (ix[e] >= 0) {
             if (PASS == 1) {
-                const int64_t o = (int64_t)rr * a.N + idx;
+                const int64_t o = (int64_t)rr * a.N + ix[e];
                 double2 t;
                 if (a.mixed) {
                     const float2 f = a.y32[o];
@@ -461,128 +505,205 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(GArg
                     t = a.w[o];
                 }
                 wv[e] = cscale(t, sc);
-                un[idx] = wv[e];
+                un[ix[e]] = wv[e];
             } else {
-                wv[e] = un[idx];
+                wv[e] = un[ix[e]];
             }
         }
     }
-    if (PASS == 2 && blockIdx.x == 0 && threadIdx.x == 0 && rr == first_reorth_rhs(a)) a.ctl->reorth_bodies += 1;
     const int K = j + 1 + (PASS == 1 ? 1 : 0);
-    double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
-    for (int k0 = 0; k0 < K; k0 += 8) dots_group<ELEM>(a, rr, j, k0, PASS == 1, wv, base, part, red);
-    if (PASS == 1 && a.redund) return;  // the update kernel reduces these partial sums
-    if (!last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk)) return;
-    reduce_partials(part, a.nchunk, a.pstride, K, tot);
-    double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
-    for (int k = threadIdx.x; k <= j; k += blockDim.x) {
-        const double2 hk = cscale(tot[k], 1.0 / beta[k]);
-        h[k] = hk;
-        tot[k] = hk;
-    }
+    for (int k0 = 0; k0 < K; k0 += 8) dots_group<ELEM>(a, rr, j, k0, K, PASS == 1, wv, ix, wred);
     __syncthreads();
-    if (PASS == 2) return;
-    column_decision(a, rr, j, tot);
+    double2 *row = part_rows(a, rr) + (int64_t)L.cx * a.pstride;
+    const int nw = blockDim.x >> 5;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        double2 s = wred[0][k];
+        for (int w = 1; w < nw; ++w) s = s + wred[w][k];
+        row[k] = s;
+    }
+    if (!reduce_rows(a, rr, L.cx, K, tot)) return;
+    double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) h[k] = cscale(tot[k], 1.0 / beta[k]);
+    if (PASS == 1 && threadIdx.x == 0) h[j + 1] = tot[j + 1];  // ||w||^2 in .x
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool past_deadline(const SolveCtl *c) {
+    return c->deadline != 0ull && globaltimer_ns() > c->deadline;
+}
+
+// Some RHS of some member with flag f set (whole CTA).
+__device__ __forceinline__ bool any_flag(const GroupArgs &g, int f, int f2 = -1) {
+    int any = 0;
+    for (int i = 0; i < g.n; ++i)
+        for (int rr = threadIdx.x; rr < g.m[i].nrhs; rr += blockDim.x) {
+            const int *st = g.m[i].st + rr * ST_STRIDE;
+            any |= st[f] && (f2 < 0 || st[f2]);
+        }
+    return __syncthreads_or(any) != 0;
+}
+
+// End of an Arnoldi step (one CTA): cycles that ended in this step close
+// (ACTIVE -> 0, PENDING -> 1), then the next iteration runs while some RHS is
+// still in its cycle; members with no RHS in a cycle skip their next product.
+__device__ void iteration_control(const GroupArgs &g) {
+    for (int i = 0; i < g.n; ++i)
+        for (int rr = threadIdx.x; rr < g.m[i].nrhs; rr += blockDim.x) {
+            int *st = g.m[i].st + rr * ST_STRIDE;
+            if (st[ST_END]) {
+                st[ST_END] = 0;
+                st[ST_ACTIVE] = 0;
+                st[ST_PENDING] = 1;
+            }
+        }
+    __syncthreads();
+    const bool any = any_flag(g, ST_ACTIVE);
+    unsigned member_on[kMaxMembers];
+    if (g.prod_if)
+        for (int i = 0; i < g.n; ++i) {
+            int on = 0;
+            for (int rr = threadIdx.x; rr < g.m[i].nrhs; rr += blockDim.x) on |= g.m[i].st[rr * ST_STRIDE + ST_ACTIVE];
+            member_on[i] = __syncthreads_or(on) ? 1u : 0u;
+        }
+    if (threadIdx.x != 0) return;
+    SolveCtl *c = g.m[0].ctl;
+    c->j += 1;
+    c->inner_bodies += 1;
+    c->reorth_pending = 0;
+    const bool late = past_deadline(c);
+    if (any && late) c->timed_out = 1;
+    const unsigned cond = (any && c->j < g.m[0].m && !late) ? 1u : 0u;
+    c->cond_iter = (int)cond;
+    if (g.graph) {
+        cudaGraphSetConditional(g.h_iter, cond);
+        cudaGraphSetConditional(g.h_reorth, 0u);
+        // next iteration's products: the members still in a cycle; when the
+        // loop ends, all on again for the next cycle's first step
+        if (g.prod_if)
+            for (int i = 0; i < g.n; ++i) cudaGraphSetConditional(g.h_prod[i], cond ? member_on[i] : 1u);
+    }
 }
 
 // u_{j+1} <- u_{j+1} - sum_k (h_k / beta_k) u_k and its copy for the next
-// product.  PASS 1 with a.redund: every CTA first reduces the dots' partial
-// sums (same order everywhere, so the same h as the last-CTA reduction); one
-// extra CTA (blockIdx.x == nchunk) takes the second-pass decision and, without
-// one, finalises the Hessenberg column, alongside the update.  PASS 2 (after a
-// second Gram-Schmidt pass) also forms ||u_{j+1}|| and finalises the column.
-template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(GArgs a) {
+// product, from the h the dots kernel stored.
+// PASS 1: one extra CTA per RHS (cx == nchunk) takes the second-pass
+//   decision and, without one, finalises the Hessenberg column, alongside the
+//   update; the last CTA of the whole grid then runs the iteration control
+//   (or, when some RHS asked for a second pass, leaves it to that pass).
+// PASS 2 (after a second Gram-Schmidt pass): also forms ||u_{j+1}|| across
+//   the chunks and finalises the column with h1 + h2.
+template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(const __grid_constant__ GroupArgs g) {
     __shared__ double red[8];
-    __shared__ double2 cf[129];
-    __shared__ double2 tot[130];
-    const int rr = blockIdx.y;
-    int *st = a.st + rr * ST_STRIDE;
-    if (!st[ST_ACTIVE]) return;
-    if (PASS == 2 && !st[ST_REORTH]) return;
-    const int j = a.ctl->j;
-    const double *beta = a.beta + (int64_t)rr * (a.m + 1);
-    if (PASS == 1 && a.redund) {
-        // every CTA reduces the dots' partial sums in the same fixed order:
-        // tot[k] = <u_k, w> (k <= j), tot[j+1].x = ||w||^2
-        reduce_partials(a.part + (int64_t)rr * a.nchunk * a.pstride, a.nchunk, a.pstride, j + 2, tot);
-        for (int k = threadIdx.x; k <= j; k += blockDim.x) {
-            const double2 hk = cscale(tot[k], 1.0 / beta[k]);  // h_k = <v_k, w>
-            cf[k] = cscale(hk, 1.0 / beta[k]);
-            tot[k] = hk;
-        }
-        __syncthreads();
-        if (blockIdx.x == a.nchunk) {  // one extra CTA: the step decision and Hessenberg column
-            double2 *h1 = a.h1 + (int64_t)rr * (a.m + 1);
-            for (int k = threadIdx.x; k <= j; k += blockDim.x) h1[k] = tot[k];
-            column_decision(a, rr, j, tot);
-            return;
-        }
-    } else {  // h from the dots' last CTA
-        const double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
-        for (int k = threadIdx.x; k <= j; k += blockDim.x) cf[k] = cscale(__ldcg(h + k), 1.0 / beta[k]);
-        __syncthreads();
-    }
-    const int64_t base = (int64_t)blockIdx.x * blockDim.x * ELEM;
-    double2 *un = basis(a, j + 1, rr);
-    double2 wv[ELEM];
+    __shared__ double2 cf[kMaxK];
+    __shared__ double2 tot[kMaxK];
+    __shared__ unsigned s_t;
+    const Loc L = locate(g, PASS == 1);
+    if (L.mi >= 0) {
+        const GArgs &a = g.m[L.mi];
+        const int rr = L.rr;
+        int *st = a.st + rr * ST_STRIDE;
+        const int j = a.ctl->j;
+        const bool work = st[ST_ACTIVE] && (PASS == 1 || st[ST_REORTH]) && j < a.m;
+        if (work) {
+            const double *beta = a.beta + (int64_t)rr * (a.m + 1);
+            const double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
+            for (int k = threadIdx.x; k <= j; k += blockDim.x) {
+                const double2 hk = __ldcg(h + k);
+                cf[k] = cscale(hk, 1.0 / beta[k]);
+                tot[k] = hk;
+            }
+            if (PASS == 1 && threadIdx.x == 0) tot[j + 1] = __ldcg(h + j + 1);
+            __syncthreads();
+            if (PASS == 1 && L.cx == a.nchunk) {
+                column_decision(a, rr, j, tot);
+            } else {
+                double2 *un = basis(a, j + 1, rr);
+                double2 wv[ELEM];
+                int64_t ix[ELEM];
 #pragma unroll
-    for (int e = 0; e < ELEM; ++e) {
-        const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
-        wv[e] = idx < a.N ? un[idx] : make_double2(0, 0);
-    }
-    int k = 0;
-    const int64_t vstride = (int64_t)a.cap * a.N;
-    constexpr int UNR = ELEM == 1 ? 8 : 4;  // basis vectors per step, loads first
-    for (; k + UNR <= j + 1; k += UNR) {
-        const double2 *u0 = basis(a, k, rr);
+                for (int e = 0; e < ELEM; ++e) {
+                    ix[e] = elem_index(a, L.cx, e);
+                    wv[e] = ix[e] >= 0 ? un[ix[e]] : make_double2(0, 0);
+                }
+                int k = 0;
+                const int64_t vstride = (int64_t)a.cap * a.N;
+                constexpr int UNR = ELEM == 1 ? 8 : 4;  // basis vectors per step, loads first
+                for (; k + UNR <= j + 1; k += UNR) {
+                    const double2 *u0 = basis(a, k, rr);
 #pragma unroll
-        for (int e = 0; e < ELEM; ++e) {
-            const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
-            if (idx < a.N) {
-                double2 uv[UNR];
+                    for (int e = 0; e < ELEM; ++e) {
+                        if (ix[e] >= 0) {
+                            double2 uv[UNR];
 #pragma unroll
-                for (int kk = 0; kk < UNR; ++kk) uv[kk] = u0[kk * vstride + idx];
+                            for (int kk = 0; kk < UNR; ++kk) uv[kk] = u0[kk * vstride + ix[e]];
 #pragma unroll
-                for (int kk = 0; kk < UNR; ++kk) wv[e] = wv[e] - cmul(cf[k + kk], uv[kk]);
+                            for (int kk = 0; kk < UNR; ++kk) wv[e] = cfms(cf[k + kk], uv[kk], wv[e]);
+                        }
+                    }
+                }
+                for (; k <= j; ++k) {
+                    const double2 c = cf[k];
+                    const double2 *uk = basis(a, k, rr);
+#pragma unroll
+                    for (int e = 0; e < ELEM; ++e)
+                        if (ix[e] >= 0) wv[e] = cfms(c, uk[ix[e]], wv[e]);
+                }
+                double acc = 0;
+#pragma unroll
+                for (int e = 0; e < ELEM; ++e) {
+                    if (ix[e] >= 0) {
+                        un[ix[e]] = wv[e];
+                        if (a.mixed)
+                            a.x32[(int64_t)rr * a.N + ix[e]] = make_float2((float)wv[e].x, (float)wv[e].y);
+                        else
+                            a.xin64[(int64_t)rr * a.N + ix[e]] = wv[e];
+                        acc += cabs2(wv[e]);
+                    }
+                }
+                if (PASS == 2) {
+                    acc = block_sum1(acc, red);
+                    if (threadIdx.x == 0) part_rows(a, rr)[(int64_t)L.cx * a.pstride] = make_double2(acc, 0);
+                    if (reduce_rows(a, rr, L.cx, 1, tot)) {
+                        const double wn = sqrt(tot[0].x);
+                        const double2 *h1 = a.h1 + (int64_t)rr * (a.m + 1);
+                        const double2 *h2 = a.h2 + (int64_t)rr * (a.m + 1);
+                        for (int kk = threadIdx.x; kk <= j; kk += blockDim.x) cf[kk] = __ldcg(h1 + kk) + __ldcg(h2 + kk);
+                        if (threadIdx.x == 0) st[ST_REORTH] = 0;
+                        __syncthreads();
+                        finalize_column(a, rr, j, cf, wn);
+                    }
+                }
             }
         }
     }
-    for (; k <= j; ++k) {
-        const double2 c = cf[k];
-        const double2 *uk = basis(a, k, rr);
-#pragma unroll
-        for (int e = 0; e < ELEM; ++e) {
-            const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
-            if (idx < a.N) wv[e] = wv[e] - cmul(c, uk[idx]);
-        }
-    }
-    double acc = 0;
-#pragma unroll
-    for (int e = 0; e < ELEM; ++e) {
-        const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
-        if (idx < a.N) {
-            un[idx] = wv[e];
-            if (a.mixed)
-                a.x32[(int64_t)rr * a.N + idx] = make_float2((float)wv[e].x, (float)wv[e].y);
-            else
-                a.xin64[(int64_t)rr * a.N + idx] = wv[e];
-            acc += cabs2(wv[e]);
-        }
-    }
-    if (PASS == 1) return;
-    acc = block_sum1(acc, red);
-    double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * a.pstride] = make_double2(acc, 0);
-    if (!last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk)) return;
-    reduce_partials(part, a.nchunk, a.pstride, 1, tot);
-    const double wn = sqrt(tot[0].x);
-    const double2 *h1 = a.h1 + (int64_t)rr * (a.m + 1);
-    const double2 *h2 = a.h2 + (int64_t)rr * (a.m + 1);
-    for (int kk = threadIdx.x; kk <= j; kk += blockDim.x) cf[kk] = __ldcg(h1 + kk) + __ldcg(h2 + kk);  // totals
-    if (threadIdx.x == 0) st[ST_REORTH] = 0;
+    if (PASS != 1) return;
+    // the last CTA of the grid: iteration control, unless a second pass is due
+    SolveCtl *c = g.m[0].ctl;
+    __threadfence();
     __syncthreads();
-    finalize_column(a, rr, j, cf, wn);
+    if (threadIdx.x == 0) s_t = atomicAdd(&c->tick, 1u);
+    __syncthreads();
+    if (s_t != gridDim.x - 1) return;
+    __threadfence();
+    if (threadIdx.x == 0) c->tick = 0u;
+    if (any_flag(g, ST_ACTIVE, ST_REORTH)) {
+        if (threadIdx.x == 0) {
+            c->reorth_pending = 1;
+            c->reorth_bodies += 1;
+            if (g.graph) cudaGraphSetConditional(g.h_reorth, 1u);
+        }
+        return;
+    }
+    iteration_control(g);
 }
+
+// After a second Gram-Schmidt pass: the step's iteration control.
+__global__ void k_iter_ctl(const __grid_constant__ GroupArgs g) { iteration_control(g); }
 
 // Least squares of a finished cycle: R y = g with R the leading jl x jl
 // upper triangle of the rotated Hessenberg matrix; ys[k] = y_k / beta_k.
@@ -631,18 +752,20 @@ __device__ void cycle_least_squares(const GArgs &a, int rr, int jl, double2 *ys)
 }
 
 // d <- d + sum_k (y_k / beta_k) u_k for RHS whose cycle produced an update.
-template <int ELEM> __global__ void __launch_bounds__(256) k_update_d(GArgs a) {
+template <int ELEM> __global__ void __launch_bounds__(256) k_update_d(const __grid_constant__ GroupArgs g) {
     __shared__ double2 ys[128];
-    const int rr = blockIdx.y;
+    const Loc L = locate(g, false);
+    if (L.mi < 0) return;
+    const GArgs &a = g.m[L.mi];
+    const int rr = L.rr;
     const int *st = a.st + rr * ST_STRIDE;
     if (!st[ST_PENDING]) return;
     const int jl = st[ST_JLEN];
     cycle_least_squares(a, rr, jl, ys);
-    const int64_t base = (int64_t)blockIdx.x * blockDim.x * ELEM;
 #pragma unroll
     for (int e = 0; e < ELEM; ++e) {
-        const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
-        if (idx < a.N) {
+        const int64_t idx = elem_index(a, L.cx, e);
+        if (idx >= 0) {
             const int64_t o = (int64_t)rr * a.N + idx;
             double2 s = a.dbuf[o];
             for (int k = 0; k < jl; ++k) s = cfma(ys[k], basis(a, k, rr)[idx], s);
@@ -653,14 +776,16 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_update_d(GArgs a) {
 }
 
 // x <- x + d at the end of a sweep.
-template <int ELEM> __global__ void __launch_bounds__(256) k_apply_d(GArgs a) {
-    const int rr = blockIdx.y;
+template <int ELEM> __global__ void __launch_bounds__(256) k_apply_d(const __grid_constant__ GroupArgs g) {
+    const Loc L = locate(g, false);
+    if (L.mi < 0) return;
+    const GArgs &a = g.m[L.mi];
+    const int rr = L.rr;
     if (!a.st[rr * ST_STRIDE + ST_INNER]) return;
-    const int64_t base = (int64_t)blockIdx.x * blockDim.x * ELEM;
 #pragma unroll
     for (int e = 0; e < ELEM; ++e) {
-        const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
-        if (idx < a.N) {
+        const int64_t idx = elem_index(a, L.cx, e);
+        if (idx >= 0) {
             const int64_t o = (int64_t)rr * a.N + idx;
             a.x[o] = a.x[o] + a.dbuf[o];
         }
@@ -670,19 +795,21 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_apply_d(GArgs a) {
 // Inner restart (MIXED): r_in = r - Z32 d with the FP32 product of d in y32;
 // r_in becomes u_0 of a new cycle unless the inner target is met, the restart
 // gained less than 10%, or a cap is reached.
-template <int ELEM> __global__ void __launch_bounds__(256) k_inner_residual(GArgs a) {
+template <int ELEM> __global__ void __launch_bounds__(256) k_inner_residual(const __grid_constant__ GroupArgs g) {
     __shared__ double red[8];
     __shared__ double2 tot[1];
-    const int rr = blockIdx.y;
+    const Loc L = locate(g, false);
+    if (L.mi < 0) return;
+    const GArgs &a = g.m[L.mi];
+    const int rr = L.rr;
     int *st = a.st + rr * ST_STRIDE;
     if (!st[ST_INNER] || !st[ST_PENDING]) return;
-    const int64_t base = (int64_t)blockIdx.x * blockDim.x * ELEM;
     double2 *u0 = basis(a, 0, rr);
     double acc = 0;
 #pragma unroll
     for (int e = 0; e < ELEM; ++e) {
-        const int64_t idx = base + (int64_t)e * blockDim.x + threadIdx.x;
-        if (idx < a.N) {
+        const int64_t idx = elem_index(a, L.cx, e);
+        if (idx >= 0) {
             const int64_t o = (int64_t)rr * a.N + idx;
             const float2 f = a.y32[o];
             const double2 t = a.rbuf[o] - make_double2(f.x, f.y);
@@ -692,10 +819,8 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_inner_residual(GArg
         }
     }
     acc = block_sum1(acc, red);
-    double2 *part = a.part + (int64_t)rr * a.nchunk * a.pstride;
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * a.pstride] = make_double2(acc, 0);
-    if (!last_cta(a.cnt + rr * CNT_STRIDE, a.nchunk)) return;
-    reduce_partials(part, a.nchunk, a.pstride, 1, tot);
+    if (threadIdx.x == 0) part_rows(a, rr)[(int64_t)L.cx * a.pstride] = make_double2(acc, 0);
+    if (!reduce_rows(a, rr, L.cx, 1, tot)) return;
     if (threadIdx.x != 0) return;
     double *nm = a.nrm + rr * NM_STRIDE;
     const double rin = sqrt(tot[0].x), prev = nm[NM_RIN];
@@ -707,26 +832,24 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_inner_residual(GArg
     st[ST_RESTARTS] += 1;
     st[ST_ACTIVE] = 1;
     a.beta[(int64_t)rr * (a.m + 1)] = rin;
-    double2 *g = a.g + (int64_t)rr * (a.m + 1);
-    g[0] = make_double2(rin, 0);
-    for (int i = 1; i <= a.m; ++i) g[i] = make_double2(0, 0);
+    double2 *gg = a.g + (int64_t)rr * (a.m + 1);
+    gg[0] = make_double2(rin, 0);
+    for (int i = 1; i <= a.m; ++i) gg[i] = make_double2(0, 0);
 }
 
 // ---------------------------------------------------------------- loop control
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 // Start of a solve: counters, deadline, x = 0 for a zero guess, and whether the
 // first true residual needs a product (it does not when x = 0).
-__global__ void k_solve_begin(GArgs a, cudaGraphConditionalHandle h_first_product, int use_graph) {
-    SolveCtl *c = a.ctl;
-    const int64_t total = (int64_t)a.nrhs * a.N;
+__global__ void k_solve_begin(const __grid_constant__ GroupArgs g, cudaGraphConditionalHandle h_first) {
+    SolveCtl *c = g.m[0].ctl;
     if (c->zero)
-        for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x)
-            a.x[k] = make_double2(0, 0);
+        for (int i = 0; i < g.n; ++i) {
+            const GArgs &a = g.m[i];
+            const int64_t total = (int64_t)a.nrhs * a.N;
+            for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+                 k += (int64_t)gridDim.x * blockDim.x)
+                a.x[k] = make_double2(0, 0);
+        }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         c->j = 0;
         c->sweeps = 0;
@@ -734,89 +857,56 @@ __global__ void k_solve_begin(GArgs a, cudaGraphConditionalHandle h_first_produc
         c->outer_bodies = 0;
         c->restart_bodies = 0;
         c->inner_bodies = 0;
+        c->reorth_bodies = 0;
+        c->reorth_pending = 0;
+        c->tick = 0u;
         c->deadline = c->timeout_ns > 0 ? globaltimer_ns() + (unsigned long long)c->timeout_ns : 0ull;
         c->cond_first = c->zero ? 0 : 1;
-        if (use_graph) cudaGraphSetConditional(h_first_product, c->zero ? 0u : 1u);
+        if (g.graph) cudaGraphSetConditional(h_first, c->zero ? 0u : 1u);
     }
-}
-
-__device__ __forceinline__ bool any_active(const GArgs &a) {
-    int any = 0;
-    for (int rr = threadIdx.x; rr < a.nrhs; rr += blockDim.x) any |= a.st[rr * ST_STRIDE + ST_ACTIVE];
-    return __syncthreads_or(any) != 0;
-}
-
-__device__ __forceinline__ bool past_deadline(const SolveCtl *c) {
-    return c->deadline != 0ull && globaltimer_ns() > c->deadline;
 }
 
 // After a true residual: another sweep while some RHS is active, within the
 // sweep cap and the deadline.
-__global__ void k_sweep_ctl(GArgs a, cudaGraphConditionalHandle h_sweep, int use_graph) {
-    const bool any = any_active(a);
+__global__ void k_sweep_ctl(const __grid_constant__ GroupArgs g, cudaGraphConditionalHandle h_sweep) {
+    const bool any = any_flag(g, ST_ACTIVE);
     if (threadIdx.x != 0) return;
-    SolveCtl *c = a.ctl;
+    SolveCtl *c = g.m[0].ctl;
     c->sweeps += 1;
     const bool late = past_deadline(c);
     if (any && late) c->timed_out = 1;
     const unsigned cond = (any && c->sweeps < c->max_outer && !late) ? 1u : 0u;
     c->cond_sweep = (int)cond;
-    if (use_graph) cudaGraphSetConditional(h_sweep, cond);
+    if (g.graph) cudaGraphSetConditional(h_sweep, cond);
 }
 
-__global__ void k_restart_begin(GArgs a, cudaGraphConditionalHandle h_restart, int use_graph) {
+__global__ void k_restart_begin(const __grid_constant__ GroupArgs g, cudaGraphConditionalHandle h_restart) {
     if (threadIdx.x != 0) return;
-    a.ctl->outer_bodies += 1;
-    a.ctl->cond_restart = 1;
-    if (use_graph) cudaGraphSetConditional(h_restart, 1u);
+    SolveCtl *c = g.m[0].ctl;
+    c->outer_bodies += 1;
+    c->cond_restart = 1;
+    if (g.graph) cudaGraphSetConditional(h_restart, 1u);
 }
 
 // After a restart: another cycle while some RHS started one (MIXED only).
-__global__ void k_restart_ctl(GArgs a, cudaGraphConditionalHandle h_restart, int use_graph) {
-    const bool any = a.mixed && any_active(a);
+__global__ void k_restart_ctl(const __grid_constant__ GroupArgs g, cudaGraphConditionalHandle h_restart) {
+    const bool any = g.m[0].mixed && any_flag(g, ST_ACTIVE);
     if (threadIdx.x != 0) return;
-    SolveCtl *c = a.ctl;
+    SolveCtl *c = g.m[0].ctl;
     const bool late = past_deadline(c);
     if (any && late) c->timed_out = 1;
     const unsigned cond = (any && !late) ? 1u : 0u;
     c->cond_restart = (int)cond;
-    if (use_graph) cudaGraphSetConditional(h_restart, cond);
+    if (g.graph) cudaGraphSetConditional(h_restart, cond);
 }
 
-__global__ void k_cycle_begin(GArgs a, cudaGraphConditionalHandle h_iter, int use_graph) {
+__global__ void k_cycle_begin(const __grid_constant__ GroupArgs g) {
     if (threadIdx.x != 0) return;
-    a.ctl->j = 0;
-    a.ctl->restart_bodies += 1;
-    a.ctl->cond_iter = 1;
-    if (use_graph) cudaGraphSetConditional(h_iter, 1u);
-}
-
-// After an Arnoldi step: cycles that ended in this step close (ACTIVE -> 0,
-// PENDING -> 1), then the next iteration runs while some RHS is still in its
-// cycle.
-__global__ void k_iter_ctl(GArgs a, cudaGraphConditionalHandle h_iter, int use_graph) {
-    for (int rr = threadIdx.x; rr < a.nrhs; rr += blockDim.x) {
-        int *st = a.st + rr * ST_STRIDE;
-        if (st[ST_END]) {
-            st[ST_END] = 0;
-            st[ST_ACTIVE] = 0;
-            st[ST_PENDING] = 1;
-        }
-    }
-    __syncthreads();
-    const bool any = any_active(a);
-    if (threadIdx.x != 0) return;
-    SolveCtl *c = a.ctl;
-    c->j += 1;
-    c->inner_bodies += 1;
-    const bool late = past_deadline(c);
-    if (any && late) c->timed_out = 1;
-    const unsigned cond = (any && c->j < a.m && !late) ? 1u : 0u;
-    c->cond_iter = (int)cond;
-    if (use_graph) {
-        cudaGraphSetConditional(h_iter, cond);
-        cudaGraphSetConditional(a.h_reorth, 0u);
-    }
+    SolveCtl *c = g.m[0].ctl;
+    c->j = 0;
+    c->restart_bodies += 1;
+    c->cond_iter = 1;
+    if (g.graph) cudaGraphSetConditional(g.h_iter, 1u);
 }
 
 // ---------------------------------------------------------------- workspace
@@ -840,20 +930,23 @@ void free_solve_ws(ztoep_plan_t p) {
     w = SolveWs{};
 }
 
-// Launch geometry: depends on N only, so a RHS is summed in the same order
-// alone and in any batch.  Small systems: 128 threads x 1 element (enough
-// CTAs to cover every SM while keeping the partial sums of the cross-CTA
-// reductions few); large ones: 256 threads x 4 elements.
+// Chunks of a RHS: 256 threads x ELEM elements (ELEM = 4 for large systems),
+// and, once there are at least half as many chunks as SMs, their count
+// rounded up to a multiple of the SM count with the elements spread evenly,
+// so every SM gets the same FP64 work.  Depends on N (and the device) only,
+// so a RHS is summed in the same order alone, in any batch and in any group.
 struct Geom {
-    int threads, elem;
+    int threads, elem, per_cta, nchunk;
 };
 static Geom geom_for(int64_t N, int nsm) {
-    const int64_t ctas_small = (N + 255) / 256;
-    if (ctas_small >= 8LL * nsm) return {256, 4};
-    return {256, 1};
+    const int elem = (N + 255) / 256 >= 8LL * nsm ? 4 : 1;
+    const int64_t span = 256LL * elem;
+    int64_t nchunk = (N + span - 1) / span;
+    if (nchunk >= nsm / 2) nchunk = (nchunk + nsm - 1) / nsm * nsm;
+    const int64_t per = (N + nchunk - 1) / nchunk;
+    return {256, elem, (int)per, (int)((N + per - 1) / per)};
 }
 
-constexpr int kHostCtlInts = 32;  // host mirror of SolveCtl after st
 
 static ztoep_status_t ensure_solve_ws(ztoep_plan_t p, int nrhs, int m) {
     SolveWs &w = p->sws;
@@ -861,7 +954,8 @@ static ztoep_status_t ensure_solve_ws(ztoep_plan_t p, int nrhs, int m) {
     free_solve_ws(p);
     const int64_t N = p->N;
     const Geom gm = geom_for(N, p->nsm);
-    const int nchunk = (int)((N + gm.threads * gm.elem - 1) / (gm.threads * gm.elem));
+    const int ngroups = (gm.nchunk + kRedGroup - 1) / kRedGroup;
+    const int cstride = ngroups + 1;
     const int pstride = m + 2;
     const size_t vec = sizeof(double2) * (size_t)nrhs * N;
     size_t acc = 0;
@@ -879,73 +973,98 @@ static ztoep_status_t ensure_solve_ws(ztoep_plan_t p, int nrhs, int m) {
     ZT_TRY(dalloc((void **)&w.y, sizeof(double2) * (size_t)nrhs * m, &acc));
     ZT_TRY(dalloc((void **)&w.h1, sizeof(double2) * (size_t)nrhs * (m + 1), &acc));
     ZT_TRY(dalloc((void **)&w.h2, sizeof(double2) * (size_t)nrhs * (m + 1), &acc));
-    ZT_TRY(dalloc((void **)&w.part, sizeof(double2) * (size_t)nrhs * nchunk * pstride, &acc));
+    ZT_TRY(dalloc((void **)&w.part, sizeof(double2) * (size_t)nrhs * (gm.nchunk + ngroups) * pstride, &acc));
     ZT_TRY(dalloc((void **)&w.nrm, sizeof(double) * (size_t)nrhs * (NM_STRIDE + m + 1), &acc));
     ZT_TRY(dalloc((void **)&w.st, sizeof(int) * (size_t)nrhs * ST_STRIDE, &acc));
-    ZT_TRY(dalloc((void **)&w.cnt, sizeof(unsigned) * (size_t)nrhs * CNT_STRIDE, &acc));
+    ZT_TRY(dalloc((void **)&w.cnt, sizeof(unsigned) * (size_t)nrhs * cstride, &acc));
     ZT_TRY(dalloc((void **)&w.ctl, sizeof(SolveCtl), &acc));
-    ZT_CUDA(cudaMemset(w.cnt, 0, sizeof(unsigned) * (size_t)nrhs * CNT_STRIDE));
+    ZT_CUDA(cudaMemset(w.cnt, 0, sizeof(unsigned) * (size_t)nrhs * cstride));
     ZT_CUDA(cudaMallocHost((void **)&w.hst, sizeof(int) * (size_t)nrhs * ST_STRIDE + sizeof(SolveCtl) + 64));
     ZT_CUDA(cudaMallocHost((void **)&w.hnrm, sizeof(double) * (size_t)nrhs * NM_STRIDE));
     w.cap = nrhs;
     w.m = m;
+    w.cstride = cstride;
     w.bytes = acc;
     return ZTOEP_OK;
 }
 
-static GArgs make_args(ztoep_plan_t p, int nrhs, int m, bool mixed, int nchunk) {
+// One system of a solve: its plan and RHS count.
+struct Member {
+    ztoep_plan_t p;
+    int nrhs;
+};
+
+static GArgs make_args(ztoep_plan_t p, int nrhs, int m, bool mixed, SolveCtl *ctl) {
     SolveWs &w = p->sws;
+    const Geom gm = geom_for(p->N, p->nsm);
     GArgs a{};
     a.Vb = w.Vb; a.w = w.w; a.x = w.xbuf; a.v = w.vbuf; a.xin64 = w.xin64; a.rbuf = w.rbuf; a.dbuf = w.dbuf;
     a.x32 = (float2 *)p->ws32.xin; a.y32 = (const float2 *)p->ws32.yout;
-    a.H = w.H; a.cs = w.cs; a.sn = w.sn; a.g = w.g; a.y = w.y; a.h1 = w.h1; a.h2 = w.h2; a.part = w.part;
+    a.H = w.H; a.cs = w.cs; a.sn = w.sn; a.g = w.g; a.h1 = w.h1; a.h2 = w.h2; a.part = w.part;
     a.nrm = w.nrm; a.beta = w.nrm + (size_t)w.cap * NM_STRIDE; a.st = w.st; a.cnt = w.cnt;
-    a.ctl = (SolveCtl *)w.ctl;
-    a.N = p->N; a.cap = w.cap; a.m = m; a.nchunk = nchunk; a.pstride = w.m + 2; a.nrhs = nrhs;
-    // Redundant reduction of the pass-1 partials when its L2 traffic (every one
-    // of the nchunk update CTAs reads nchunk partial rows) stays small against
-    // the Arnoldi's own; else the dots' last CTA per RHS reduces once.
-    a.redund = (int64_t)nrhs * nchunk * nchunk <= (1 << 18) ? 1 : 0;
+    a.ctl = ctl;
+    a.N = p->N; a.cap = w.cap; a.m = m; a.nchunk = gm.nchunk; a.per_cta = gm.per_cta;
+    a.ngroups = (gm.nchunk + kRedGroup - 1) / kRedGroup; a.cstride = w.cstride; a.pstride = w.m + 2;
+    a.nrhs = nrhs;
     a.mixed = mixed ? 1 : 0;
     return a;
 }
 
+// The work list of a solve of `n` members (the first member's control block
+// is the group's).
+static GroupArgs make_group(const Member *mem, int n, int m, bool mixed) {
+    GroupArgs g{};
+    g.n = n;
+    SolveCtl *ctl = (SolveCtl *)mem[0].p->sws.ctl;
+    for (int i = 0; i < n; ++i) g.m[i] = make_args(mem[i].p, mem[i].nrhs, m, mixed, ctl);
+    return g;
+}
+
+static int group_elem(const Member *mem, int n) { return geom_for(mem[0].p->N, mem[0].p->nsm).elem; }
+
+static unsigned group_ctas(const GroupArgs &g, bool extra) {
+    unsigned t = 0;
+    for (int i = 0; i < g.n; ++i) t += (unsigned)(g.m[i].nchunk + (extra ? 1 : 0)) * g.m[i].nrhs;
+    return t;
+}
+
 template <int ELEM> struct Launch {
-    static ztoep_status_t vnorm(const GArgs &a, dim3 g, int t, cudaStream_t s) {
+    static ztoep_status_t vnorm(const GroupArgs &g, cudaStream_t s) {
         KScope ks(K_MISC, s);
-        k_vnorm<ELEM><<<g, t, 0, s>>>(a);
+        k_vnorm<ELEM><<<group_ctas(g, false), 256, 0, s>>>(g);
         return ok();
     }
-    static ztoep_status_t residual(const GArgs &a, dim3 g, int t, int first, cudaStream_t s) {
+    static ztoep_status_t residual(const GroupArgs &g, int first, cudaStream_t s) {
         KScope ks(K_MISC, s);
-        k_residual<ELEM><<<g, t, 0, s>>>(a, first);
+        k_residual<ELEM><<<group_ctas(g, false), 256, 0, s>>>(g, first);
         return ok();
     }
-    static ztoep_status_t arnoldi(const GArgs &a, dim3 g, int t, int pass, cudaStream_t s) {
+    static ztoep_status_t arnoldi(const GroupArgs &g, int pass, cudaStream_t s) {
         KScope ks(K_ARNOLDI, s);
-        ks.add(2);
+        ks.add(pass == 1 ? 2 : 3);
         if (pass == 1) {
-            k_dots<ELEM, 1><<<g, t, 0, s>>>(a);
-            k_upd<ELEM, 1><<<dim3(g.x + (a.redund ? 1 : 0), g.y), t, 0, s>>>(a);  // (+ the column CTA)
+            k_dots<ELEM, 1><<<group_ctas(g, false), 256, 0, s>>>(g);
+            k_upd<ELEM, 1><<<group_ctas(g, true), 256, 0, s>>>(g);  // (+ one decision CTA per RHS)
         } else {
-            k_dots<ELEM, 2><<<g, t, 0, s>>>(a);
-            k_upd<ELEM, 2><<<g, t, 0, s>>>(a);
+            k_dots<ELEM, 2><<<group_ctas(g, false), 256, 0, s>>>(g);
+            k_upd<ELEM, 2><<<group_ctas(g, false), 256, 0, s>>>(g);
+            k_iter_ctl<<<1, 256, 0, s>>>(g);
         }
         return ok();
     }
-    static ztoep_status_t update_d(const GArgs &a, dim3 g, int t, cudaStream_t s) {
+    static ztoep_status_t update_d(const GroupArgs &g, cudaStream_t s) {
         KScope ks(K_MISC, s);
-        k_update_d<ELEM><<<g, t, 0, s>>>(a);
+        k_update_d<ELEM><<<group_ctas(g, false), 256, 0, s>>>(g);
         return ok();
     }
-    static ztoep_status_t apply_d(const GArgs &a, dim3 g, int t, cudaStream_t s) {
+    static ztoep_status_t apply_d(const GroupArgs &g, cudaStream_t s) {
         KScope ks(K_MISC, s);
-        k_apply_d<ELEM><<<g, t, 0, s>>>(a);
+        k_apply_d<ELEM><<<group_ctas(g, false), 256, 0, s>>>(g);
         return ok();
     }
-    static ztoep_status_t inner_residual(const GArgs &a, dim3 g, int t, cudaStream_t s) {
+    static ztoep_status_t inner_residual(const GroupArgs &g, cudaStream_t s) {
         KScope ks(K_MISC, s);
-        k_inner_residual<ELEM><<<g, t, 0, s>>>(a);
+        k_inner_residual<ELEM><<<group_ctas(g, false), 256, 0, s>>>(g);
         return ok();
     }
     static ztoep_status_t ok() {
@@ -955,60 +1074,67 @@ template <int ELEM> struct Launch {
 };
 
 struct Ops {
-    Geom gm;
-    dim3 grid;
-    ztoep_status_t vnorm(const GArgs &a, cudaStream_t s) const {
-        return gm.elem == 4 ? Launch<4>::vnorm(a, grid, gm.threads, s) : Launch<1>::vnorm(a, grid, gm.threads, s);
+    int elem;
+    ztoep_status_t vnorm(const GroupArgs &g, cudaStream_t s) const {
+        return elem == 4 ? Launch<4>::vnorm(g, s) : Launch<1>::vnorm(g, s);
     }
-    ztoep_status_t residual(const GArgs &a, int first, cudaStream_t s) const {
-        return gm.elem == 4 ? Launch<4>::residual(a, grid, gm.threads, first, s)
-                            : Launch<1>::residual(a, grid, gm.threads, first, s);
+    ztoep_status_t residual(const GroupArgs &g, int first, cudaStream_t s) const {
+        return elem == 4 ? Launch<4>::residual(g, first, s) : Launch<1>::residual(g, first, s);
     }
-    ztoep_status_t arnoldi(const GArgs &a, int pass, cudaStream_t s) const {
-        return gm.elem == 4 ? Launch<4>::arnoldi(a, grid, gm.threads, pass, s)
-                            : Launch<1>::arnoldi(a, grid, gm.threads, pass, s);
+    ztoep_status_t arnoldi(const GroupArgs &g, int pass, cudaStream_t s) const {
+        return elem == 4 ? Launch<4>::arnoldi(g, pass, s) : Launch<1>::arnoldi(g, pass, s);
     }
-    ztoep_status_t update_d(const GArgs &a, cudaStream_t s) const {
-        return gm.elem == 4 ? Launch<4>::update_d(a, grid, gm.threads, s)
-                            : Launch<1>::update_d(a, grid, gm.threads, s);
+    ztoep_status_t update_d(const GroupArgs &g, cudaStream_t s) const {
+        return elem == 4 ? Launch<4>::update_d(g, s) : Launch<1>::update_d(g, s);
     }
-    ztoep_status_t apply_d(const GArgs &a, cudaStream_t s) const {
-        return gm.elem == 4 ? Launch<4>::apply_d(a, grid, gm.threads, s)
-                            : Launch<1>::apply_d(a, grid, gm.threads, s);
+    ztoep_status_t apply_d(const GroupArgs &g, cudaStream_t s) const {
+        return elem == 4 ? Launch<4>::apply_d(g, s) : Launch<1>::apply_d(g, s);
     }
-    ztoep_status_t inner_residual(const GArgs &a, cudaStream_t s) const {
-        return gm.elem == 4 ? Launch<4>::inner_residual(a, grid, gm.threads, s)
-                            : Launch<1>::inner_residual(a, grid, gm.threads, s);
+    ztoep_status_t inner_residual(const GroupArgs &g, cudaStream_t s) const {
+        return elem == 4 ? Launch<4>::inner_residual(g, s) : Launch<1>::inner_residual(g, s);
     }
 };
 
-static ztoep_status_t launch_small(void (*k)(GArgs, cudaGraphConditionalHandle, int), int blocks, const GArgs &a,
-                                   cudaGraphConditionalHandle h, cudaStream_t s, int use_graph = 1) {
+static ztoep_status_t launch_ctl(void (*k)(GroupArgs, cudaGraphConditionalHandle), int blocks, const GroupArgs &g,
+                                 cudaGraphConditionalHandle h, cudaStream_t s) {
     KScope ks(K_MISC, s);
-    k<<<blocks, 256, 0, s>>>(a, h, use_graph);
+    k<<<blocks, 256, 0, s>>>(g, h);
+    ZT_CUDA(cudaGetLastError());
+    return ZTOEP_OK;
+}
+static ztoep_status_t launch_ctl(void (*k)(GroupArgs), const GroupArgs &g, cudaStream_t s) {
+    KScope ks(K_MISC, s);
+    k<<<1, 256, 0, s>>>(g);
     ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
 }
 
-// Add a conditional node after the work captured so far on `s`; returns its body.
-static ztoep_status_t add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
-                                      cudaGraph_t *body) {
+// Add conditional nodes after the work captured so far on `s`, all on the
+// same dependencies (so they can run concurrently); returns their bodies.
+static ztoep_status_t add_conditionals(cudaStream_t s, const cudaGraphConditionalHandle *h, int n,
+                                       cudaGraphConditionalNodeType type, cudaGraph_t *bodies) {
     cudaStreamCaptureStatus cst;
     cudaGraph_t g = nullptr;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
     ZT_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, nullptr, &ndeps));
     if (cst != cudaStreamCaptureStatusActive) return ZTOEP_ERR_CUDA;
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = type;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    ZT_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
-    *body = cp.conditional.phGraph_out[0];
-    ZT_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    std::vector<cudaGraphNode_t> dep(deps, deps + ndeps), nodes(n);
+    for (int i = 0; i < n; ++i) {
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h[i];
+        cp.conditional.type = type;
+        cp.conditional.size = 1;
+        ZT_CUDA(cudaGraphAddNode(&nodes[i], g, dep.data(), nullptr, dep.size(), &cp));
+        bodies[i] = cp.conditional.phGraph_out[0];
+    }
+    ZT_CUDA(cudaStreamUpdateCaptureDependencies(s, nodes.data(), nullptr, n, cudaStreamSetCaptureDependencies));
     return ZTOEP_OK;
+}
+static ztoep_status_t add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                                      cudaGraph_t *body) {
+    return add_conditionals(s, &h, 1, type, body);
 }
 
 static ztoep_status_t capture_begin(cudaStream_t s, cudaGraph_t g, uint64_t *count) {
@@ -1023,47 +1149,101 @@ static ztoep_status_t capture_end(cudaStream_t s) {
     return ZTOEP_OK;
 }
 
+// Events of one graph capture (fork/join of the members' products).
+struct CaptureEvents {
+    std::vector<cudaEvent_t> ev;
+    ~CaptureEvents() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    ztoep_status_t make(cudaEvent_t *out) {
+        cudaEvent_t e = nullptr;
+        ZT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ev.push_back(e);
+        *out = e;
+        return ZTOEP_OK;
+    }
+};
+
+// Product of every member on its own buffers: FP32 (x32 -> y32) or FP64
+// (in64 -> w), the members concurrently (member 0 on `s`, the others on their
+// plans' capture streams, joined back to `s`).
+static ztoep_status_t member_products(const Member *mem, int n, bool fp32, bool xbuf_in, cudaStream_t s,
+                                      CaptureEvents &ce) {
+    auto one = [&](int i, cudaStream_t si) -> ztoep_status_t {
+        ztoep_plan_t p = mem[i].p;
+        if (fp32) return run_matvec<float>(p, mem[i].nrhs, (const float2 *)p->ws32.xin, (float2 *)p->ws32.yout, si);
+        return run_matvec<double>(p, mem[i].nrhs, xbuf_in ? p->sws.xbuf : p->sws.xin64, p->sws.w, si);
+    };
+    if (n == 1) return one(0, s);
+    cudaEvent_t fork = nullptr;
+    ZT_TRY(ce.make(&fork));
+    ZT_CUDA(cudaEventRecord(fork, s));
+    for (int i = 1; i < n; ++i) {
+        cudaStream_t si = mem[i].p->cap;
+        ZT_CUDA(cudaStreamWaitEvent(si, fork, 0));
+        ZT_TRY(one(i, si));
+        cudaEvent_t join = nullptr;
+        ZT_TRY(ce.make(&join));
+        ZT_CUDA(cudaEventRecord(join, si));
+        ZT_CUDA(cudaStreamWaitEvent(s, join, 0));
+    }
+    return one(0, s);
+}
+
 // Whole solve as one graph:
-//   begin -> IF(x != 0){FP64 product} -> residual -> sweep control ->
+//   begin -> IF(x != 0){FP64 products} -> residual -> sweep control ->
 //   WHILE(sweep){ restart begin ->
-//                 WHILE(restart){ cycle begin -> WHILE(iter){product, Arnoldi, iteration control}
-//                                 -> d += V y -> [MIXED: FP32 product of d, r_in = r - Z d]
+//                 WHILE(restart){ cycle begin -> WHILE(iter){products, Arnoldi (+ iteration control)}
+//                                 -> d += V y -> [MIXED: FP32 products of d, r_in = r - Z d]
 //                                 -> restart control }
-//                 -> x += d -> FP64 product -> residual -> sweep control }
-static ztoep_status_t build_graph(ztoep_plan_t p, SolveGraph &sg, int prec, int nrhs, int m) {
+//                 -> x += d -> FP64 products -> residual -> sweep control }
+// The Arnoldi step is k_dots + k_upd, whose last CTA runs the iteration
+// control; a RHS that asks for a second Gram-Schmidt pass makes it set the IF
+// node that runs k_dots<2>, k_upd<2> and the iteration control instead.  In a
+// group of several members, each member's iteration product sits in its own
+// IF node (members with no RHS in a cycle skip it) and the members' products
+// run concurrently; every other kernel is one launch for all members.
+static ztoep_status_t build_graph(const Member *mem, int n, SolveGraph &sg, int prec, int m) {
     const bool mixed = prec == ZTOEP_MIXED;
-    SolveWs &w = p->sws;
-    const Geom gm = geom_for(p->N, p->nsm);
-    const int per_cta = gm.threads * gm.elem;
-    const int nchunk = (int)((p->N + per_cta - 1) / per_cta);
-    GArgs a = make_args(p, nrhs, m, mixed, nchunk);
-    const Ops ops{gm, dim3(nchunk, nrhs)};
-    cudaStream_t s = p->cap;
+    GroupArgs g = make_group(mem, n, m, mixed);
+    const Ops ops{group_elem(mem, n)};
+    ztoep_plan_t p0 = mem[0].p;
+    cudaStream_t s = p0->cap;
+    CaptureEvents ce;
     cudaGraph_t top = nullptr;
     ZT_CUDA(cudaGraphCreate(&top, 0));
     sg.graph = top;
-    a.graph = 1;
-    cudaGraphConditionalHandle h_first, h_sweep, h_iter;
+    g.graph = 1;
+    g.prod_if = n > 1 ? 1 : 0;
+    cudaGraphConditionalHandle h_first, h_sweep;
     ZT_CUDA(cudaGraphConditionalHandleCreate(&h_first, top, 0, 0));
     ZT_CUDA(cudaGraphConditionalHandleCreate(&h_sweep, top, 0, 0));
     cudaGraph_t body_first = nullptr, body_sweep = nullptr, body_iter = nullptr;
 
-    // top level
+    // top level.  GroupArgs is copied into every launch when it is captured,
+    // so each loop handle is created before the first kernel that sets it is
+    // captured (k_cycle_begin: h_iter; k_upd<1> and k_iter_ctl: h_iter,
+    // h_reorth and the members' h_prod).
     ZT_TRY(capture_begin(s, top, &sg.k_fixed));
-    ZT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(int) * (size_t)w.cap * ST_STRIDE, s));
-    ZT_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(unsigned) * (size_t)w.cap * CNT_STRIDE, s));
-    const int zblocks = (int)std::min<int64_t>(4 * p->nsm, ((int64_t)nrhs * p->N + 255) / 256);
-    ZT_TRY(launch_small(k_solve_begin, std::max(1, zblocks), a, h_first, s));
-    ZT_TRY(ops.vnorm(a, s));
+    for (int i = 0; i < n; ++i) {
+        SolveWs &w = mem[i].p->sws;
+        ZT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(int) * (size_t)w.cap * ST_STRIDE, s));
+        ZT_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(unsigned) * (size_t)w.cap * w.cstride, s));
+    }
+    int64_t elems = 0;
+    for (int i = 0; i < n; ++i) elems += (int64_t)mem[i].nrhs * mem[i].p->N;
+    const int zblocks = (int)std::min<int64_t>(4 * p0->nsm, (elems + 255) / 256);
+    ZT_TRY(launch_ctl(k_solve_begin, std::max(1, zblocks), g, h_first, s));
+    ZT_TRY(ops.vnorm(g, s));
     ZT_TRY(add_conditional(s, h_first, cudaGraphCondTypeIf, &body_first));
-    ZT_TRY(ops.residual(a, 1, s));
-    ZT_TRY(launch_small(k_sweep_ctl, 1, a, h_sweep, s));
+    ZT_TRY(ops.residual(g, 1, s));
+    ZT_TRY(launch_ctl(k_sweep_ctl, 1, g, h_sweep, s));
     ZT_TRY(add_conditional(s, h_sweep, cudaGraphCondTypeWhile, &body_sweep));
     ZT_TRY(capture_end(s));
 
-    // first product (skipped for a zero guess)
+    // first products (skipped for a zero guess)
     ZT_TRY(capture_begin(s, body_first, &sg.k_first_product));
-    ZT_TRY(run_matvec<double>(p, nrhs, w.xbuf, w.w, s));
+    ZT_TRY(member_products(mem, n, false, true, s, ce));
     ZT_TRY(capture_end(s));
 
     // one sweep: inner restarts, x += d, FP64 residual
@@ -1071,51 +1251,88 @@ static ztoep_status_t build_graph(ztoep_plan_t p, SolveGraph &sg, int prec, int 
     cudaGraph_t body_restart = nullptr;
     ZT_CUDA(cudaGraphConditionalHandleCreate(&h_restart, body_sweep, 0, 0));
     ZT_TRY(capture_begin(s, body_sweep, &sg.k_sweep));
-    ZT_TRY(launch_small(k_restart_begin, 1, a, h_restart, s));
+    ZT_TRY(launch_ctl(k_restart_begin, 1, g, h_restart, s));
     ZT_TRY(add_conditional(s, h_restart, cudaGraphCondTypeWhile, &body_restart));
-    ZT_TRY(ops.apply_d(a, s));
-    ZT_TRY(run_matvec<double>(p, nrhs, w.xbuf, w.w, s));
-    ZT_TRY(ops.residual(a, 0, s));
-    ZT_TRY(launch_small(k_sweep_ctl, 1, a, h_sweep, s));
+    ZT_TRY(ops.apply_d(g, s));
+    ZT_TRY(member_products(mem, n, false, true, s, ce));
+    ZT_TRY(ops.residual(g, 0, s));
+    ZT_TRY(launch_ctl(k_sweep_ctl, 1, g, h_sweep, s));
     ZT_TRY(capture_end(s));
 
     // one restart: GMRES cycle, d += V y, FP32 inner residual (MIXED)
-    ZT_CUDA(cudaGraphConditionalHandleCreate(&h_iter, body_restart, 0, 0));
+    ZT_CUDA(cudaGraphConditionalHandleCreate(&g.h_iter, body_restart, 0, 0));
     ZT_TRY(capture_begin(s, body_restart, &sg.k_restart));
-    ZT_TRY(launch_small(k_cycle_begin, 1, a, h_iter, s));
-    ZT_TRY(add_conditional(s, h_iter, cudaGraphCondTypeWhile, &body_iter));
-    ZT_TRY(ops.update_d(a, s));
+    ZT_TRY(launch_ctl(k_cycle_begin, g, s));
+    ZT_TRY(add_conditional(s, g.h_iter, cudaGraphCondTypeWhile, &body_iter));
+    ZT_TRY(ops.update_d(g, s));
     if (mixed) {
-        ZT_TRY(run_matvec<float>(p, nrhs, a.x32, (float2 *)p->ws32.yout, s));
-        ZT_TRY(ops.inner_residual(a, s));
+        ZT_TRY(member_products(mem, n, true, false, s, ce));
+        ZT_TRY(ops.inner_residual(g, s));
     }
-    ZT_TRY(launch_small(k_restart_ctl, 1, a, h_restart, s));
+    ZT_TRY(launch_ctl(k_restart_ctl, 1, g, h_restart, s));
     ZT_TRY(capture_end(s));
 
     // one iteration; the second Gram-Schmidt pass only when a RHS asked for it
-    // (its condition starts at 0 and is reset by every iteration control)
+    // (its condition starts at 0 in every iteration)
     cudaGraph_t body_reorth = nullptr;
-    ZT_CUDA(cudaGraphConditionalHandleCreate(&a.h_reorth, body_iter, 0, cudaGraphCondAssignDefault));
+    ZT_CUDA(cudaGraphConditionalHandleCreate(&g.h_reorth, body_iter, 0, cudaGraphCondAssignDefault));
+    cudaGraph_t body_prod[kMaxMembers] = {};
+    if (g.prod_if)
+        for (int i = 0; i < n; ++i)
+            ZT_CUDA(cudaGraphConditionalHandleCreate(&g.h_prod[i], body_iter, 1, cudaGraphCondAssignDefault));
     ZT_TRY(capture_begin(s, body_iter, &sg.k_iter));
-    if (mixed)
-        ZT_TRY(run_matvec<float>(p, nrhs, a.x32, (float2 *)p->ws32.yout, s));
+    if (g.prod_if)
+        ZT_TRY(add_conditionals(s, g.h_prod, n, cudaGraphCondTypeIf, body_prod));
+    else if (mixed)
+        ZT_TRY(run_matvec<float>(p0, mem[0].nrhs, (const float2 *)p0->ws32.xin, (float2 *)p0->ws32.yout, s));
     else
-        ZT_TRY(run_matvec<double>(p, nrhs, w.xin64, w.w, s));
-    ZT_TRY(ops.arnoldi(a, 1, s));
-    ZT_TRY(add_conditional(s, a.h_reorth, cudaGraphCondTypeIf, &body_reorth));
-    ZT_TRY(launch_small(k_iter_ctl, 1, a, h_iter, s));
+        ZT_TRY(run_matvec<double>(p0, mem[0].nrhs, p0->sws.xin64, p0->sws.w, s));
+    ZT_TRY(ops.arnoldi(g, 1, s));
+    ZT_TRY(add_conditional(s, g.h_reorth, cudaGraphCondTypeIf, &body_reorth));
     ZT_TRY(capture_end(s));
     ZT_TRY(capture_begin(s, body_reorth, &sg.k_reorth));
-    ZT_TRY(ops.arnoldi(a, 2, s));
+    ZT_TRY(ops.arnoldi(g, 2, s));
     ZT_TRY(capture_end(s));
+    for (int i = 0; g.prod_if && i < n; ++i) {  // each member's iteration product
+        ztoep_plan_t p = mem[i].p;
+        uint64_t cnt = 0;
+        ZT_TRY(capture_begin(p->cap, body_prod[i], &cnt));
+        if (mixed)
+            ZT_TRY(run_matvec<float>(p, mem[i].nrhs, (const float2 *)p->ws32.xin, (float2 *)p->ws32.yout, p->cap));
+        else
+            ZT_TRY(run_matvec<double>(p, mem[i].nrhs, p->sws.xin64, p->sws.w, p->cap));
+        ZT_TRY(capture_end(p->cap));
+        sg.k_iter += cnt;
+    }
 
     ZT_CUDA(cudaGraphInstantiate(&sg.exec, top, 0));
     sg.prec = prec;
-    sg.nrhs = nrhs;
+    sg.nrhs = mem[0].nrhs;
     sg.m = m;
     return ZTOEP_OK;
 }
 
+static void abandon_capture(const Member *mem, int n) {
+    capture_count_end();
+    for (int i = 0; i < n; ++i) {
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(mem[i].p->cap, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(mem[i].p->cap, &junk);
+            if (junk) cudaGraphDestroy(junk);
+        }
+    }
+    cudaGetLastError();
+}
+
+static void destroy_graph(SolveGraph &sg) {
+    if (sg.exec) cudaGraphExecDestroy(sg.exec);
+    if (sg.graph) cudaGraphDestroy(sg.graph);
+    sg = SolveGraph{};
+}
+
+// Cached graph of a single-system solve (instantiated once per precision, RHS
+// count and restart length).
 static ztoep_status_t get_graph(ztoep_plan_t p, int prec, int nrhs, int m, SolveGraph **out) {
     for (auto &g : p->graphs)
         if (g.exec && g.prec == prec && g.nrhs == nrhs && g.m == m) {
@@ -1124,21 +1341,12 @@ static ztoep_status_t get_graph(ztoep_plan_t p, int prec, int nrhs, int m, Solve
         }
     SolveGraph &slot = p->graphs[p->graph_next];
     p->graph_next = (p->graph_next + 1) % 4;
-    if (slot.exec) cudaGraphExecDestroy(slot.exec);
-    if (slot.graph) cudaGraphDestroy(slot.graph);
-    slot = SolveGraph{};
-    ztoep_status_t st = build_graph(p, slot, prec, nrhs, m);
+    destroy_graph(slot);
+    const Member mem{p, nrhs};
+    ztoep_status_t st = build_graph(&mem, 1, slot, prec, m);
     if (st != ZTOEP_OK) {
-        capture_count_end();
-        cudaStreamCaptureStatus cs;
-        if (cudaStreamIsCapturing(p->cap, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
-            cudaGraph_t junk = nullptr;
-            cudaStreamEndCapture(p->cap, &junk);
-        }
-        cudaGetLastError();
-        if (slot.exec) cudaGraphExecDestroy(slot.exec);
-        if (slot.graph) cudaGraphDestroy(slot.graph);
-        slot = SolveGraph{};
+        abandon_capture(&mem, 1);
+        destroy_graph(slot);
         return st;
     }
     *out = &slot;
@@ -1146,76 +1354,76 @@ static ztoep_status_t get_graph(ztoep_plan_t p, int prec, int nrhs, int m, Solve
 }
 
 // The same solve with the loops driven from the host: every kernel is a
-// separate launch (for profilers that cannot see inside conditional graphs).
-// The loop decisions are read back from the control block.
-static ztoep_status_t run_host_loop(ztoep_plan_t p, int prec, int nrhs, int m, cudaStream_t s) {
+// separate launch (for profilers that cannot look inside conditional graph
+// nodes).  The loop decisions are read back from the control block.
+static ztoep_status_t run_host_loop(const Member *mem, int n, int prec, int m, cudaStream_t s) {
     const bool mixed = prec == ZTOEP_MIXED;
-    SolveWs &w = p->sws;
-    const Geom gm = geom_for(p->N, p->nsm);
-    const int per_cta = gm.threads * gm.elem;
-    const int nchunk = (int)((p->N + per_cta - 1) / per_cta);
-    const GArgs a = make_args(p, nrhs, m, mixed, nchunk);
-    const Ops ops{gm, dim3(nchunk, nrhs)};
-    SolveCtl *hc = reinterpret_cast<SolveCtl *>(w.hst + (size_t)w.cap * ST_STRIDE);
+    GroupArgs g = make_group(mem, n, m, mixed);
+    const Ops ops{group_elem(mem, n)};
+    SolveWs &w0 = mem[0].p->sws;
+    SolveCtl *hc = reinterpret_cast<SolveCtl *>(w0.hst + (size_t)w0.cap * ST_STRIDE);
+    CaptureEvents ce;
     auto read_ctl = [&]() -> ztoep_status_t {
-        ZT_CUDA(cudaMemcpyAsync(hc, w.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
+        ZT_CUDA(cudaMemcpyAsync(hc, w0.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
         ZT_CUDA(cudaStreamSynchronize(s));
         return ZTOEP_OK;
     };
     const cudaGraphConditionalHandle none = 0;
-    ZT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(int) * (size_t)w.cap * ST_STRIDE, s));
-    ZT_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(unsigned) * (size_t)w.cap * CNT_STRIDE, s));
-    const int zblocks = (int)std::min<int64_t>(4 * p->nsm, ((int64_t)nrhs * p->N + 255) / 256);
-    ZT_TRY(launch_small(k_solve_begin, std::max(1, zblocks), a, none, s, 0));
-    ZT_TRY(ops.vnorm(a, s));
+    for (int i = 0; i < n; ++i) {
+        SolveWs &w = mem[i].p->sws;
+        ZT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(int) * (size_t)w.cap * ST_STRIDE, s));
+        ZT_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(unsigned) * (size_t)w.cap * w.cstride, s));
+    }
+    int64_t elems = 0;
+    for (int i = 0; i < n; ++i) elems += (int64_t)mem[i].nrhs * mem[i].p->N;
+    const int zblocks = (int)std::min<int64_t>(4 * mem[0].p->nsm, (elems + 255) / 256);
+    ZT_TRY(launch_ctl(k_solve_begin, std::max(1, zblocks), g, none, s));
+    ZT_TRY(ops.vnorm(g, s));
     ZT_TRY(read_ctl());
-    if (hc->cond_first) ZT_TRY(run_matvec<double>(p, nrhs, w.xbuf, w.w, s));
-    ZT_TRY(ops.residual(a, 1, s));
-    ZT_TRY(launch_small(k_sweep_ctl, 1, a, none, s, 0));
+    if (hc->cond_first) ZT_TRY(member_products(mem, n, false, true, s, ce));
+    ZT_TRY(ops.residual(g, 1, s));
+    ZT_TRY(launch_ctl(k_sweep_ctl, 1, g, none, s));
     ZT_TRY(read_ctl());
     while (hc->cond_sweep) {
-        ZT_TRY(launch_small(k_restart_begin, 1, a, none, s, 0));
+        ZT_TRY(launch_ctl(k_restart_begin, 1, g, none, s));
         for (;;) {
-            ZT_TRY(launch_small(k_cycle_begin, 1, a, none, s, 0));
+            ZT_TRY(launch_ctl(k_cycle_begin, g, s));
             for (int it = 0; it < m; ++it) {
-                if (mixed)
-                    ZT_TRY(run_matvec<float>(p, nrhs, a.x32, (float2 *)p->ws32.yout, s));
-                else
-                    ZT_TRY(run_matvec<double>(p, nrhs, w.xin64, w.w, s));
-                ZT_TRY(ops.arnoldi(a, 1, s));
-                ZT_TRY(ops.arnoldi(a, 2, s));
-                ZT_TRY(launch_small(k_iter_ctl, 1, a, none, s, 0));
+                ZT_TRY(member_products(mem, n, mixed, false, s, ce));
+                ZT_TRY(ops.arnoldi(g, 1, s));
                 ZT_TRY(read_ctl());
+                if (hc->reorth_pending) {
+                    ZT_TRY(ops.arnoldi(g, 2, s));
+                    ZT_TRY(read_ctl());
+                }
                 if (!hc->cond_iter) break;
             }
-            ZT_TRY(ops.update_d(a, s));
+            ZT_TRY(ops.update_d(g, s));
             if (mixed) {
-                ZT_TRY(run_matvec<float>(p, nrhs, a.x32, (float2 *)p->ws32.yout, s));
-                ZT_TRY(ops.inner_residual(a, s));
+                ZT_TRY(member_products(mem, n, true, false, s, ce));
+                ZT_TRY(ops.inner_residual(g, s));
             }
-            ZT_TRY(launch_small(k_restart_ctl, 1, a, none, s, 0));
+            ZT_TRY(launch_ctl(k_restart_ctl, 1, g, none, s));
             ZT_TRY(read_ctl());
             if (!hc->cond_restart) break;
         }
-        ZT_TRY(ops.apply_d(a, s));
-        ZT_TRY(run_matvec<double>(p, nrhs, w.xbuf, w.w, s));
-        ZT_TRY(ops.residual(a, 0, s));
-        ZT_TRY(launch_small(k_sweep_ctl, 1, a, none, s, 0));
+        ZT_TRY(ops.apply_d(g, s));
+        ZT_TRY(member_products(mem, n, false, true, s, ce));
+        ZT_TRY(ops.residual(g, 0, s));
+        ZT_TRY(launch_ctl(k_sweep_ctl, 1, g, none, s));
         ZT_TRY(read_ctl());
     }
     return ZTOEP_OK;
 }
 
-// Prepare buffers and the graph; V/X must already be in vbuf/xbuf (X only when
-// no zero guess).  Runs the solve graph on `s` and fetches the per-RHS state.
-static ztoep_status_t solve_core(ztoep_plan_t p, const ztoep_solve_opts_t *o, int nrhs, ztoep_solve_info_t *info,
-                                 cudaStream_t s) {
+// Runs the solve of the members (V / X already in each member's vbuf / xbuf,
+// X only without a zero guess) on `s` and fetches the per-RHS states.  `sg`:
+// the graph to launch, or null for the host-driven loop.
+static ztoep_status_t solve_core(const Member *mem, int n, const ztoep_solve_opts_t *o, SolveGraph *sg,
+                                 ztoep_solve_info_t *const *info, cudaStream_t s) {
     const int m = o->restart;
-    const bool host_loop = (o->flags & ZTOEP_FLAG_HOST_LOOP) != 0;
-    SolveGraph *g = nullptr;
-    if (!host_loop) ZT_TRY(get_graph(p, o->prec, nrhs, m, &g));
-    SolveWs &w = p->sws;
-    SolveCtl *hc = reinterpret_cast<SolveCtl *>(w.hst + (size_t)w.cap * ST_STRIDE);
+    SolveWs &w0 = mem[0].p->sws;
+    SolveCtl *hc = reinterpret_cast<SolveCtl *>(w0.hst + (size_t)w0.cap * ST_STRIDE);
     std::memset(hc, 0, sizeof(SolveCtl));
     hc->zero = (o->flags & ZTOEP_FLAG_ZERO_GUESS) ? 1 : 0;
     hc->max_iter = o->max_iter;
@@ -1223,45 +1431,48 @@ static ztoep_status_t solve_core(ztoep_plan_t p, const ztoep_solve_opts_t *o, in
     hc->tol = o->tol;
     hc->inner_tol = o->inner_tol;
     hc->timeout_ns = o->timeout_ns;
-    ZT_CUDA(cudaMemcpyAsync(w.ctl, hc, sizeof(SolveCtl), cudaMemcpyHostToDevice, s));
-    if (host_loop)
-        ZT_TRY(run_host_loop(p, o->prec, nrhs, m, s));
+    ZT_CUDA(cudaMemcpyAsync(w0.ctl, hc, sizeof(SolveCtl), cudaMemcpyHostToDevice, s));
+    if (!sg)
+        ZT_TRY(run_host_loop(mem, n, o->prec, m, s));
     else
-        ZT_CUDA(cudaGraphLaunch(g->exec, s));
-    ZT_CUDA(cudaMemcpyAsync(w.hst, w.st, sizeof(int) * (size_t)nrhs * ST_STRIDE, cudaMemcpyDeviceToHost, s));
-    ZT_CUDA(cudaMemcpyAsync(hc, w.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
-    ZT_CUDA(cudaMemcpyAsync(w.hnrm, w.nrm, sizeof(double) * (size_t)nrhs * NM_STRIDE, cudaMemcpyDeviceToHost, s));
-    int dev_err = 0;
-    ZT_CUDA(cudaMemcpyAsync(&dev_err, p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    ZT_CUDA(cudaStreamSynchronize(s));
-    if (g)
-        add_launches(g->k_fixed + (hc->zero ? 0 : g->k_first_product) + (uint64_t)hc->outer_bodies * g->k_sweep +
-                     (uint64_t)hc->restart_bodies * g->k_restart + (uint64_t)hc->inner_bodies * g->k_iter +
-                     (uint64_t)hc->reorth_bodies * g->k_reorth);
-    bool timed_out = hc->timed_out != 0;
-    if (dev_err != 0) {  // a bounded device-side wait gave up
-        ZT_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), s));
-        timed_out = true;
+        ZT_CUDA(cudaGraphLaunch(sg->exec, s));
+    std::vector<int> dev_err(n, 0);
+    for (int i = 0; i < n; ++i) {
+        SolveWs &w = mem[i].p->sws;
+        ZT_CUDA(cudaMemcpyAsync(w.hst, w.st, sizeof(int) * (size_t)mem[i].nrhs * ST_STRIDE, cudaMemcpyDeviceToHost, s));
+        ZT_CUDA(cudaMemcpyAsync(w.hnrm, w.nrm, sizeof(double) * (size_t)mem[i].nrhs * NM_STRIDE,
+                                cudaMemcpyDeviceToHost, s));
+        ZT_CUDA(cudaMemcpyAsync(&dev_err[i], mem[i].p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     }
+    ZT_CUDA(cudaMemcpyAsync(hc, w0.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
+    ZT_CUDA(cudaStreamSynchronize(s));
+    if (sg)
+        add_launches(sg->k_fixed + (hc->zero ? 0 : sg->k_first_product) + (uint64_t)hc->outer_bodies * sg->k_sweep +
+                     (uint64_t)hc->restart_bodies * sg->k_restart + (uint64_t)hc->inner_bodies * sg->k_iter +
+                     (uint64_t)hc->reorth_bodies * sg->k_reorth);
+    const bool timed_out = hc->timed_out != 0;
     ztoep_status_t worst = ZTOEP_OK;
-    for (int rr = 0; rr < nrhs; ++rr) {
-        const int *st = w.hst + rr * ST_STRIDE;
-        const double *nm = w.hnrm + rr * NM_STRIDE;
-        ztoep_status_t rs;
-        switch (st[ST_STATUS]) {
-            case RS_CONVERGED: rs = ZTOEP_OK; break;
-            case RS_NONFINITE: rs = ZTOEP_ERR_NONFINITE; break;
-            case RS_MAXITER: rs = ZTOEP_ERR_NOCONV; break;
-            default: rs = timed_out ? ZTOEP_ERR_TIMEOUT : ZTOEP_ERR_NOCONV; break;
-        }
-        if (dev_err != 0) rs = ZTOEP_ERR_TIMEOUT;
-        if (rs != ZTOEP_OK && (worst == ZTOEP_OK || rs == ZTOEP_ERR_NONFINITE || rs == ZTOEP_ERR_TIMEOUT))
-            worst = rs;
-        if (info) {
-            info[rr].outer = st[ST_OUTER];
-            info[rr].inner_iters = st[ST_ITERS];
-            info[rr].status = rs;
-            info[rr].rel_residual = nm[NM_VNORM] > 0 ? nm[NM_RNORM] / nm[NM_VNORM] : nm[NM_RNORM];
+    for (int i = 0; i < n; ++i) {
+        if (dev_err[i] != 0) ZT_CUDA(cudaMemsetAsync(mem[i].p->err, 0, sizeof(int), s));  // a bounded wait gave up
+        for (int rr = 0; rr < mem[i].nrhs; ++rr) {
+            const int *st = mem[i].p->sws.hst + rr * ST_STRIDE;
+            const double *nm = mem[i].p->sws.hnrm + rr * NM_STRIDE;
+            ztoep_status_t rs;
+            switch (st[ST_STATUS]) {
+                case RS_CONVERGED: rs = ZTOEP_OK; break;
+                case RS_NONFINITE: rs = ZTOEP_ERR_NONFINITE; break;
+                case RS_MAXITER: rs = ZTOEP_ERR_NOCONV; break;
+                default: rs = timed_out ? ZTOEP_ERR_TIMEOUT : ZTOEP_ERR_NOCONV; break;
+            }
+            if (dev_err[i] != 0) rs = ZTOEP_ERR_TIMEOUT;
+            if (rs != ZTOEP_OK && (worst == ZTOEP_OK || rs == ZTOEP_ERR_NONFINITE || rs == ZTOEP_ERR_TIMEOUT))
+                worst = rs;
+            if (info && info[i]) {
+                info[i][rr].outer = st[ST_OUTER];
+                info[i][rr].inner_iters = st[ST_ITERS];
+                info[i][rr].status = rs;
+                info[i][rr].rel_residual = nm[NM_VNORM] > 0 ? nm[NM_RNORM] / nm[NM_VNORM] : nm[NM_RNORM];
+            }
         }
     }
     return worst;
@@ -1275,6 +1486,20 @@ static ztoep_status_t prepare(ztoep_plan_t p, const ztoep_solve_opts_t *o, int n
     }
     ZT_TRY(ensure_ws<double>(p, nrhs));
     return ZTOEP_OK;
+}
+
+static bool hard_error(ztoep_status_t st) {
+    return st == ZTOEP_ERR_ARG || st == ZTOEP_ERR_CUDA || st == ZTOEP_ERR_NOMEM || st == ZTOEP_ERR_UNSUPPORTED;
+}
+
+// One system: the plan's cached graph (or the host-driven loop).
+static ztoep_status_t solve_single(ztoep_plan_t p, const ztoep_solve_opts_t *o, int nrhs, ztoep_solve_info_t *info,
+                                   cudaStream_t s) {
+    SolveGraph *g = nullptr;
+    if (!(o->flags & ZTOEP_FLAG_HOST_LOOP)) ZT_TRY(get_graph(p, o->prec, nrhs, o->restart, &g));
+    const Member mem{p, nrhs};
+    ztoep_solve_info_t *const infos[1] = {info};
+    return solve_core(&mem, 1, o, g, infos, s);
 }
 
 }  // namespace ztoep
@@ -1299,9 +1524,8 @@ ztoep_status_t ztoep_solve(ztoep_plan_t p, const ztoep_solve_opts_t *o, int32_t 
     const size_t bytes = sizeof(double2) * (size_t)nrhs * p->N;
     ZT_CUDA(cudaMemcpyAsync(w.vbuf, V, bytes, cudaMemcpyDeviceToDevice, s));
     if (!(o->flags & ZTOEP_FLAG_ZERO_GUESS)) ZT_CUDA(cudaMemcpyAsync(w.xbuf, X, bytes, cudaMemcpyDeviceToDevice, s));
-    const ztoep_status_t st = solve_core(p, o, nrhs, info, s);
-    if (st == ZTOEP_ERR_ARG || st == ZTOEP_ERR_CUDA || st == ZTOEP_ERR_NOMEM || st == ZTOEP_ERR_UNSUPPORTED)
-        return st;
+    const ztoep_status_t st = solve_single(p, o, nrhs, info, s);
+    if (hard_error(st)) return st;
     ZT_CUDA(cudaMemcpyAsync(X, w.xbuf, bytes, cudaMemcpyDeviceToDevice, s));
     return st;
 }
@@ -1316,11 +1540,67 @@ ztoep_status_t ztoep_solve_host(ztoep_plan_t p, const ztoep_solve_opts_t *o, int
     const size_t bytes = sizeof(double2) * (size_t)nrhs * p->N;
     ZT_CUDA(cudaMemcpyAsync(w.vbuf, Vh, bytes, cudaMemcpyHostToDevice, s));
     if (!(o->flags & ZTOEP_FLAG_ZERO_GUESS)) ZT_CUDA(cudaMemcpyAsync(w.xbuf, Xh, bytes, cudaMemcpyHostToDevice, s));
-    const ztoep_status_t st = solve_core(p, o, nrhs, info, s);
-    if (st == ZTOEP_ERR_ARG || st == ZTOEP_ERR_CUDA || st == ZTOEP_ERR_NOMEM || st == ZTOEP_ERR_UNSUPPORTED)
-        return st;
+    const ztoep_status_t st = solve_single(p, o, nrhs, info, s);
+    if (hard_error(st)) return st;
     ZT_CUDA(cudaMemcpyAsync(Xh, w.xbuf, bytes, cudaMemcpyDeviceToHost, s));
     ZT_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
+
+ztoep_status_t ztoep_solve_group(int32_t count, const ztoep_plan_t *plans, const ztoep_solve_opts_t *o,
+                                 const int32_t *nrhs, const void *const *V, void *const *X,
+                                 ztoep_solve_info_t *const *info, void *stream) {
+    if (count < 1 || count > kMaxMembers || !plans || !valid_opts(o) || !nrhs || !V || !X) return ZTOEP_ERR_ARG;
+    Member mem[kMaxMembers];
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || nrhs[i] < 1 || !V[i] || !X[i] || V[i] == X[i]) return ZTOEP_ERR_ARG;
+        for (int k = 0; k < i; ++k)
+            if (plans[k] == plans[i]) return ZTOEP_ERR_ARG;  // each member needs its own plan (workspace)
+        if (plans[i]->device != plans[0]->device) return ZTOEP_ERR_ARG;
+        mem[i] = Member{plans[i], nrhs[i]};
+    }
+    // one launch per step needs one chunk shape (elements per thread) for all
+    for (int i = 1; i < count; ++i)
+        if (geom_for(plans[i]->N, plans[i]->nsm).elem != geom_for(plans[0]->N, plans[0]->nsm).elem)
+            return ZTOEP_ERR_UNSUPPORTED;
+    // lock the plans in address order (no deadlock with other group calls)
+    std::vector<ztoep_plan_t> order(plans, plans + count);
+    std::sort(order.begin(), order.end());
+    std::vector<std::unique_lock<std::mutex>> locks;
+    for (ztoep_plan_t p : order) locks.emplace_back(p->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < count; ++i) {
+        ztoep_plan_t p = mem[i].p;
+        ZT_TRY(prepare(p, o, mem[i].nrhs, s));
+        const size_t bytes = sizeof(double2) * (size_t)mem[i].nrhs * p->N;
+        ZT_CUDA(cudaMemcpyAsync(p->sws.vbuf, V[i], bytes, cudaMemcpyDeviceToDevice, s));
+        if (!(o->flags & ZTOEP_FLAG_ZERO_GUESS))
+            ZT_CUDA(cudaMemcpyAsync(p->sws.xbuf, X[i], bytes, cudaMemcpyDeviceToDevice, s));
+    }
+    ztoep_status_t st;
+    if (count == 1) {
+        st = solve_single(mem[0].p, o, mem[0].nrhs, info ? info[0] : nullptr, s);
+    } else if (o->flags & ZTOEP_FLAG_HOST_LOOP) {
+        st = solve_core(mem, count, o, nullptr, info, s);
+    } else {
+        // the members' copies of V and X above are ordered before the graph on s
+        SolveGraph sg;
+        st = build_graph(mem, count, sg, o->prec, o->restart);
+        if (st != ZTOEP_OK) {
+            abandon_capture(mem, count);
+            destroy_graph(sg);
+            return st;
+        }
+        st = solve_core(mem, count, o, &sg, info, s);
+        if (hard_error(st)) cudaStreamSynchronize(s);
+        destroy_graph(sg);  // the graph has finished (solve_core synchronised the stream)
+    }
+    if (hard_error(st)) return st;
+    for (int i = 0; i < count; ++i) {
+        ztoep_plan_t p = mem[i].p;
+        ZT_CUDA(cudaMemcpyAsync(X[i], p->sws.xbuf, sizeof(double2) * (size_t)mem[i].nrhs * p->N,
+                                cudaMemcpyDeviceToDevice, s));
+    }
     return st;
 }
 

@@ -390,161 +390,191 @@ __global__ void __launch_bounds__(256) k_edge_finish(const cplx_t<R> *__restrict
     if (lane == 0) y[(int64_t)r * N + NT + e] = s;
 }
 
-// FP32 edge coupling, one pass over B with no E split: a CTA owns a tile of
-// E2_TW columns of B and reads all E rows of it; warp w takes the rows
-// w*UNR.., w*UNR + W*UNR.., ... (UNR rows per step, loads first).
-//   Ep[tile][r][e] = sum_{t in tile} B[e][t] x_T[r][t]  (complete per warp, no
-//                    cross-warp step: every row of the tile is one warp's)
-//   ET[r][t]       = sum_e B[e][t] x_E[r][e]            (per-warp sums added in
-//                    warp order through shared memory at the end)
-// So B^T x_E needs no partial buffers and no fold, and the loop has no
-// barrier.  Rows are taken in chunks of E2_ECH so x_E fits in shared memory.
-constexpr int E2_W = 8, E2_U = 2, E2_CPL = 2, E2_TW = 32 * E2_U * E2_CPL, E2_ECH = 1024;
+// FP32 edge coupling in one pass over [B | C]: the FP32 copy of B carries C
+// in the E columns after the N_T Toeplitz ones, so one row of it times the
+// whole x = (x_T, x_E) is the edge row y_E = B x_T + C x_E.
+//   ET[r][t]    = sum_e B[e][t] x_E[r][e]       (t < N_T; complete per column)
+//   y[r][N_T+e] = sum_t [B|C][e][t] x[r][t]     (per-CTA row partials, summed
+//                 by the last CTAs to finish)
+// The N_T + E columns are split into G contiguous ranges, G a multiple of the
+// SM count, so every SM streams the same share of B.  A CTA walks its range
+// in sub-tiles of E3_TW columns and reads all E rows of each; warp w takes
+// rows w*UNR.., w*UNR + W*UNR.., ... (UNR rows per step, loads first), so each
+// row's partial is one warp's and needs no cross-warp step; the B^T x_E sums
+// of the warps are added in warp order through shared memory.  Rows are taken
+// in chunks of E3_ECH so x_E fits in shared memory.
+// Row partials: Ep[cta][r][e] (accumulated over the CTA's sub-tiles by the
+// same thread).  The last CTA to finish in each group of E3_GROUP CTAs adds
+// the group's partials in CTA order into Eg[g][r][e]; the last group to
+// finish adds the group sums in group order into y.  The tickets are
+// last-arriver counters (no waiting) that reset themselves, and every sum has
+// an order fixed by the plan's geometry, so a RHS is summed identically alone
+// and in any batch.
+constexpr int E3_W = 8, E3_U = 2, E3_CPL = 2, E3_TW = 32 * E3_U * E3_CPL, E3_ECH = 1024, E3_GROUP = 16;
+
+struct Edge3Args {
+    const float2 *x;  // [nrhs][N]
+    const float2 *B;  // [E][ldb]: B in columns < NT, C in NT .. NT+E-1, zeros after
+    float2 *ET;       // [nrhs][NT]
+    float2 *Ep;       // [G][nrhs][E]
+    float2 *Eg;       // [ngroups][nrhs][E]
+    float2 *y;        // [nrhs][N] (rows NT.. written here)
+    unsigned *cnt;    // [ngroups + 1] tickets, zero between launches
+    int64_t NT, ncol, ldb, N;
+    int E, nrhs, r0, rc, range, G, ngroups;
+};
+
+// out[k] = sum_{c < n} src[c * stride + k0] in c order, loads issued 16 at a time.
+__device__ __forceinline__ float2 ordered_sum(const float2 *src, int n, int64_t stride) {
+    float2 s = make_float2(0.f, 0.f);
+    int c = 0;
+    for (; c + 16 <= n; c += 16) {
+        float2 v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = __ldcg(src + (int64_t)(c + i) * stride);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) s = s + v[i];
+    }
+    for (; c < n; ++c) s = s + __ldcg(src + (int64_t)c * stride);
+    return s;
+}
 
 template <int RC>
-__global__ void __launch_bounds__(256) k_edge2(const float2 *__restrict__ x, const float2 *__restrict__ B,
-                                               float2 *__restrict__ ET, float2 *__restrict__ Ep, int64_t NT,
-                                               int64_t ldb, int E, int64_t N, int nrhs, int r0, int rc) {
-    constexpr int U = E2_U, CPL = E2_CPL, W = E2_W, UNR = 4;
+__global__ void __launch_bounds__(256) k_edge3(Edge3Args a) {
+    constexpr int U = E3_U, CPL = E3_CPL, W = E3_W, UNR = 4;
     // x_E of the current row chunk, later reused for the cross-warp sums
-    constexpr int SX = E2_ECH * RC, SR = W * E2_TW * RC;
+    constexpr int SX = E3_ECH * RC, SR = W * E3_TW * RC;
     __shared__ float2 sh[SX > SR ? SX : SR];
+    __shared__ unsigned s_ticket;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tile = blockIdx.x;
-    const int64_t tbase = (int64_t)tile * E2_TW;
+    const int cta = blockIdx.x;
+    const int64_t c0 = (int64_t)cta * a.range;
+    const int64_t c1 = c0 + a.range < a.ncol ? c0 + a.range : a.ncol;
+    const int E = a.E, rc = a.rc, r0 = a.r0;
 
-    float2 xt[U][CPL][RC], acc[U][CPL][RC];
+    for (int64_t tbase = c0; tbase < c1; tbase += E3_TW) {
+        const bool first = tbase == c0;
+        float2 xt[U][CPL][RC], acc[U][CPL][RC];
 #pragma unroll
-    for (int u = 0; u < U; ++u)
+        for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-            const int64_t t = tbase + (int64_t)(u * 32 + lane) * CPL + c;
+            for (int c = 0; c < CPL; ++c) {
+                const int64_t t = tbase + (int64_t)(u * 32 + lane) * CPL + c;
 #pragma unroll
-            for (int q = 0; q < RC; ++q) {
-                acc[u][c][q] = make_float2(0.f, 0.f);
-                xt[u][c][q] = (t < NT && q < rc) ? x[(int64_t)(r0 + q) * N + t] : make_float2(0.f, 0.f);
+                for (int q = 0; q < RC; ++q) {
+                    acc[u][c][q] = make_float2(0.f, 0.f);
+                    xt[u][c][q] = (t < c1 && q < rc) ? a.x[(int64_t)(r0 + q) * a.N + t] : make_float2(0.f, 0.f);
+                }
             }
-        }
-    for (int ec = 0; ec < E; ec += E2_ECH) {
-        const int ne = min(E2_ECH, E - ec);
-        __syncthreads();
-        for (int k = threadIdx.x; k < ne * RC; k += blockDim.x) {
-            const int el = k / RC, q = k - el * RC;
-            sh[k] = q < rc ? x[(int64_t)(r0 + q) * N + NT + ec + el] : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-        for (int el0 = warp * UNR; el0 < ne; el0 += W * UNR) {
-            float4 raw[UNR][U];
-#pragma unroll
-            for (int k = 0; k < UNR; ++k) {
-                const float2 *brow = B + (int64_t)(ec + el0 + k) * ldb + tbase;
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    raw[k][u] = (el0 + k < ne)
-                                    ? __ldcs(reinterpret_cast<const float4 *>(brow + (int64_t)(u * 32 + lane) * CPL))
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int ec = 0; ec < E; ec += E3_ECH) {
+            const int ne = min(E3_ECH, E - ec);
+            __syncthreads();
+            for (int k = threadIdx.x; k < ne * RC; k += blockDim.x) {
+                const int el = k / RC, q = k - el * RC;
+                sh[k] = q < rc ? a.x[(int64_t)(r0 + q) * a.N + a.NT + ec + el] : make_float2(0.f, 0.f);
             }
-            float2 part[UNR][RC];
+            __syncthreads();
+            for (int el0 = warp * UNR; el0 < ne; el0 += W * UNR) {
+                float4 raw[UNR][U];
 #pragma unroll
-            for (int k = 0; k < UNR; ++k) {
-                const int el = el0 + k;
-                float2 bv[U][CPL];
+                for (int k = 0; k < UNR; ++k) {
+                    const float2 *brow = a.B + (int64_t)(ec + el0 + k) * a.ldb + tbase;
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    bv[u][0] = make_float2(raw[k][u].x, raw[k][u].y);
-                    bv[u][1] = make_float2(raw[k][u].z, raw[k][u].w);
+                    for (int u = 0; u < U; ++u)  // only this CTA's columns: no byte of B is fetched twice
+                        raw[k][u] = (el0 + k < ne && tbase + (u * 32 + lane) * CPL < c1)
+                                        ? __ldcs(reinterpret_cast<const float4 *>(brow + (int64_t)(u * 32 + lane) * CPL))
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                float2 part[UNR][RC];
+#pragma unroll
+                for (int k = 0; k < UNR; ++k) {
+                    const int el = el0 + k;
+                    float2 bv[U][CPL];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        bv[u][0] = make_float2(raw[k][u].x, raw[k][u].y);
+                        bv[u][1] = make_float2(raw[k][u].z, raw[k][u].w);
+                    }
+#pragma unroll
+                    for (int q = 0; q < RC; ++q) {
+                        const float2 xe = el < ne ? sh[el * RC + q] : make_float2(0.f, 0.f);
+                        float2 pt = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+#pragma unroll
+                            for (int c = 0; c < CPL; ++c) {
+                                acc[u][c][q] = cfma(bv[u][c], xe, acc[u][c][q]);
+                                pt = cfma(bv[u][c], xt[u][c][q], pt);
+                            }
+                        part[k][q] = pt;
+                    }
                 }
 #pragma unroll
                 for (int q = 0; q < RC; ++q) {
-                    const float2 xe = el < ne ? sh[el * RC + q] : make_float2(0.f, 0.f);
-                    float2 pt = make_float2(0.f, 0.f);
+                    float2 v4[UNR];
 #pragma unroll
-                    for (int u = 0; u < U; ++u)
-#pragma unroll
-                        for (int c = 0; c < CPL; ++c) {
-                            acc[u][c][q] = cfma(bv[u][c], xe, acc[u][c][q]);
-                            pt = cfma(bv[u][c], xt[u][c][q], pt);
-                        }
-                    part[k][q] = pt;
+                    for (int k = 0; k < UNR; ++k) v4[k] = part[k][q];
+                    const float2 tot = warp_rs4<float>(v4);
+                    const int k = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
+                    if ((lane & 7) == 0 && el0 + k < ne && q < rc) {
+                        float2 *dst = a.Ep + ((int64_t)cta * a.nrhs + r0 + q) * E + ec + el0 + k;
+                        *dst = first ? tot : *dst + tot;  // the same thread owns this row in every sub-tile
+                    }
                 }
             }
+        }
+        __syncthreads();
+        // B^T x_E of this sub-tile: add the W per-warp sums in warp order
 #pragma unroll
-            for (int q = 0; q < RC; ++q) {
-                float2 v4[UNR];
+        for (int u = 0; u < U; ++u)
 #pragma unroll
-                for (int k = 0; k < UNR; ++k) v4[k] = part[k][q];
-                const float2 tot = warp_rs4<float>(v4);
-                const int k = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
-                if ((lane & 7) == 0 && el0 + k < ne && q < rc)
-                    Ep[((int64_t)tile * nrhs + r0 + q) * E + ec + el0 + k] = tot;
+            for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                for (int q = 0; q < RC; ++q)
+                    sh[(warp * E3_TW + (u * 32 + lane) * CPL + c) * RC + q] = acc[u][c][q];
+        __syncthreads();
+        for (int k = threadIdx.x; k < E3_TW * RC; k += blockDim.x) {
+            const int col = k / RC, q = k - col * RC;
+            const int64_t t = tbase + col;
+            if (t < c1 && t < a.NT && q < rc) {
+                float2 sum = sh[col * RC + q];
+#pragma unroll
+                for (int w = 1; w < W; ++w) sum = sum + sh[(w * E3_TW + col) * RC + q];
+                a.ET[(int64_t)(r0 + q) * a.NT + t] = sum;
             }
         }
     }
-    __syncthreads();
-    // B^T x_E: add the W per-warp sums in warp order
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int c = 0; c < CPL; ++c)
-#pragma unroll
-            for (int q = 0; q < RC; ++q) sh[(warp * E2_TW + (u * 32 + lane) * CPL + c) * RC + q] = acc[u][c][q];
-    __syncthreads();
-    for (int k = threadIdx.x; k < E2_TW * RC; k += blockDim.x) {
-        const int col = k / RC, q = k - col * RC;
-        const int64_t t = tbase + col;
-        if (t < NT && q < rc) {
-            float2 sum = sh[col * RC + q];
-#pragma unroll
-            for (int w = 1; w < W; ++w) sum = sum + sh[(w * E2_TW + col) * RC + q];
-            ET[(int64_t)(r0 + q) * NT + t] = sum;
-        }
-    }
-}
 
-// y_E[r][e] = sum_tile Ep[tile][r][e] + sum_e' C[e][e'] x_E[r][e'].  A CTA
-// owns 8 edge rows of one RHS: thread (g, l), g < 32, adds tiles g, g+32, ...
-// of row e0+l (four accumulators), the 32 group sums are added by a pairwise
-// tree in a fixed order, and warp w forms the C x_E term of row e0+w.
-__global__ void __launch_bounds__(256) k_edge_finish2(const float2 *__restrict__ x, const float2 *__restrict__ Cm,
-                                                      const float2 *__restrict__ Ep, float2 *__restrict__ y,
-                                                      int64_t NT, int E, int64_t N, int nrhs, int ntile) {
-    __shared__ float2 red[32][8];
-    __shared__ float2 cx[8];
-    const int l = threadIdx.x & 7, g = threadIdx.x >> 3;
-    const int e0 = blockIdx.x * 8, r = blockIdx.y;
-    const int e = e0 + l;
-    float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
-    if (e < E) {
-        const float2 *col = Ep + (int64_t)r * E + e;
-        const int64_t ts = (int64_t)nrhs * E;  // stride between tiles
-        int t = g;
-        for (; t + 96 < ntile; t += 128) {
-            s0 = s0 + col[(int64_t)t * ts];
-            s1 = s1 + col[(int64_t)(t + 32) * ts];
-            s2 = s2 + col[(int64_t)(t + 64) * ts];
-            s3 = s3 + col[(int64_t)(t + 96) * ts];
-        }
-        for (; t < ntile; t += 32) s0 = s0 + col[(int64_t)t * ts];
-    }
-    red[g][l] = (s0 + s1) + (s2 + s3);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    {
-        const int er = e0 + w;
-        float2 c = make_float2(0.f, 0.f);
-        if (er < E) {
-            const float2 *crow = Cm + (int64_t)er * E;
-            const float2 *xe = x + (int64_t)r * N + NT;
-            for (int j = lane; j < E; j += 32) c = cfma(crow[j], xe[j], c);
-        }
-        c = warp_sum<float>(c);
-        if (lane == 0) cx[w] = c;
-    }
+    // level 1: the last CTA of the group adds the group's row partials
+    const int g = cta / E3_GROUP;
+    const int gfirst = g * E3_GROUP;
+    const int gsize = min(E3_GROUP, a.G - gfirst);
+    __threadfence();
     __syncthreads();
-    for (int h = 16; h > 0; h >>= 1) {
-        if (g < h) red[g][l] = red[g][l] + red[g + h][l];
-        __syncthreads();
+    if (threadIdx.x == 0) s_ticket = atomicAdd(a.cnt + g, 1u);
+    __syncthreads();
+    if (s_ticket != (unsigned)gsize - 1) return;
+    __threadfence();
+    if (threadIdx.x == 0) a.cnt[g] = 0u;
+    const int64_t pstride = (int64_t)a.nrhs * E;  // between CTAs (and between groups)
+    for (int k = threadIdx.x; k < E * rc; k += blockDim.x) {
+        const int q = k / E, e = k - q * E;
+        const int64_t off = (int64_t)(r0 + q) * E + e;
+        a.Eg[(int64_t)g * pstride + off] = ordered_sum(a.Ep + (int64_t)gfirst * pstride + off, gsize, pstride);
     }
-    if (threadIdx.x < 8 && e < E) y[(int64_t)r * N + NT + e] = red[0][l] + cx[l];
+    // level 2: the last group adds the group sums into y_E
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_ticket = atomicAdd(a.cnt + a.ngroups, 1u);
+    __syncthreads();
+    if (s_ticket != (unsigned)a.ngroups - 1) return;
+    __threadfence();
+    if (threadIdx.x == 0) a.cnt[a.ngroups] = 0u;
+    for (int k = threadIdx.x; k < E * rc; k += blockDim.x) {
+        const int q = k / E, e = k - q * E;
+        const int64_t off = (int64_t)(r0 + q) * E + e;
+        a.y[(int64_t)(r0 + q) * a.N + a.NT + e] = ordered_sum(a.Eg + off, a.ngroups, pstride);
+    }
 }
 
 // ------------------------------------------------------------ conversions
@@ -585,7 +615,19 @@ static int edge_ntile(ztoep_plan_t p, size_t csize) {
     int tile = (csize == 8) ? EdgeGeom<float>::TILE : EdgeGeom<double>::TILE;
     return (int)((p->NT + tile - 1) / tile);
 }
-static int edge2_ntile(ztoep_plan_t p) { return (int)((p->NT + E2_TW - 1) / E2_TW); }
+// Column split of k_edge3: about 4 CTAs per SM over the N_T + E columns of
+// [B | C], each range a multiple of 4 columns (16-byte loads) and at least 32.
+struct Edge3Geom {
+    int G, range, ngroups;
+};
+static Edge3Geom edge3_geom(ztoep_plan_t p) {
+    const int64_t ncol = p->NT + p->E;
+    const int want = 4 * p->nsm;
+    int64_t range = (ncol + want - 1) / want;
+    range = std::max<int64_t>(32, (range + 3) / 4 * 4);
+    const int G = (int)((ncol + range - 1) / range);
+    return {G, (int)range, (G + E3_GROUP - 1) / E3_GROUP};
+}
 static int edge_nsplit(ztoep_plan_t p, int ntile, size_t csize) {
     if (p->E == 0) return 0;
     // enough CTAs for several resident per SM (FP32: 4 per SM, FP64: 2)
@@ -609,7 +651,7 @@ static int tc_edge_splits(ztoep_plan_t p) { return cgemm_splits((int)p->NT, tc_e
 
 static void free_ws(MatvecWs &w) {
     cudaFree(w.xin); cudaFree(w.yout); cudaFree(w.X1); cudaFree(w.Xh); cudaFree(w.ET); cudaFree(w.Ep); cudaFree(w.Yh);
-    cudaFree(w.Fs); cudaFree(w.Us);
+    cudaFree(w.Fs); cudaFree(w.Us); cudaFree(w.Eg); cudaFree(w.cnt);
     w = MatvecWs{};
 }
 
@@ -633,8 +675,14 @@ template <typename R> ztoep_status_t ensure_ws(ztoep_plan_t p, int nrhs) {
         ZT_TRY(dalloc(&w.Us, side, &acc));
     } else if (p->E > 0) {
         ZT_TRY(dalloc(&w.ET, cs * (size_t)std::max(nsplit, 1) * nrhs * p->NT, &acc));
-        const int parts = std::max(cs == 8 ? edge2_ntile(p) : ntile, tc ? tc_edge_splits(p) : 0);
+        const int parts = std::max(cs == 8 ? edge3_geom(p).G : ntile, tc ? tc_edge_splits(p) : 0);
         ZT_TRY(dalloc(&w.Ep, cs * (size_t)parts * nrhs * p->E, &acc));
+        if (cs == 8) {
+            const Edge3Geom eg = edge3_geom(p);
+            ZT_TRY(dalloc(&w.Eg, cs * (size_t)eg.ngroups * nrhs * p->E, &acc));
+            ZT_TRY(dalloc((void **)&w.cnt, sizeof(unsigned) * (eg.ngroups + 1), &acc));
+            ZT_CUDA(cudaMemset(w.cnt, 0, sizeof(unsigned) * (eg.ngroups + 1)));
+        }
     }
     if (tc || p->side_k > 0) ZT_TRY(dalloc(&w.Yh, cs * nrhs * (size_t)p->F * p->b, &acc));
     w.cap = nrhs;
@@ -661,6 +709,9 @@ template <> const float2 *twy_of<float>(ztoep_plan_t p) { return p->twy32; }
 template <> const double2 *twy_of<double>(ztoep_plan_t p) { return p->twy64; }
 
 static int64_t edge_ldb(int64_t NT) { return (NT + 1023) / 1024 * 1024; }
+// Row stride of the FP32 [B | C]: the N_T + E columns plus one sub-tile of
+// zeros, so k_edge3's 16-byte loads of a sub-tile never leave the row.
+static int64_t edge_ldb32(int64_t NT, int E) { return (NT + E + E3_TW + 1023) / 1024 * 1024; }
 
 // Geometry of an FFT pass along dimension dim (0 = x, 1 = y): the heuristic,
 // or the plan's tuned channel batch and thread count for FP32 passes (the
@@ -819,29 +870,29 @@ static ztoep_status_t launch_edge(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, 
     return ZTOEP_OK;
 }
 
-// FP32 edge coupling without E splits (k_edge2): ET holds B^T x_E directly.
-static ztoep_status_t launch_edge2(ztoep_plan_t p, int nrhs, const float2 *x, float2 *y, MatvecWs &w,
-                                   cudaStream_t s, cudaEvent_t et_ready = nullptr) {
-    float2 *ET = reinterpret_cast<float2 *>(w.ET);
-    float2 *Ep = reinterpret_cast<float2 *>(w.Ep);
-    const int ntile = edge2_ntile(p);
-    const int64_t ldb = edge_ldb(p->NT);
+// FP32 edge coupling (k_edge3): ET holds B^T x_E and y_E = B x_T + C x_E is
+// written by the kernel's last CTA, so the whole branch is one launch per
+// group of up to 4 RHS.
+static ztoep_status_t launch_edge3(ztoep_plan_t p, int nrhs, const float2 *x, float2 *y, MatvecWs &w,
+                                   cudaStream_t s) {
+    const Edge3Geom eg = edge3_geom(p);
+    Edge3Args a{};
+    a.x = x; a.B = p->B32; a.ET = reinterpret_cast<float2 *>(w.ET); a.Ep = reinterpret_cast<float2 *>(w.Ep);
+    a.Eg = reinterpret_cast<float2 *>(w.Eg); a.y = y; a.cnt = w.cnt;
+    a.NT = p->NT; a.ncol = p->NT + p->E; a.ldb = edge_ldb32(p->NT, p->E); a.N = p->N;
+    a.E = p->E; a.nrhs = nrhs; a.range = eg.range; a.G = eg.G; a.ngroups = eg.ngroups;
     for (int r0 = 0; r0 < nrhs; r0 += 4) {
-        const int rc = std::min(4, nrhs - r0);
+        a.r0 = r0;
+        a.rc = std::min(4, nrhs - r0);
         KScope ks(K_EDGE, s);
-        if (rc == 1)
-            k_edge2<1><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc);
-        else if (rc == 2)
-            k_edge2<2><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc);
+        if (a.rc == 1)
+            k_edge3<1><<<eg.G, 256, 0, s>>>(a);
+        else if (a.rc == 2)
+            k_edge3<2><<<eg.G, 256, 0, s>>>(a);
         else
-            k_edge2<4><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ldb, p->E, p->N, nrhs, r0, rc);
+            k_edge3<4><<<eg.G, 256, 0, s>>>(a);
         ZT_CUDA(cudaGetLastError());
     }
-    if (et_ready) ZT_CUDA(cudaEventRecord(et_ready, s));  // ET is final; the finish only writes y_E
-    dim3 gf((p->E + 7) / 8, nrhs);
-    KScope ks(K_MISC, s);
-    k_edge_finish2<<<gf, 256, 0, s>>>(x, p->C32, Ep, y, p->NT, p->E, p->N, nrhs, ntile);
-    ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
 }
 
@@ -853,7 +904,7 @@ static ztoep_status_t tc_edge(ztoep_plan_t p, int nrhs, const float2 *x, float2 
                               cudaEvent_t et_ready = nullptr) {
     const int kc = tc_edge_kchunk(p);
     CgemmArgs g1{};
-    g1.A = p->B32; g1.lda = edge_ldb(p->NT); g1.strideA = 0;
+    g1.A = p->B32; g1.lda = edge_ldb32(p->NT, p->E); g1.strideA = 0;
     g1.X = x; g1.ldx = p->N; g1.strideX = 0;
     g1.C = reinterpret_cast<float2 *>(w.Ep); g1.ldc_q = p->E; g1.ldc_m = 1; g1.strideC = 0;
     g1.strideCk = (int64_t)nrhs * p->E;
@@ -919,8 +970,8 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
             ZT_TRY(tc_edge(p, nrhs, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), w, br,
                            p->ev_et));
         } else if (sizeof(R) == sizeof(float)) {
-            ZT_TRY(launch_edge2(p, nrhs, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), w, br,
-                                p->ev_et));
+            ZT_TRY(launch_edge3(p, nrhs, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), w, br));
+            ZT_CUDA(cudaEventRecord(p->ev_et, br));
         } else {
             ZT_TRY(launch_edge<R>(p, nrhs, x, y, w, br, true));
             ZT_CUDA(cudaEventRecord(p->ev_et, br));
@@ -996,6 +1047,30 @@ void free_matvec_ws(ztoep_plan_t p) {
 }
 
 int64_t edge_row_stride(int64_t NT) { return edge_ldb(NT); }
+int64_t edge_row_stride32(int64_t NT, int E) { return edge_ldb32(NT, E); }
+
+// [B | C] in FP32 from the FP64 B (row stride ldb64) and C: row e holds
+// B[e][0..NT), C[e][0..E), then zeros up to ldb32.
+__global__ void k_pack_bc32(const double2 *__restrict__ B, int64_t ldb64, const double2 *__restrict__ Cm,
+                            float2 *__restrict__ out, int64_t ldb32, int E, int64_t NT) {
+    const int64_t total = (int64_t)E * ldb32;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = k / ldb32, t = k - e * ldb32;
+        double2 v = make_double2(0.0, 0.0);
+        if (t < NT)
+            v = B[e * ldb64 + t];
+        else if (t < NT + E)
+            v = Cm[e * (int64_t)E + (t - NT)];
+        out[k] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+ztoep_status_t pack_bc32(ztoep_plan_t p, cudaStream_t s) {
+    KScope ks(K_MISC, s);
+    k_pack_bc32<<<1024, 256, 0, s>>>(p->B64, edge_ldb(p->NT), p->C64, p->B32, edge_ldb32(p->NT, p->E), p->E, p->NT);
+    ZT_CUDA(cudaGetLastError());
+    return ZTOEP_OK;
+}
 
 }  // namespace ztoep
 
@@ -1047,7 +1122,7 @@ ztoep_status_t ensure_tensor_data(ztoep_plan_t p, int nrhs, cudaStream_t s) {
         ZT_TRY(dalloc((void **)&p->B32T, sizeof(float2) * (size_t)p->NT * p->E, &acc));
         dim3 g((unsigned)((p->NT + 31) / 32), (unsigned)((p->E + 31) / 32));
         KScope ks(K_MISC, s);
-        k_transpose32<<<g, dim3(32, 8), 0, s>>>(p->B32, edge_ldb(p->NT), p->B32T, p->E, p->NT);
+        k_transpose32<<<g, dim3(32, 8), 0, s>>>(p->B32, edge_ldb32(p->NT, p->E), p->B32T, p->E, p->NT);
         ZT_CUDA(cudaGetLastError());
     }
     p->tc_bytes += acc;

@@ -19,6 +19,8 @@ namespace ztoep {
 void free_matvec_ws(ztoep_plan_t p);
 void free_solve_ws(ztoep_plan_t p);
 int64_t edge_row_stride(int64_t NT);
+int64_t edge_row_stride32(int64_t NT, int E);
+ztoep_status_t pack_bc32(ztoep_plan_t p, cudaStream_t s);
 
 bool is_smooth(int n) {
     if (n < 1) return false;
@@ -174,7 +176,7 @@ static size_t plan_bytes(int nx, int ny, int b, int E, int lx, int ly, int side_
     if (side_k > 0)
         s += (size_t)4 * side_k * lx * ly * b * (16 + 8);  // side generator spectra
     else
-        s += (size_t)E * ldb * (16 + 8);
+        s += (size_t)E * ldb * 16 + (size_t)E * edge_row_stride32(NT, E) * 8;
     s += (size_t)E * E * (16 + 8);
     s += (size_t)lx * ly * (sizeof(int) + sizeof(int2)) + (size_t)(lx + ly) * 24 + (size_t)nx * ny + 64;
     return s;
@@ -339,7 +341,7 @@ static ztoep_status_t plan_build(ztoep_plan_t p, const ztoep_desc_t *d, const do
     } else if (p->E > 0) {
         const int64_t ldb = edge_row_stride(p->NT);
         ZT_TRY(dalloc((void **)&p->B64, sizeof(double2) * (size_t)p->E * ldb, &acc));
-        ZT_TRY(dalloc((void **)&p->B32, sizeof(float2) * (size_t)p->E * ldb, &acc));
+        ZT_TRY(dalloc((void **)&p->B32, sizeof(float2) * (size_t)p->E * edge_row_stride32(p->NT, p->E), &acc));
         ZT_TRY(dalloc((void **)&p->C64, sizeof(double2) * (size_t)p->E * p->E, &acc));
         ZT_TRY(dalloc((void **)&p->C32, sizeof(float2) * (size_t)p->E * p->E, &acc));
         ZT_CUDA(cudaMemsetAsync(p->B64, 0, sizeof(double2) * (size_t)p->E * ldb, s));
@@ -350,9 +352,9 @@ static ztoep_status_t plan_build(ztoep_plan_t p, const ztoep_desc_t *d, const do
             k_zero_columns<<<1024, 256, 0, s>>>(p->B64, ldb, p->E, p->active, p->nx * p->ny, p->b);
             ZT_CUDA(cudaGetLastError());
         }
-        ZT_TRY(launch_c128_to_c64(p->B64, p->B32, (int64_t)p->E * ldb, s));
         ZT_CUDA(cudaMemcpyAsync(p->C64, C, sizeof(double2) * (size_t)p->E * p->E, cudaMemcpyDeviceToDevice, s));
         ZT_TRY(launch_c128_to_c64(p->C64, p->C32, (int64_t)p->E * p->E, s));
+        ZT_TRY(pack_bc32(p, s));
     }
     p->resident = acc;
     return ZTOEP_OK;

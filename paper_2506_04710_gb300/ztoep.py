@@ -109,7 +109,7 @@ EXPORTS = ["ztoep_default_opts", "ztoep_plan", "ztoep_matvec", "ztoep_solve", "z
            "ztoep_port_matrices", "ztoep_far_field_grid", "ztoep_solve_schur",
            "ztoep_sched_create", "ztoep_sched_submit", "ztoep_sched_poll", "ztoep_sched_wait",
            "ztoep_sched_get_stats", "ztoep_sched_destroy", "ztoep_plan_autotune", "ztoep_plan_tuned",
-           "ztoep_plan_get_tune"]
+           "ztoep_plan_get_tune", "ztoep_solve_group"]
 
 K_FFT, K_BLOCKPROD, K_EDGE, K_ARNOLDI, K_MISC, K_TENSOR, K_TENSOR_PIPE = range(7)
 ZTOEP_TIMING_SERIAL = 1 << 30  # products run their branches one after another while timed
@@ -135,6 +135,10 @@ def lib(path: str | None = None):
     L.ztoep_solve_host.argtypes = [c_p, ctypes.POINTER(SolveOpts), c_i32, c_p, c_p, ctypes.POINTER(SolveInfo),
                                    c_p]
     L.ztoep_solve_host.restype = c_i32
+    L.ztoep_solve_group.argtypes = [c_i32, ctypes.POINTER(c_p), ctypes.POINTER(SolveOpts), ctypes.POINTER(c_i32),
+                                    ctypes.POINTER(c_p), ctypes.POINTER(c_p),
+                                    ctypes.POINTER(ctypes.POINTER(SolveInfo)), c_p]
+    L.ztoep_solve_group.restype = c_i32
     L.ztoep_forward_spectrum.argtypes = [c_p, c_i32, c_i32, c_p, c_p, c_p]
     L.ztoep_forward_spectrum.restype = c_i32
     L.ztoep_plan_spectrum.argtypes = [c_p, c_p, c_p]
@@ -289,6 +293,21 @@ def ztoep_solve_host(plan, opts: SolveOpts, nrhs: int, V_host, X_host, info=None
     ip = info if info is not None else None
     return lib().ztoep_solve_host(plan, ctypes.byref(opts), nrhs, _hptr(V_host), _hptr(X_host), ip,
                                   _stream_ptr(stream))
+
+
+def ztoep_solve_group(plans, opts: SolveOpts, V, X, infos=None, stream=None) -> int:
+    """One solve of several systems (plans of any sizes): V[i], X[i] device
+    complex128 [nrhs_i][N_i]; infos[i] an info_array(nrhs_i) or None."""
+    n = len(plans)
+    P = (c_p * n)(*[c_p(p) for p in plans])
+    R = (c_i32 * n)(*[int(v.shape[0]) for v in V])
+    VP = (c_p * n)(*[_dptr(v) for v in V])
+    XP = (c_p * n)(*[_dptr(x) for x in X])
+    IP = None
+    if infos is not None:
+        IP = (ctypes.POINTER(SolveInfo) * n)(*[ctypes.cast(i, ctypes.POINTER(SolveInfo)) if i is not None
+                                               else ctypes.POINTER(SolveInfo)() for i in infos])
+    return lib().ztoep_solve_group(n, P, ctypes.byref(opts), R, VP, XP, IP, _stream_ptr(stream))
 
 
 def ztoep_forward_spectrum(plan, prec: int, nrhs: int, X, Xhat, stream=None) -> int:

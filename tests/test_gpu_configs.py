@@ -94,6 +94,18 @@ def test_c2_solve_config_rhs_and_manufactured(c2, prec):
     assert err <= 1e-7
 
 
+def test_products_sampled_rows_wide_edge_ranges():
+    """40x40 b64 array with 640 edge unknowns: more columns of [B | C] than
+    one 128-column sub-tile per CTA of the FP32 edge kernel covers, so each CTA
+    accumulates its row partials over two sub-tiles; 1 and 3 RHS."""
+    prob = synth.make_problem(40, 40, 64, 640, seed=8, rhs="planewave", nrhs=3)
+    plan = ztoep.Plan.from_problem(prob)
+    rows = sample_rows(prob, 200)
+    for r in (1, 3):
+        check_products_sampled(prob, plan, rows, prob.V[:r])
+    plan.close()
+
+
 @pytest.fixture(scope="module")
 def c3():
     prob, tol = synth.config_problem("c3_19x9gap_b48")

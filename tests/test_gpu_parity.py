@@ -38,6 +38,8 @@ CASES = {
     "7x6_b12_e20": dict(nx=7, ny=6, b=12, n_edge=20, rhs="planewave", nrhs=5, seed=9),
     "9x4_b40_e24": dict(nx=9, ny=4, b=40, n_edge=24, rhs="planewave", nrhs=6, seed=13),
     "6x6_b33_e0_gap": dict(nx=6, ny=6, b=33, n_edge=0, gap_column=3, rhs="planewave", nrhs=2, seed=17),
+    # more edge rows than the FP32 edge kernel stages at once (1024)
+    "6x5_b4_e1100": dict(nx=6, ny=5, b=4, n_edge=1100, rhs="planewave", nrhs=3, seed=19),
 }
 
 
@@ -204,11 +206,10 @@ def test_batch_equals_alone_bitwise():
 
 
 def test_batch_equals_alone_across_reduction_modes():
-    """20x20 b96 (N = 38,720, 152 chunks of 256): one RHS alone reduces the
-    Gram-Schmidt partial sums redundantly in every update CTA, a batch of 12
-    (12 x 152^2 > 2^18) in the dots' last CTA per RHS; both sum in the same
-    order, so each solution is bitwise the same, in both precisions, and the
-    batch meets the tolerance against the oracle."""
+    """20x20 b96 (N = 38,720: as many chunks as SMs, two-level Gram-Schmidt
+    reductions over ten groups): one RHS alone and in a batch of 12 sum in
+    the same order, so each solution is bitwise the same, in both precisions,
+    and the batch meets the tolerance against the oracle."""
     prob = synth.make_problem(20, 20, 96, 320, seed=5, rhs="planewave", nrhs=12)
     plan = ztoep.Plan.from_problem(prob)
     V = dev(prob.V)
