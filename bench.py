@@ -432,6 +432,11 @@ def run_ours(args, world, rank, local):
             clocks = Clocks(gid)
             mixed = serve_stream(args, "mixed", args.serve_requests, dev)
             clk = clocks.stop()
+            grouped = None
+            if args.serve_group_max > 1:  # the same requests, grouped solves
+                clocks = Clocks(gid)
+                grouped = serve_stream(args, "mixed", args.serve_requests, dev, group_max=args.serve_group_max)
+                grouped["clocks"] = clocks.stop()
             unique = None
             if args.serve_unique > 0:
                 clocks = Clocks(gid)
@@ -443,7 +448,8 @@ def run_ours(args, world, rank, local):
                 fp64s = serve_stream(args, "fp64", args.serve_fp64, dev)
                 fp64s["clocks"] = clocks.stop()
             sections["serve"] = {"workload": SERVE_DESC, "mixed": mixed, "clocks": clk,
-                                 "mixed_unique_designs": unique, "fp64_plain_prefix": fp64s}
+                                 "mixed_grouped": grouped, "mixed_unique_designs": unique,
+                                 "fp64_plain_prefix": fp64s}
             torch.cuda.empty_cache()
         sections["libs"] = section_libs(dev, stream, libs_cases)
 
@@ -794,7 +800,7 @@ SERVE_DESC = ("Poisson stream, mean 50 requests/s: square arrays Nx=Ny ~ U{8..48
               "E = 16 Nx, 1-64 plane-wave RHS, 4 element designs (seeds); solved to rel. residual 1e-8")
 
 
-def serve_stream(args, prec_name, n_req, dev, designs=4):
+def serve_stream(args, prec_name, n_req, dev, designs=4, group_max=1):
     """Replays the first n_req requests of the stream at their arrival times
     through the scheduler.  Inputs are generated on the device by the client
     ahead of arrival (bounded by --serve-input-gb of unconsumed inputs) and
@@ -805,7 +811,7 @@ def serve_stream(args, prec_name, n_req, dev, designs=4):
     reqs = synth.serving_requests(n=n_req, rate=50.0, seed=0, designs=designs)
     prec = ztoep.ZTOEP_MIXED if prec_name == "mixed" else ztoep.ZTOEP_FP64
     sched = ztoep.Scheduler(hbm_budget=int(args.serve_budget_gb * 2**30), workers=args.serve_workers,
-                            device=dev.index or 0)
+                            device=dev.index or 0, group_max=group_max)
     gen = torch.cuda.Stream(dev)
     cap = args.serve_input_gb * 2**30
     live = {}  # rid -> input bytes still held
@@ -871,7 +877,8 @@ def serve_stream(args, prec_name, n_req, dev, designs=4):
             "max_in_flight": int(stats.max_in_flight), "peak_bytes": int(stats.peak_bytes),
             "plans_built": int(stats.plans_built), "plans_reused": int(stats.plans_reused),
             "plans_evicted": int(stats.plans_evicted), "gpu_launches": int(launches),
-            "workers": args.serve_workers, "budget_gb": args.serve_budget_gb}
+            "workers": args.serve_workers, "budget_gb": args.serve_budget_gb,
+            "group_max": group_max, "grouped_solves": int(stats.groups)}
 
 
 def run_serve(args, world, rank, local):
@@ -891,12 +898,14 @@ def run_serve(args, world, rank, local):
     serve_stream(args, "mixed", 4, dev)  # warm-up: library, generator, allocator
     clocks = Clocks(gpu_id)
     mixed = serve_stream(args, "mixed", args.serve, dev)
+    grouped = (serve_stream(args, "mixed", args.serve, dev, group_max=args.serve_group_max)
+               if args.serve_group_max > 1 else None)
     fp64 = serve_stream(args, "fp64", args.serve_fp64, dev) if args.serve_fp64 > 0 else None
     clk = clocks.stop()
     line = {"metric": METRIC, "mode": "serving", "value": mixed["rhs_solves_per_s"], "unit": "RHS solves/s",
             "higher_is_better": True, "n_gpus": 1, "dtype": "c64 products + f64 refinement",
             "data": "synthetic", "config": {"workload": SERVE_DESC, "requests": args.serve},
-            "mixed": mixed, "fp64_plain": fp64, "clocks": clk}
+            "mixed": mixed, "mixed_grouped": grouped, "fp64_plain": fp64, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
@@ -1119,6 +1128,8 @@ def main():
                     help="serving mode: replay this many requests of the Poisson stream")
     ap.add_argument("--serve-fp64", type=int, default=6, help="requests replayed through the FP64 path")
     ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-group-max", type=int, default=4,
+                    help="also replay the requests with up to this many per grouped solve (1: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
     ap.add_argument("--serve-input-gb", type=float, default=32.0)
     ap.add_argument("--product-only", action="store_true",

@@ -417,7 +417,9 @@ ZTOEP_API const char *ztoep_version(void);
  * admitted requests run concurrently, so their kernels overlap on the device.
  * Plans (the FFT'd generating blocks, B and C) stay resident under their
  * plan_key and are reused by later requests with the same key; idle ones are
- * evicted least-recently-used when the budget requires.  Each request gets
+ * evicted least-recently-used when the budget requires.  With group_max > 1
+ * a worker takes the queue head together with the requests right behind it
+ * that can share one grouped solve (ztoep_solve_group).  Each request gets
  * exactly the arithmetic of a ztoep_solve of the same request alone. */
 typedef struct ztoep_sched_s *ztoep_sched_t;
 
@@ -427,6 +429,10 @@ typedef struct {
     int32_t device;      /* CUDA device index */
     int32_t fake_backend;/* 1: no CUDA work; each request sleeps fake_us (host-logic tests) */
     int64_t fake_us;
+    int32_t group_max;   /* up to this many queued requests (0..8; 0 and 1 = one at a time) that
+                            follow each other in arrival order, have device inputs, equal options,
+                            plans of their own and sizes within a factor 4 run as one
+                            ztoep_solve_group; a group completes when its last member converges */
 } ztoep_sched_opts_t;
 
 typedef struct {
@@ -456,6 +462,7 @@ typedef struct {
     int64_t submitted, completed, max_in_flight;
     size_t bytes_in_use, peak_bytes, resident_plan_bytes;
     int64_t plans_built, plans_reused, plans_evicted;
+    int64_t groups;      /* grouped solves run (two or more requests) */
 } ztoep_sched_stats_t;
 
 /* Errors: ARG (bad options), CUDA. */

@@ -10,8 +10,10 @@
 // arrives while others run starts as soon as a worker and memory free up.
 // The queue is FIFO (only its head is considered, so large requests are not
 // starved).  Every request runs exactly the ztoep_solve it would run alone.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <memory>
 #include <mutex>
@@ -61,8 +63,9 @@ struct ztoep_sched_s {
     bool stop = false;
     int64_t next_id = 1, submitted = 0, completed = 0, in_flight = 0, max_in_flight = 0;
     size_t bytes_work = 0, peak = 0;
-    int64_t built = 0, reused = 0, evicted = 0;
+    int64_t built = 0, reused = 0, evicted = 0, groups = 0;
     uint64_t tick = 0;
+    int nsm = 152;  // SM count of the device (chunk shapes of the grouped solve)
     // Plans evicted under mu, destroyed by a worker after it releases mu:
     // ztoep_plan_destroy frees device memory, and cudaFree can wait for the
     // whole device, which must not block the other workers' bookkeeping.
@@ -102,52 +105,32 @@ struct ztoep_sched_s {
         }
     }
 
-    void run(Req *q, cudaStream_t s) {
+    // Plan of a request: the resident one of its key, or a new build from its
+    // inputs (device inputs directly, host inputs through stream-ordered
+    // staging).  Sets q->consumed once T, B and C are no longer read.
+    ztoep_status_t acquire(Req *q, cudaStream_t s, ztoep_plan_t *out, bool *from_cache) {
         ztoep_request_t &r = q->r;
-        if (o.fake_backend) {  // host logic only: no device work, plans are bookkeeping entries
-            std::this_thread::sleep_for(std::chrono::microseconds(o.fake_us));
-            std::lock_guard<std::mutex> lk(mu);
-            q->status = ZTOEP_OK;
-            q->consumed = 1;
-            if (r.plan_key) {
-                auto it = plans.find(r.plan_key);
-                if (it != plans.end()) {
-                    ++reused;
-                    q->reused = 1;
-                } else {
-                    ++built;
-                    CachedPlan cp;
-                    cp.bytes = q->fp / 2;
-                    plans.emplace(r.plan_key, cp);
-                    it = plans.find(r.plan_key);
-                }
-                it->second.refs++;
-                q->holds_ref = true;
-            }
-            return;
-        }
-        cudaSetDevice(o.device);
         ztoep_plan_t plan = nullptr;
-        bool from_cache = false;
+        *from_cache = false;
         {
             std::lock_guard<std::mutex> lk(mu);
             if (r.plan_key) {
                 auto it = plans.find(r.plan_key);
                 if (it != plans.end()) {
                     plan = it->second.plan;
-                    from_cache = true;
+                    *from_cache = true;
                     it->second.refs++;  // not evictable while this request uses it
                     q->holds_ref = true;
+                    q->consumed = 1;
                 }
             }
         }
         ztoep_status_t st = ZTOEP_OK;
-        if (plan) {
-            std::lock_guard<std::mutex> lk(mu);
-            q->consumed = 1;
-        } else {
+        if (!plan) {
             if (r.inputs_on_device) {
                 st = ztoep_plan(&r.desc, r.T, r.B, r.C, s, &plan);
+                // ztoep_plan is stream-ordered: the blocks are read once the stream passes it
+                if (st == ZTOEP_OK) cudaStreamSynchronize(s);
             } else {  // stage the host blocks on the device for the plan build
                 const int64_t nt = (int64_t)r.desc.nx * r.desc.ny * r.desc.b, e = r.desc.n_edge;
                 const size_t tb = sizeof(double2) * (size_t)(2 * r.desc.ny - 1) * (2 * r.desc.nx - 1) * r.desc.b * r.desc.b;
@@ -163,7 +146,6 @@ struct ztoep_sched_s {
                         cudaMemcpyAsync(dC, r.C, cb, cudaMemcpyHostToDevice, s);
                     }
                     st = ztoep_plan(&r.desc, dT, dB, dC, s, &plan);
-                    cudaStreamSynchronize(s);
                 } else {
                     cudaGetLastError();
                     st = ZTOEP_ERR_NOMEM;
@@ -173,40 +155,158 @@ struct ztoep_sched_s {
                 if (dC) cudaFreeAsync(dC, s);
                 cudaStreamSynchronize(s);
             }
-        }
-        if (!from_cache) {
-            // ztoep_plan is stream-ordered: the blocks are read once the stream passes it
-            if (st == ZTOEP_OK && r.inputs_on_device) cudaStreamSynchronize(s);
             std::lock_guard<std::mutex> lk(mu);
             q->consumed = 1;
         }
-        if (st == ZTOEP_OK) {
-            ztoep_solve_opts_t so = r.opts;
-            so.flags |= ZTOEP_FLAG_ZERO_GUESS;
-            st = r.inputs_on_device ? ztoep_solve(plan, &so, r.nrhs, r.V, r.X, r.info, s)
-                                    : ztoep_solve_host(plan, &so, r.nrhs, r.V, r.X, r.info, s);
-            cudaStreamSynchronize(s);
-        }
-        q->status = st;
+        *out = plan;
+        return st;
+    }
+
+    // After the solve: a new plan joins the resident set under its key (or is
+    // destroyed); statistics.
+    void release(Req *q, ztoep_plan_t plan, bool from_cache) {
         q->reused = from_cache ? 1 : 0;
         std::lock_guard<std::mutex> lk(mu);
         if (from_cache) {
             ++reused;
         } else if (plan) {
             ++built;
-            if (r.plan_key && plans.find(r.plan_key) == plans.end()) {
+            if (q->r.plan_key && plans.find(q->r.plan_key) == plans.end()) {
                 ztoep_plan_info_t pi{};
                 ztoep_plan_get_info(plan, &pi);
                 CachedPlan cp;
                 cp.plan = plan;
                 cp.bytes = pi.resident_bytes;
                 cp.refs = 1;  // released when the request completes
-                plans.emplace(r.plan_key, cp);
+                plans.emplace(q->r.plan_key, cp);
                 q->holds_ref = true;
             } else {
                 ztoep_plan_destroy(plan);
             }
         }
+    }
+
+    // Host logic only: no device work, plans are bookkeeping entries.
+    void run_fake(const std::vector<Req *> &grp) {
+        std::this_thread::sleep_for(std::chrono::microseconds(o.fake_us));
+        std::lock_guard<std::mutex> lk(mu);
+        for (Req *q : grp) {
+            ztoep_request_t &r = q->r;
+            q->status = ZTOEP_OK;
+            q->consumed = 1;
+            if (!r.plan_key) continue;
+            auto it = plans.find(r.plan_key);
+            if (it != plans.end()) {
+                ++reused;
+                q->reused = 1;
+            } else {
+                ++built;
+                CachedPlan cp;
+                cp.bytes = q->fp / 2;
+                plans.emplace(r.plan_key, cp);
+                it = plans.find(r.plan_key);
+            }
+            it->second.refs++;
+            q->holds_ref = true;
+        }
+    }
+
+    // One request alone (ztoep_solve / ztoep_solve_host), or several device-
+    // input requests as one grouped solve (ztoep_solve_group: one launch per
+    // step for all of them, each with exactly its solve-alone arithmetic).
+    void run(const std::vector<Req *> &grp, cudaStream_t s) {
+        if (o.fake_backend) {
+            run_fake(grp);
+            return;
+        }
+        cudaSetDevice(o.device);
+        const int n = (int)grp.size();
+        std::vector<ztoep_plan_t> pl(n, nullptr);
+        std::vector<char> cached(n, 0);
+        std::vector<ztoep_status_t> ast(n, ZTOEP_OK);
+        for (int i = 0; i < n; ++i) {
+            bool fc = false;
+            ast[i] = acquire(grp[i], s, &pl[i], &fc);
+            cached[i] = fc;
+        }
+        ztoep_solve_opts_t so = grp[0]->r.opts;
+        so.flags |= ZTOEP_FLAG_ZERO_GUESS;
+        if (n == 1) {
+            ztoep_request_t &r = grp[0]->r;
+            ztoep_status_t st = ast[0];
+            if (st == ZTOEP_OK) {
+                st = r.inputs_on_device ? ztoep_solve(pl[0], &so, r.nrhs, r.V, r.X, r.info, s)
+                                        : ztoep_solve_host(pl[0], &so, r.nrhs, r.V, r.X, r.info, s);
+                cudaStreamSynchronize(s);
+            }
+            grp[0]->status = st;
+        } else {
+            // members whose plan failed are solved by nobody and report that error
+            std::vector<ztoep_plan_t> gp;
+            std::vector<int32_t> gr;
+            std::vector<const void *> gv;
+            std::vector<void *> gx;
+            std::vector<std::vector<ztoep_solve_info_t>> tmp(n);
+            std::vector<ztoep_solve_info_t *> gi;
+            std::vector<int> idx;
+            for (int i = 0; i < n; ++i) {
+                if (ast[i] != ZTOEP_OK) continue;
+                ztoep_request_t &r = grp[i]->r;
+                tmp[i].assign(r.nrhs, ztoep_solve_info_t{});
+                gp.push_back(pl[i]);
+                gr.push_back(r.nrhs);
+                gv.push_back(r.V);
+                gx.push_back(r.X);
+                gi.push_back(tmp[i].data());
+                idx.push_back(i);
+            }
+            ztoep_status_t gst = ZTOEP_OK;
+            if (!gp.empty()) {
+                gst = ztoep_solve_group((int32_t)gp.size(), gp.data(), &so, gr.data(), gv.data(), gx.data(),
+                                        gi.data(), s);
+                cudaStreamSynchronize(s);
+            }
+            for (int i = 0; i < n; ++i) grp[i]->status = ast[i];
+            for (int k = 0; k < (int)idx.size(); ++k) {
+                Req *q = grp[idx[k]];
+                ztoep_status_t st = ZTOEP_OK;
+                if (gst == ZTOEP_ERR_ARG || gst == ZTOEP_ERR_CUDA || gst == ZTOEP_ERR_NOMEM ||
+                    gst == ZTOEP_ERR_UNSUPPORTED) {
+                    st = gst;
+                } else {
+                    for (const ztoep_solve_info_t &in : tmp[idx[k]])
+                        if (in.status != ZTOEP_OK && (st == ZTOEP_OK || in.status == ZTOEP_ERR_NONFINITE ||
+                                                      in.status == ZTOEP_ERR_TIMEOUT))
+                            st = (ztoep_status_t)in.status;
+                }
+                q->status = st;
+                if (q->r.info) std::memcpy(q->r.info, tmp[idx[k]].data(), sizeof(ztoep_solve_info_t) * q->r.nrhs);
+            }
+        }
+        for (int i = 0; i < n; ++i) release(grp[i], pl[i], cached[i] != 0);
+    }
+
+    // Can request c join the group grp (in one grouped solve)?  Device
+    // inputs, the same options, a plan of its own, the same chunk shape of
+    // the solver's kernels, and a size within a factor 4 of the first one's
+    // (the group runs until its slowest member converges).
+    bool groupable(const std::vector<Req *> &grp, const Req *c) const {
+        const ztoep_request_t &a = grp[0]->r, &b = c->r;
+        if (!o.fake_backend && (!a.inputs_on_device || !b.inputs_on_device)) return false;
+        if (a.opts.tol != b.opts.tol || a.opts.restart != b.opts.restart || a.opts.max_iter != b.opts.max_iter ||
+            a.opts.max_outer != b.opts.max_outer || a.opts.prec != b.opts.prec ||
+            a.opts.inner_tol != b.opts.inner_tol || a.opts.timeout_ns != b.opts.timeout_ns ||
+            a.opts.flags != b.opts.flags)
+            return false;
+        for (const Req *g : grp)
+            if (b.plan_key && g->r.plan_key == b.plan_key) return false;
+        auto n_of = [](const ztoep_request_t &r) {
+            return (double)r.desc.nx * r.desc.ny * r.desc.b + r.desc.n_edge;
+        };
+        auto big = [&](const ztoep_request_t &r) { return (n_of(r) + 255) / 256 >= 8.0 * nsm; };
+        if (big(a) != big(b)) return false;
+        const double ca = n_of(a) * a.nrhs, cb = n_of(b) * b.nrhs;
+        return cb <= 4 * ca && ca <= 4 * cb;
     }
 
     void worker() {
@@ -215,41 +315,54 @@ struct ztoep_sched_s {
             cudaSetDevice(o.device);
             cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
         }
+        const size_t gmax = (size_t)std::max(1, std::min(o.group_max, 8));
         for (;;) {
-            Req *q = nullptr;
+            std::vector<Req *> grp;
             std::vector<ztoep_plan_t> victims;
             {
                 std::unique_lock<std::mutex> lk(mu);
                 cv_work.wait(lk, [&] { return (stop && queue.empty()) || (!queue.empty() && try_admit(queue.front())); });
-                victims.swap(doomed);
                 if (queue.empty()) {
+                    victims.swap(doomed);
                     lk.unlock();
                     for (ztoep_plan_t v : victims) ztoep_plan_destroy(v);
                     break;
                 }
-                q = queue.front();
+                grp.push_back(queue.front());
                 queue.pop_front();
-                q->state = 1;
-                q->t_start = Clock::now();
-                ++in_flight;
+                // the next requests in arrival order join while they fit
+                while (grp.size() < gmax && !queue.empty() && groupable(grp, queue.front()) &&
+                       try_admit(queue.front())) {
+                    grp.push_back(queue.front());
+                    queue.pop_front();
+                }
+                victims.swap(doomed);
+                for (Req *q : grp) {
+                    q->state = 1;
+                    q->t_start = Clock::now();
+                    ++in_flight;
+                }
                 max_in_flight = std::max(max_in_flight, in_flight);
+                if (grp.size() > 1) ++groups;
             }
             for (ztoep_plan_t v : victims) ztoep_plan_destroy(v);  // outside mu
-            run(q, s);
+            run(grp, s);
             {
                 std::lock_guard<std::mutex> lk(mu);
-                bytes_work -= q->fp;
-                if (q->holds_ref) {
-                    auto it = plans.find(q->r.plan_key);
-                    if (it != plans.end()) {
-                        it->second.refs--;
-                        it->second.last_use = ++tick;
+                for (Req *q : grp) {
+                    bytes_work -= q->fp;
+                    if (q->holds_ref) {
+                        auto it = plans.find(q->r.plan_key);
+                        if (it != plans.end()) {
+                            it->second.refs--;
+                            it->second.last_use = ++tick;
+                        }
                     }
+                    --in_flight;
+                    ++completed;
+                    q->t_done = Clock::now();
+                    q->state = 2;
                 }
-                --in_flight;
-                ++completed;
-                q->t_done = Clock::now();
-                q->state = 2;
             }
             cv_done.notify_all();
             cv_work.notify_all();
@@ -261,7 +374,9 @@ struct ztoep_sched_s {
 extern "C" {
 
 ztoep_status_t ztoep_sched_create(const ztoep_sched_opts_t *o, ztoep_sched_t *out) {
-    if (!o || !out || o->workers < 1 || o->workers > 64 || o->hbm_budget == 0 || o->fake_us < 0) return ZTOEP_ERR_ARG;
+    if (!o || !out || o->workers < 1 || o->workers > 64 || o->hbm_budget == 0 || o->fake_us < 0 || o->group_max < 0 ||
+        o->group_max > 8)
+        return ZTOEP_ERR_ARG;
     *out = nullptr;
     auto *s = new (std::nothrow) ztoep_sched_s();
     if (!s) return ZTOEP_ERR_NOMEM;
@@ -270,6 +385,7 @@ ztoep_status_t ztoep_sched_create(const ztoep_sched_opts_t *o, ztoep_sched_t *ou
         delete s;
         return ZTOEP_ERR_CUDA;
     }
+    if (!o->fake_backend) cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, o->device);
     for (int i = 0; i < o->workers; ++i) s->threads.emplace_back([s] { s->worker(); });
     *out = s;
     return ZTOEP_OK;
@@ -350,6 +466,7 @@ ztoep_status_t ztoep_sched_get_stats(ztoep_sched_t s, ztoep_sched_stats_t *st) {
     st->plans_built = s->built;
     st->plans_reused = s->reused;
     st->plans_evicted = s->evicted;
+    st->groups = s->groups;
     return ZTOEP_OK;
 }
 

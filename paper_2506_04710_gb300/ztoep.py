@@ -76,7 +76,7 @@ class TuneInfo(ctypes.Structure):
 
 class SchedOpts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("workers", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("fake_backend", ctypes.c_int32), ("fake_us", ctypes.c_int64)]
+                ("fake_backend", ctypes.c_int32), ("fake_us", ctypes.c_int64), ("group_max", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -95,7 +95,7 @@ class SchedStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("max_in_flight", ctypes.c_int64),
                 ("bytes_in_use", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
                 ("resident_plan_bytes", ctypes.c_size_t), ("plans_built", ctypes.c_int64),
-                ("plans_reused", ctypes.c_int64), ("plans_evicted", ctypes.c_int64)]
+                ("plans_reused", ctypes.c_int64), ("plans_evicted", ctypes.c_int64), ("groups", ctypes.c_int64)]
 
 
 _lib = None
@@ -299,7 +299,7 @@ def ztoep_solve_group(plans, opts: SolveOpts, V, X, infos=None, stream=None) -> 
     """One solve of several systems (plans of any sizes): V[i], X[i] device
     complex128 [nrhs_i][N_i]; infos[i] an info_array(nrhs_i) or None."""
     n = len(plans)
-    P = (c_p * n)(*[c_p(p) for p in plans])
+    P = (c_p * n)(*[p.value if isinstance(p, c_p) else p for p in plans])
     R = (c_i32 * n)(*[int(v.shape[0]) for v in V])
     VP = (c_p * n)(*[_dptr(v) for v in V])
     XP = (c_p * n)(*[_dptr(x) for x in X])
@@ -429,8 +429,9 @@ class Scheduler:
     """Owner of a serving scheduler; keeps every submitted request's buffers
     alive until the request is done."""
 
-    def __init__(self, hbm_budget: int, workers: int = 4, device: int = 0, fake_us: int | None = None):
-        o = SchedOpts(hbm_budget, workers, device, 1 if fake_us is not None else 0, fake_us or 0)
+    def __init__(self, hbm_budget: int, workers: int = 4, device: int = 0, fake_us: int | None = None,
+                 group_max: int = 1):
+        o = SchedOpts(hbm_budget, workers, device, 1 if fake_us is not None else 0, fake_us or 0, group_max)
         self.handle = ztoep_sched_create(o)
         self._keep = {}
 

@@ -54,6 +54,11 @@ def test_host_only_calls(lib):
     assert ztoep.ztoep_footprint(bad, 1, 30) == 0
     bad2, _ = ztoep.make_desc(4, 4, 8, 0, lx=6)  # 6 < 2*4-1
     assert ztoep.ztoep_footprint(bad2, 1, 30) == 0
+    # grouped solve: bad counts are rejected before any device work
+    assert ztoep.lib().ztoep_solve_group(0, None, ctypes.byref(o), None, None, None, None, None) == ztoep.ZTOEP_ERR_ARG
+    nine = ctypes.c_void_p(1)
+    assert ztoep.lib().ztoep_solve_group(9, (ctypes.c_void_p * 9)(*[nine] * 9), ctypes.byref(o),
+                                         (ctypes.c_int32 * 9)(*[1] * 9), None, None, None, None) == ztoep.ZTOEP_ERR_ARG
 
 
 def test_structs_match_header_layout(tmp_path):

@@ -130,3 +130,25 @@ def test_stream_shaped_requests_against_oracle():
             assert oracle.relres(Z, Xh, p.V).max() <= o.tol
     assert s.stats().max_in_flight >= 2
     s.close()
+
+
+def test_grouped_solves_equal_alone():
+    """group_max = 4, one worker: consecutive compatible requests (device
+    inputs, sizes within a factor 4) run as grouped solves; each result is
+    bitwise the one of the request solved alone."""
+    shapes = [(6, 16, 24, 3, 31), (7, 16, 28, 2, 32), (6, 24, 24, 4, 33), (5, 16, 20, 3, 34), (8, 12, 32, 2, 35)]
+    probs = [synth.make_problem(nx, nx, b, e, seed=sd, rhs="planewave", nrhs=r) for nx, b, e, r, sd in shapes]
+    s = ztoep.Scheduler(hbm_budget=16 << 30, workers=1, group_max=4)
+    subs = []
+    for p in probs:
+        T, B, C, V = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (p.T, p.B, p.C, p.V))
+        X = torch.zeros_like(V)
+        subs.append((s.submit((p.nx, p.ny, p.b, p.n_edge), T, B, C, V, X, opts=opts(), on_device=True), p, X))
+    for rid, p, X in subs:
+        rc, st, info = s.wait(rid, 120000)
+        assert rc == 0 and st.status == 0
+        assert max(i["rel_residual"] for i in info) <= 1e-8
+        Xa, _ = alone(p)
+        assert torch.equal(X.cpu(), Xa)
+    assert s.stats().groups >= 1
+    s.close()

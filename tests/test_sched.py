@@ -1,5 +1,7 @@
 """Host logic of the serving scheduler (admission by device-memory footprint,
 FIFO order, resident-plan cache and eviction) with the fake backend: no GPU."""
+import time
+
 import numpy as np
 import pytest
 
@@ -100,4 +102,43 @@ def test_inputs_released_once_consumed():
     assert s.drop_inputs(a) and s.drop_inputs(b)
     assert s._keep[b][1] is None and s._keep[b][4] is not None  # V, X kept
     assert s.poll(b).inputs_consumed == 1
+    s.close()
+
+
+def test_grouping_takes_consecutive_compatible_requests():
+    """group_max = 4 with one worker: the head and the three compatible
+    requests behind it run as one group; a request with a key already in the
+    group (its plan would be shared) ends the group, FIFO order is kept."""
+    s = ztoep.Scheduler(hbm_budget=1 << 40, workers=1, fake_us=20000, group_max=4)
+    t0 = time.perf_counter()
+    subs = [(submit(s, 8, 32, 64, 1), time.perf_counter())]  # runs alone: taken before the rest is queued
+    for k in (11, 12, 13, 14, 14, 15):
+        subs.append((submit(s, 8, 32, 64, 2, key=k), time.perf_counter()))
+    states = [s.wait(i, 10000)[1] for i, _ in subs]
+    assert all(st.state == 2 and st.status == 0 for st in states)
+    st = s.stats()
+    assert st.completed == 7 and st.groups >= 1
+    # FIFO: start times (submission + time queued) never go back in arrival order
+    starts = [1e3 * (t - t0) + x.queue_ms for (_, t), x in zip(subs, states)]
+    assert all(b >= a - 1.0 for a, b in zip(starts, starts[1:]))
+    s.close()
+
+
+def test_grouping_respects_size_ratio_and_budget():
+    fp = fp_of(16, 32, 256, 8)
+    s = ztoep.Scheduler(hbm_budget=int(2.5 * fp), workers=1, fake_us=10000, group_max=8)
+    ids = [submit(s, 16, 32, 256, 8) for _ in range(6)]
+    for i in ids:
+        assert s.wait(i, 10000)[0] == 0
+    st = s.stats()
+    assert st.max_in_flight <= 2 and st.peak_bytes <= int(2.5 * fp)
+    s.close()
+    # a request over 4x the head's size does not join its group
+    s = ztoep.Scheduler(hbm_budget=1 << 40, workers=1, fake_us=10000, group_max=8)
+    a = submit(s, 8, 32, 64, 1)
+    b = submit(s, 8, 32, 64, 1)
+    c = submit(s, 8, 32, 64, 64)
+    for i in (a, b, c):
+        assert s.wait(i, 10000)[0] == 0
+    assert s.stats().max_in_flight <= 2
     s.close()
