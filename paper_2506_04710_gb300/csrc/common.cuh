@@ -197,6 +197,7 @@ struct ztoep_plan_s {
     ztoep::SolveGraph graphs[4];    // small cache of instantiated solve graphs
     int graph_next = 0;
     cudaStream_t side = nullptr;    // edge-coupling branch of the matvec
+    cudaStream_t aux = nullptr;     // solve graph branch beside the product (Givens rotations of the last column)
     cudaStream_t cap = nullptr;     // stream used to capture solve graphs
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev_et = nullptr;    // edge branch: B^T x_E complete (the rest of the branch may still run)

@@ -32,10 +32,13 @@
 namespace ztoep {
 
 enum { ST_ACTIVE = 0, ST_JLEN = 1, ST_ITERS = 2, ST_STATUS = 3, ST_OUTER = 4, ST_PENDING = 5, ST_REORTH = 6,
-       ST_INNER = 7, ST_RESTARTS = 8, ST_END = 9, ST_STRIDE = 12 };
+       ST_INNER = 7, ST_RESTARTS = 8, ST_END = 9, ST_COLUMN = 10, ST_STRIDE = 12 };
 // ST_END: the column just finalised ends the cycle; the iteration control
 // turns it into ACTIVE = 0, PENDING = 1 once every kernel of the step is done
 // (the Arnoldi kernels of the step test ACTIVE, so it must not change under them).
+// ST_COLUMN: Hessenberg column ctl->j - 1 is orthogonalised (its entries and
+// beta stored) and waits for its Givens rotations, which run beside the next
+// step's product.
 enum { RS_RUNNING = 0, RS_CONVERGED = 1, RS_NONFINITE = 2, RS_MAXITER = 3 };
 enum { NM_VNORM = 0, NM_TARGET = 2, NM_RNORM = 3, NM_W0 = 5, NM_RIN = 6, NM_STRIDE = 8 };
 // Inner (FP32-residual) restarts of one sweep: at most this many, and they stop
@@ -190,37 +193,44 @@ __device__ __forceinline__ double block_sum1(double v, double *red) {
     return s;
 }
 
-// sum_{i < n} src[i * stride] in i order (n <= 16 loads in flight at a time).
-__device__ __forceinline__ double2 ordered_sum(const double2 *src, int n, int64_t stride) {
-    double2 s = make_double2(0, 0);
-    int i = 0;
-    for (; i + 16 <= n; i += 16) {
-        double2 v[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = __ldcg(src + (int64_t)(i + q) * stride);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) s = s + v[q];
+// out[k] = sum_{i < n} src[i * stride + k] for k < K, whole CTA: each
+// thread first adds a contiguous run of rows in order (one row when
+// n <= blockDim), then a pairwise tree over the runs through shared memory
+// `scr` (blockDim entries).  The order depends only on n, K and blockDim, and
+// the dependent FP64 chain is about log2(n) adds long.
+__device__ void tree_sum(const double2 *src, int n, int64_t stride, int K, double2 *out, double2 *scr) {
+    int P = 1;
+    while (P < n && P < (int)blockDim.x) P <<= 1;
+    const int run = (n + P - 1) / P;
+    const int per = blockDim.x / P;  // columns per pass
+    const int i = threadIdx.x % P, kk = threadIdx.x / P;
+    for (int kb = 0; kb < K; kb += per) {
+        const int k = kb + kk;
+        double2 v = make_double2(0, 0);
+        if (k < K && kk < per) {
+            const int r0 = i * run, r1 = min(n, r0 + run);
+            for (int r = r0; r < r1; ++r) v = v + __ldcg(src + (int64_t)r * stride + k);
+        }
+        scr[threadIdx.x] = v;
+        __syncthreads();
+        for (int h = P >> 1; h > 0; h >>= 1) {
+            if (i < h) scr[threadIdx.x] = scr[threadIdx.x] + scr[threadIdx.x + h];
+            __syncthreads();
+        }
+        if (i == 0 && k < K && kk < per) out[k] = scr[threadIdx.x];
+        __syncthreads();
     }
-    if (i < n) {
-        double2 v[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = (i + q < n) ? __ldcg(src + (int64_t)(i + q) * stride) : make_double2(0, 0);
-#pragma unroll
-        for (int q = 0; q < 16; ++q)
-            if (i + q < n) s = s + v[q];
-    }
-    return s;
 }
 
 // Cross-CTA sum of one RHS's partial rows (chunk cx has written row cx,
 // columns 0..K-1).  The last CTA to finish in each group of kRedGroup chunks
-// adds the group's rows in chunk order into a group row; the last group to
-// finish adds the group rows in group order into tot[0..K) (shared memory).
-// Returns true in that one CTA (all threads).  The tickets are last-arriver
-// counters that reset themselves; nothing waits.  The order depends only on
-// nchunk and K.
+// adds the group's rows into a group row; the last group to finish adds the
+// group rows into tot[0..K) (shared memory).  Returns true in that one CTA
+// (all threads).  The tickets are last-arriver counters that reset
+// themselves; nothing waits.  The order depends only on nchunk and K.
 __device__ bool reduce_rows(const GArgs &a, int rr, int cx, int K, double2 *tot) {
     __shared__ unsigned s_t;
+    __shared__ double2 scr[256];
     double2 *rows = part_rows(a, rr);
     unsigned *cnt = a.cnt + (int64_t)rr * a.cstride;
     const int g = cx / kRedGroup, g0 = g * kRedGroup;
@@ -232,8 +242,7 @@ __device__ bool reduce_rows(const GArgs &a, int rr, int cx, int K, double2 *tot)
     if (s_t != (unsigned)gs - 1) return false;
     __threadfence();
     if (threadIdx.x == 0) cnt[g] = 0u;  // no other CTA of this launch touches it again
-    for (int k = threadIdx.x; k < K; k += blockDim.x)
-        rows[(int64_t)(a.nchunk + g) * a.pstride + k] = ordered_sum(rows + (int64_t)g0 * a.pstride + k, gs, a.pstride);
+    tree_sum(rows + (int64_t)g0 * a.pstride, gs, a.pstride, K, rows + (int64_t)(a.nchunk + g) * a.pstride, scr);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_t = atomicAdd(cnt + a.ngroups, 1u);
@@ -241,9 +250,7 @@ __device__ bool reduce_rows(const GArgs &a, int rr, int cx, int K, double2 *tot)
     if (s_t != (unsigned)a.ngroups - 1) return false;
     __threadfence();
     if (threadIdx.x == 0) cnt[a.ngroups] = 0u;
-    for (int k = threadIdx.x; k < K; k += blockDim.x)
-        tot[k] = ordered_sum(rows + (int64_t)a.nchunk * a.pstride + k, a.ngroups, a.pstride);
-    __syncthreads();
+    tree_sum(rows + (int64_t)a.nchunk * a.pstride, a.ngroups, a.pstride, K, tot, scr);
     return true;
 }
 
@@ -323,6 +330,8 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_residual(const __gr
     st[ST_REORTH] = 0;
     st[ST_INNER] = 0;
     st[ST_RESTARTS] = 0;
+    st[ST_COLUMN] = 0;
+    st[ST_END] = 0;
     if (!isfinite(vn) || !isfinite(rn)) {
         st[ST_STATUS] = RS_NONFINITE;
     } else if (rn <= a.ctl->tol * vn || rn == 0.0) {
@@ -343,14 +352,15 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_residual(const __gr
 }
 
 // ---------------------------------------------------------------- Arnoldi
-// Hessenberg column j from the Gram-Schmidt coefficients hs[0..j] (shared
-// memory, rotated in place) and beta_{j+1}: the earlier Givens rotations, the
-// new one, the residual estimate and the end-of-cycle decision.  Called by
-// every thread of one CTA; the rotation chain runs in one thread on shared
-// copies of (c_i, s_i).  The least squares R y = g is solved at the update
+// Givens rotations of Hessenberg column j (stored unrotated in H by the
+// update kernel, with beta_{j+1}): the earlier rotations, the new one, the
+// residual estimate and the end-of-cycle decision.  Called by every thread
+// of one CTA; the rotation chain runs in one thread on shared copies.  It
+// runs beside the next step's product (which does no FP64 work), off the
+// Arnoldi kernels' path.  The least squares R y = g is solved at the update
 // (k_update_d).
-__device__ void finalize_column(const GArgs &a, int rr, int j, double2 *hs, double beta) {
-    __shared__ double2 s_cs[128], s_sn[128];
+__device__ void givens_column(const GArgs &a, int rr, int j) {
+    __shared__ double2 s_cs[128], s_sn[128], hs[129];
     const int m = a.m;
     int *st = a.st + rr * ST_STRIDE;
     double *nm = a.nrm + rr * NM_STRIDE;
@@ -361,9 +371,10 @@ __device__ void finalize_column(const GArgs &a, int rr, int j, double2 *hs, doub
         s_cs[i] = __ldcg(cs + i);
         s_sn[i] = __ldcg(sn + i);
     }
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) hs[i] = __ldcg(H + (int64_t)i * m + j);
     __syncthreads();
     if (threadIdx.x == 0) {
-        a.beta[(int64_t)rr * (m + 1) + j + 1] = beta;
+        const double beta = a.beta[(int64_t)rr * (m + 1) + j + 1];
         double2 p = hs[0];
         for (int i = 0; i < j; ++i) {
             const double2 q = hs[i + 1];
@@ -392,32 +403,42 @@ __device__ void finalize_column(const GArgs &a, int rr, int j, double2 *hs, doub
         const bool end =
             !(res > nm[NM_TARGET]) || !(beta > 0) || (j + 1 == m) || (st[ST_ITERS] >= a.ctl->max_iter);
         if (end) st[ST_END] = 1;
+        st[ST_COLUMN] = 0;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) H[i * m + j] = hs[i];
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) H[(int64_t)i * m + j] = hs[i];
 }
 
-// After the first Gram-Schmidt pass (hs[k] = h_k for k <= j, hs[j+1].x =
-// ||w||^2, shared memory, whole CTA): ||w - V h||^2 = ||w||^2 - sum |h_k|^2
-// (exact for orthonormal v_k up to rounding of order u ||w||^2 / ||w'||^2,
-// below 4096 u when no second pass is taken); strong cancellation (or NaN)
-// asks for the second pass, else the Hessenberg column is finalised now.
-__device__ void column_decision(const GArgs &a, int rr, int j, double2 *hs) {
-    __shared__ double s_wn2;
-    __shared__ int s_again;
+// After the first Gram-Schmidt pass (hs[k] = h_k for k <= j, shared memory;
+// w2 = ||w||^2): ||w - V h||^2 = ||w||^2 - sum |h_k|^2 (exact for orthonormal
+// v_k up to rounding of order u ||w||^2 / ||w'||^2, below 4096 u when no
+// second pass is taken); strong cancellation (or NaN) asks for the second
+// pass.  The column h goes to H; without a second pass beta_{j+1} = ||w'|| is
+// stored and the column waits for its rotations.  Whole CTA; the sum of
+// |h_k|^2 is a fixed-order warp tree.
+__device__ void column_decision(const GArgs &a, int rr, int j, const double2 *hs, double w2) {
+    __shared__ double s_hsq;
     int *st = a.st + rr * ST_STRIDE;
-    if (threadIdx.x == 0) {
-        const double w2 = hs[j + 1].x;
-        double hsq = 0;
-        for (int k = 0; k <= j; ++k) hsq += cabs2(hs[k]);
-        const double wn2 = w2 - hsq;
-        const int again = !(wn2 > kReorthEta * kReorthEta * w2);
-        st[ST_REORTH] = again;
-        s_wn2 = wn2;
-        s_again = again;
+    const int m = a.m;
+    double2 *H = a.H + (int64_t)rr * (m + 1) * m;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) H[(int64_t)i * m + j] = hs[i];
+    if (threadIdx.x < 32) {
+        double v = 0;
+        for (int k = threadIdx.x; k <= j; k += 32) v += cabs2(hs[k]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) s_hsq = v;
     }
     __syncthreads();
-    if (!s_again) finalize_column(a, rr, j, hs, sqrt(s_wn2));
+    if (threadIdx.x == 0) {
+        const double wn2 = w2 - s_hsq;
+        const int again = !(wn2 > kReorthEta * kReorthEta * w2);
+        st[ST_REORTH] = again;
+        if (!again) {
+            a.beta[(int64_t)rr * (m + 1) + j + 1] = sqrt(wn2);
+            st[ST_COLUMN] = 1;
+        }
+    }
 }
 
 // Partial dot products <u_k, w> for k in [k0, k0+8) (k <= j) plus, when
@@ -470,9 +491,10 @@ __device__ __forceinline__ void dots_group(const GArgs &a, int rr, int j, int k0
 // Gram-Schmidt dots.
 // PASS 1: w = (product of u_j) / beta_j is formed (from the FP32 or FP64
 //   product) and stored as u_{j+1}; the CTA's sums of <u_k, w> (k <= j) and
-//   ||w||^2 are reduced across the RHS's chunks; the last CTA stores
-//   h1_k = <v_k, w> and h1_{j+1} = ||w||^2.
-// PASS 2 (flagged RHS only): h2_k = <v_k, u_{j+1}>.
+//   ||w||^2 are reduced across the RHS's chunks; the last CTA stores them
+//   unscaled: h1_k = beta_k <v_k, w> and h1_{j+1} = ||w||^2 (the update
+//   kernel scales, so no division sits on this kernel's serial tail).
+// PASS 2 (flagged RHS only): h2_k = beta_k <v_k, u_{j+1}>.
 template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(const __grid_constant__ GroupArgs g) {
     __shared__ double2 wred[8][kMaxK];
     __shared__ double2 tot[kMaxK];
@@ -523,8 +545,7 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(cons
     }
     if (!reduce_rows(a, rr, L.cx, K, tot)) return;
     double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
-    for (int k = threadIdx.x; k <= j; k += blockDim.x) h[k] = cscale(tot[k], 1.0 / beta[k]);
-    if (PASS == 1 && threadIdx.x == 0) h[j + 1] = tot[j + 1];  // ||w||^2 in .x
+    for (int k = threadIdx.x; k < K; k += blockDim.x) h[k] = tot[k];  // (PASS 1: ||w||^2 in slot j+1)
 }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -590,17 +611,19 @@ __device__ void iteration_control(const GroupArgs &g) {
 }
 
 // u_{j+1} <- u_{j+1} - sum_k (h_k / beta_k) u_k and its copy for the next
-// product, from the h the dots kernel stored.
+// product, from the sums the dots kernel stored (h_k = that / beta_k).
 // PASS 1: one extra CTA per RHS (cx == nchunk) takes the second-pass
-//   decision and, without one, finalises the Hessenberg column, alongside the
-//   update; the last CTA of the whole grid then runs the iteration control
-//   (or, when some RHS asked for a second pass, leaves it to that pass).
+//   decision and stores the column (and, without a second pass, beta_{j+1})
+//   alongside the update; the last CTA of the whole grid then runs the
+//   iteration control (or, when some RHS asked for a second pass, leaves it
+//   to that pass).
 // PASS 2 (after a second Gram-Schmidt pass): also forms ||u_{j+1}|| across
-//   the chunks and finalises the column with h1 + h2.
+//   the chunks, adds h2 to the stored column and stores beta_{j+1}.
 template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(const __grid_constant__ GroupArgs g) {
     __shared__ double red[8];
     __shared__ double2 cf[kMaxK];
-    __shared__ double2 tot[kMaxK];
+    __shared__ double2 hs[kMaxK];
+    __shared__ double2 tot[1];
     __shared__ unsigned s_t;
     const Loc L = locate(g, PASS == 1);
     if (L.mi >= 0) {
@@ -613,14 +636,14 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(const
             const double *beta = a.beta + (int64_t)rr * (a.m + 1);
             const double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
             for (int k = threadIdx.x; k <= j; k += blockDim.x) {
-                const double2 hk = __ldcg(h + k);
-                cf[k] = cscale(hk, 1.0 / beta[k]);
-                tot[k] = hk;
+                const double ib = 1.0 / beta[k];
+                const double2 hk = cscale(__ldcg(h + k), ib);
+                hs[k] = hk;
+                cf[k] = cscale(hk, ib);
             }
-            if (PASS == 1 && threadIdx.x == 0) tot[j + 1] = __ldcg(h + j + 1);
             __syncthreads();
             if (PASS == 1 && L.cx == a.nchunk) {
-                column_decision(a, rr, j, tot);
+                column_decision(a, rr, j, hs, __ldcg(h + j + 1).x);
             } else {
                 double2 *un = basis(a, j + 1, rr);
                 double2 wv[ELEM];
@@ -669,13 +692,15 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(const
                     acc = block_sum1(acc, red);
                     if (threadIdx.x == 0) part_rows(a, rr)[(int64_t)L.cx * a.pstride] = make_double2(acc, 0);
                     if (reduce_rows(a, rr, L.cx, 1, tot)) {
-                        const double wn = sqrt(tot[0].x);
-                        const double2 *h1 = a.h1 + (int64_t)rr * (a.m + 1);
-                        const double2 *h2 = a.h2 + (int64_t)rr * (a.m + 1);
-                        for (int kk = threadIdx.x; kk <= j; kk += blockDim.x) cf[kk] = __ldcg(h1 + kk) + __ldcg(h2 + kk);
-                        if (threadIdx.x == 0) st[ST_REORTH] = 0;
-                        __syncthreads();
-                        finalize_column(a, rr, j, cf, wn);
+                        const int m = a.m;
+                        double2 *H = a.H + (int64_t)rr * (m + 1) * m;
+                        for (int kk = threadIdx.x; kk <= j; kk += blockDim.x)
+                            H[(int64_t)kk * m + j] = __ldcg(H + (int64_t)kk * m + j) + hs[kk];  // h1 + h2
+                        if (threadIdx.x == 0) {
+                            a.beta[(int64_t)rr * (m + 1) + j + 1] = sqrt(tot[0].x);
+                            st[ST_REORTH] = 0;
+                            st[ST_COLUMN] = 1;
+                        }
                     }
                 }
             }
@@ -700,6 +725,26 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(const
         return;
     }
     iteration_control(g);
+}
+
+// Givens rotations of the stored column ctl->j - 1, one CTA per RHS (member
+// i owns nrhs_i CTAs).  In the iteration loop it runs beside the product of
+// the next step; FINAL (after the loop) also closes the cycle of every RHS
+// still in one (it reached the restart length or the deadline).
+template <bool FINAL> __global__ void __launch_bounds__(128) k_givens(const __grid_constant__ GroupArgs g) {
+    int b = blockIdx.x, mi = 0;
+    while (mi < g.n && b >= g.m[mi].nrhs) b -= g.m[mi++].nrhs;
+    if (mi >= g.n) return;
+    const GArgs &a = g.m[mi];
+    int *st = a.st + b * ST_STRIDE;
+    const int j = a.ctl->j - 1;
+    if (!st[ST_ACTIVE]) return;
+    if (j >= 0 && j < a.m && st[ST_COLUMN]) givens_column(a, b, j);
+    if (FINAL && threadIdx.x == 0) {
+        st[ST_END] = 0;
+        st[ST_ACTIVE] = 0;
+        st[ST_PENDING] = 1;
+    }
 }
 
 // After a second Gram-Schmidt pass: the step's iteration control.
@@ -831,6 +876,9 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_inner_residual(cons
     if (!more) return;
     st[ST_RESTARTS] += 1;
     st[ST_ACTIVE] = 1;
+    st[ST_REORTH] = 0;
+    st[ST_COLUMN] = 0;
+    st[ST_END] = 0;
     a.beta[(int64_t)rr * (a.m + 1)] = rin;
     double2 *gg = a.g + (int64_t)rr * (a.m + 1);
     gg[0] = make_double2(rin, 0);
@@ -1073,6 +1121,22 @@ template <int ELEM> struct Launch {
     }
 };
 
+static unsigned group_rhs(const GroupArgs &g) {
+    unsigned t = 0;
+    for (int i = 0; i < g.n; ++i) t += (unsigned)g.m[i].nrhs;
+    return t;
+}
+
+static ztoep_status_t launch_givens(const GroupArgs &g, bool final_, cudaStream_t s) {
+    KScope ks(K_ARNOLDI, s);
+    if (final_)
+        k_givens<true><<<group_rhs(g), 128, 0, s>>>(g);
+    else
+        k_givens<false><<<group_rhs(g), 128, 0, s>>>(g);
+    ZT_CUDA(cudaGetLastError());
+    return ZTOEP_OK;
+}
+
 struct Ops {
     int elem;
     ztoep_status_t vnorm(const GroupArgs &g, cudaStream_t s) const {
@@ -1199,7 +1263,10 @@ static ztoep_status_t member_products(const Member *mem, int n, bool fp32, bool 
 //                 -> x += d -> FP64 products -> residual -> sweep control }
 // The Arnoldi step is k_dots + k_upd, whose last CTA runs the iteration
 // control; a RHS that asks for a second Gram-Schmidt pass makes it set the IF
-// node that runs k_dots<2>, k_upd<2> and the iteration control instead.  In a
+// node that runs k_dots<2>, k_upd<2> and the iteration control instead.  The
+// Givens rotations of a step's column run in the next iteration on a branch
+// beside its products (k_givens), and after the loop for the last column, so
+// the end of a cycle is seen one step late: that step's work is discarded.  In a
 // group of several members, each member's iteration product sits in its own
 // IF node (members with no RHS in a cycle skip it) and the members' products
 // run concurrently; every other kernel is one launch for all members.
@@ -1264,6 +1331,7 @@ static ztoep_status_t build_graph(const Member *mem, int n, SolveGraph &sg, int 
     ZT_TRY(capture_begin(s, body_restart, &sg.k_restart));
     ZT_TRY(launch_ctl(k_cycle_begin, g, s));
     ZT_TRY(add_conditional(s, g.h_iter, cudaGraphCondTypeWhile, &body_iter));
+    ZT_TRY(launch_givens(g, true, s));
     ZT_TRY(ops.update_d(g, s));
     if (mixed) {
         ZT_TRY(member_products(mem, n, true, false, s, ce));
@@ -1281,12 +1349,21 @@ static ztoep_status_t build_graph(const Member *mem, int n, SolveGraph &sg, int 
         for (int i = 0; i < n; ++i)
             ZT_CUDA(cudaGraphConditionalHandleCreate(&g.h_prod[i], body_iter, 1, cudaGraphCondAssignDefault));
     ZT_TRY(capture_begin(s, body_iter, &sg.k_iter));
+    // the previous column's rotations on a branch beside the products
+    cudaEvent_t ev_g0 = nullptr, ev_g1 = nullptr;
+    ZT_TRY(ce.make(&ev_g0));
+    ZT_TRY(ce.make(&ev_g1));
+    ZT_CUDA(cudaEventRecord(ev_g0, s));
+    ZT_CUDA(cudaStreamWaitEvent(p0->aux, ev_g0, 0));
+    ZT_TRY(launch_givens(g, false, p0->aux));
+    ZT_CUDA(cudaEventRecord(ev_g1, p0->aux));
     if (g.prod_if)
         ZT_TRY(add_conditionals(s, g.h_prod, n, cudaGraphCondTypeIf, body_prod));
     else if (mixed)
         ZT_TRY(run_matvec<float>(p0, mem[0].nrhs, (const float2 *)p0->ws32.xin, (float2 *)p0->ws32.yout, s));
     else
         ZT_TRY(run_matvec<double>(p0, mem[0].nrhs, p0->sws.xin64, p0->sws.w, s));
+    ZT_CUDA(cudaStreamWaitEvent(s, ev_g1, 0));
     ZT_TRY(ops.arnoldi(g, 1, s));
     ZT_TRY(add_conditional(s, g.h_reorth, cudaGraphCondTypeIf, &body_reorth));
     ZT_TRY(capture_end(s));
@@ -1389,6 +1466,7 @@ static ztoep_status_t run_host_loop(const Member *mem, int n, int prec, int m, c
         for (;;) {
             ZT_TRY(launch_ctl(k_cycle_begin, g, s));
             for (int it = 0; it < m; ++it) {
+                ZT_TRY(launch_givens(g, false, s));
                 ZT_TRY(member_products(mem, n, mixed, false, s, ce));
                 ZT_TRY(ops.arnoldi(g, 1, s));
                 ZT_TRY(read_ctl());
@@ -1398,6 +1476,7 @@ static ztoep_status_t run_host_loop(const Member *mem, int n, int prec, int m, c
                 }
                 if (!hc->cond_iter) break;
             }
+            ZT_TRY(launch_givens(g, true, s));
             ZT_TRY(ops.update_d(g, s));
             if (mixed) {
                 ZT_TRY(member_products(mem, n, true, false, s, ce));

@@ -238,6 +238,7 @@ void ztoep_plan_destroy(ztoep_plan_t p) {
     if (p->ev_et) cudaEventDestroy(p->ev_et);
     if (p->side) cudaStreamDestroy(p->side);
     if (p->cap) cudaStreamDestroy(p->cap);
+    if (p->aux) cudaStreamDestroy(p->aux);
     cudaSetDevice(cur);
     delete p;
 }
@@ -275,6 +276,7 @@ static ztoep_status_t plan_build(ztoep_plan_t p, const ztoep_desc_t *d, const do
     ZT_CUDA(cudaDeviceGetAttribute(&p->l2_bytes, cudaDevAttrL2CacheSize, p->device));
     ZT_CUDA(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
     ZT_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+    ZT_CUDA(cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking));
     ZT_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     ZT_CUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
     ZT_CUDA(cudaEventCreateWithFlags(&p->ev_et, cudaEventDisableTiming));
