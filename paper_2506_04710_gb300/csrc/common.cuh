@@ -115,12 +115,10 @@ struct MatvecWs {  // per-precision matvec workspace, sized for `cap` RHS
     void *X1 = nullptr;     // [cap][ny][lx][b] after the x pass (also reused by the inverse y pass)
     void *Xh = nullptr;     // [F][cap][b] spectrum (block product runs in place)
     void *ET = nullptr;     // [nsplit][cap][NT] B^T x_E partial sums
-    void *Ep = nullptr;     // [ntile][cap][E]   B x_T partial sums
+    void *Ep = nullptr;     // B x_T partial sums: k_edge3 [cap][E][ntile], else [ntile or K split][cap][E]
     void *Yh = nullptr;     // [F][cap][b] out-of-place block-product output (tensor path, side plans)
     void *Fs = nullptr;     // [4k][cap][Lmax] side products B x_T along each side, frequency domain
     void *Us = nullptr;     // [cap][4k][Lmax] DFTs of the side slices of x_E
-    void *Eg = nullptr;     // [ngroups][cap][E] group sums of the FP32 edge-row partials
-    unsigned *cnt = nullptr;  // [ngroups + 1] last-arriver tickets of the FP32 edge kernel
     size_t bytes = 0;
 };
 

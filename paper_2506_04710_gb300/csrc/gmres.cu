@@ -74,6 +74,8 @@ struct SolveCtl {
     int cond_first, cond_sweep, cond_restart, cond_iter;  // loop decisions (read by the host-driven mode)
     int reorth_pending;  // the step's second Gram-Schmidt pass (and iteration control) is still to run
     unsigned tick;       // last-arriver ticket of the update kernel's grid
+    int cycle_bodies;    // iteration bodies run in the current cycle (at most m + 1 in a correct run)
+    int guard;           // the iteration guard stopped the loops (a body count beyond its bound)
     double tol, inner_tol;
     long long timeout_ns;
     unsigned long long deadline;  // %globaltimer value, 0 = none
@@ -498,6 +500,18 @@ __device__ __forceinline__ void dots_group(const GArgs &a, int rr, int j, int k0
 template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(const __grid_constant__ GroupArgs g) {
     __shared__ double2 wred[8][kMaxK];
     __shared__ double2 tot[kMaxK];
+    if (PASS == 1 && blockIdx.x == 0 && threadIdx.x == 0) {
+        // Guard: every iteration body advances j, so a cycle runs at most m + 1
+        // bodies (one after its end is seen); beyond that the loops are ended
+        // and the solve reports TIMEOUT rather than running on.
+        SolveCtl *c = g.m[0].ctl;
+        if (++c->cycle_bodies > g.m[0].m + 2) {
+            c->guard = 1;
+            c->timed_out = 1;
+            c->cond_iter = 0;
+            if (g.graph) cudaGraphSetConditional(g.h_iter, 0u);
+        }
+    }
     const Loc L = locate(g, false);
     if (L.mi < 0) return;
     const GArgs &a = g.m[L.mi];
@@ -598,7 +612,7 @@ __device__ void iteration_control(const GroupArgs &g) {
     c->reorth_pending = 0;
     const bool late = past_deadline(c);
     if (any && late) c->timed_out = 1;
-    const unsigned cond = (any && c->j < g.m[0].m && !late) ? 1u : 0u;
+    const unsigned cond = (any && c->j < g.m[0].m && !late && !c->guard) ? 1u : 0u;
     c->cond_iter = (int)cond;
     if (g.graph) {
         cudaGraphSetConditional(g.h_iter, cond);
@@ -908,6 +922,8 @@ __global__ void k_solve_begin(const __grid_constant__ GroupArgs g, cudaGraphCond
         c->reorth_bodies = 0;
         c->reorth_pending = 0;
         c->tick = 0u;
+        c->cycle_bodies = 0;
+        c->guard = 0;
         c->deadline = c->timeout_ns > 0 ? globaltimer_ns() + (unsigned long long)c->timeout_ns : 0ull;
         c->cond_first = c->zero ? 0 : 1;
         if (g.graph) cudaGraphSetConditional(h_first, c->zero ? 0u : 1u);
@@ -923,7 +939,7 @@ __global__ void k_sweep_ctl(const __grid_constant__ GroupArgs g, cudaGraphCondit
     c->sweeps += 1;
     const bool late = past_deadline(c);
     if (any && late) c->timed_out = 1;
-    const unsigned cond = (any && c->sweeps < c->max_outer && !late) ? 1u : 0u;
+    const unsigned cond = (any && c->sweeps < c->max_outer && !late && !c->guard) ? 1u : 0u;
     c->cond_sweep = (int)cond;
     if (g.graph) cudaGraphSetConditional(h_sweep, cond);
 }
@@ -943,7 +959,7 @@ __global__ void k_restart_ctl(const __grid_constant__ GroupArgs g, cudaGraphCond
     SolveCtl *c = g.m[0].ctl;
     const bool late = past_deadline(c);
     if (any && late) c->timed_out = 1;
-    const unsigned cond = (any && !late) ? 1u : 0u;
+    const unsigned cond = (any && !late && !c->guard) ? 1u : 0u;
     c->cond_restart = (int)cond;
     if (g.graph) cudaGraphSetConditional(h_restart, cond);
 }
@@ -952,6 +968,7 @@ __global__ void k_cycle_begin(const __grid_constant__ GroupArgs g) {
     if (threadIdx.x != 0) return;
     SolveCtl *c = g.m[0].ctl;
     c->j = 0;
+    c->cycle_bodies = 0;
     c->restart_bodies += 1;
     c->cond_iter = 1;
     if (g.graph) cudaGraphSetConditional(g.h_iter, 1u);

@@ -393,187 +393,141 @@ __global__ void __launch_bounds__(256) k_edge_finish(const cplx_t<R> *__restrict
 // FP32 edge coupling in one pass over [B | C]: the FP32 copy of B carries C
 // in the E columns after the N_T Toeplitz ones, so one row of it times the
 // whole x = (x_T, x_E) is the edge row y_E = B x_T + C x_E.
-//   ET[r][t]    = sum_e B[e][t] x_E[r][e]       (t < N_T; complete per column)
-//   y[r][N_T+e] = sum_t [B|C][e][t] x[r][t]     (per-CTA row partials, summed
-//                 by the last CTAs to finish)
-// The N_T + E columns are split into G contiguous ranges, G a multiple of the
-// SM count, so every SM streams the same share of B.  A CTA walks its range
-// in sub-tiles of E3_TW columns and reads all E rows of each; warp w takes
+//   ET[r][t]        = sum_e B[e][t] x_E[r][e]          (t < N_T; complete per column)
+//   Ep[r][e][tile]  = sum_{t in tile} [B|C][e][t] x[r][t]  (row partials)
+// A CTA owns a tile of E3_TW columns and reads all E rows of it; warp w takes
 // rows w*UNR.., w*UNR + W*UNR.., ... (UNR rows per step, loads first), so each
 // row's partial is one warp's and needs no cross-warp step; the B^T x_E sums
 // of the warps are added in warp order through shared memory.  Rows are taken
-// in chunks of E3_ECH so x_E fits in shared memory.
-// Row partials: Ep[cta][r][e] (accumulated over the CTA's sub-tiles by the
-// same thread).  The last CTA to finish in each group of E3_GROUP CTAs adds
-// the group's partials in CTA order into Eg[g][r][e]; the last group to
-// finish adds the group sums in group order into y.  The tickets are
-// last-arriver counters (no waiting) that reset themselves, and every sum has
-// an order fixed by the plan's geometry, so a RHS is summed identically alone
-// and in any batch.
-constexpr int E3_W = 8, E3_U = 2, E3_CPL = 2, E3_TW = 32 * E3_U * E3_CPL, E3_ECH = 1024, E3_GROUP = 16;
-
-struct Edge3Args {
-    const float2 *x;  // [nrhs][N]
-    const float2 *B;  // [E][ldb]: B in columns < NT, C in NT .. NT+E-1, zeros after
-    float2 *ET;       // [nrhs][NT]
-    float2 *Ep;       // [G][nrhs][E]
-    float2 *Eg;       // [ngroups][nrhs][E]
-    float2 *y;        // [nrhs][N] (rows NT.. written here)
-    unsigned *cnt;    // [ngroups + 1] tickets, zero between launches
-    int64_t NT, ncol, ldb, N;
-    int E, nrhs, r0, rc, range, G, ngroups;
-};
-
-// out[k] = sum_{c < n} src[c * stride + k0] in c order, loads issued 16 at a time.
-__device__ __forceinline__ float2 ordered_sum(const float2 *src, int n, int64_t stride) {
-    float2 s = make_float2(0.f, 0.f);
-    int c = 0;
-    for (; c + 16 <= n; c += 16) {
-        float2 v[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = __ldcg(src + (int64_t)(c + i) * stride);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) s = s + v[i];
-    }
-    for (; c < n; ++c) s = s + __ldcg(src + (int64_t)c * stride);
-    return s;
-}
+// in chunks of E3_ECH so x_E fits in shared memory.  k_edge3_finish then adds
+// each row's tile partials (the tile index is the fastest, so a warp reads a
+// row's partials with coalesced loads) in a fixed order.
+constexpr int E3_W = 8, E3_U = 2, E3_CPL = 2, E3_TW = 32 * E3_U * E3_CPL, E3_ECH = 1024;
 
 template <int RC>
-__global__ void __launch_bounds__(256) k_edge3(Edge3Args a) {
+__global__ void __launch_bounds__(256) k_edge3(const float2 *__restrict__ x, const float2 *__restrict__ B,
+                                               float2 *__restrict__ ET, float2 *__restrict__ Ep, int64_t NT,
+                                               int64_t ncol, int64_t ldb, int E, int64_t N, int nrhs, int r0,
+                                               int rc) {
     constexpr int U = E3_U, CPL = E3_CPL, W = E3_W, UNR = 4;
     // x_E of the current row chunk, later reused for the cross-warp sums
     constexpr int SX = E3_ECH * RC, SR = W * E3_TW * RC;
     __shared__ float2 sh[SX > SR ? SX : SR];
-    __shared__ unsigned s_ticket;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int cta = blockIdx.x;
-    const int64_t c0 = (int64_t)cta * a.range;
-    const int64_t c1 = c0 + a.range < a.ncol ? c0 + a.range : a.ncol;
-    const int E = a.E, rc = a.rc, r0 = a.r0;
+    const int tile = blockIdx.x, ntile = gridDim.x;
+    const int64_t tbase = (int64_t)tile * E3_TW;
 
-    for (int64_t tbase = c0; tbase < c1; tbase += E3_TW) {
-        const bool first = tbase == c0;
-        float2 xt[U][CPL][RC], acc[U][CPL][RC];
+    float2 xt[U][CPL][RC], acc[U][CPL][RC];
 #pragma unroll
-        for (int u = 0; u < U; ++u)
+    for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int c = 0; c < CPL; ++c) {
-                const int64_t t = tbase + (int64_t)(u * 32 + lane) * CPL + c;
+        for (int c = 0; c < CPL; ++c) {
+            const int64_t t = tbase + (int64_t)(u * 32 + lane) * CPL + c;
 #pragma unroll
-                for (int q = 0; q < RC; ++q) {
-                    acc[u][c][q] = make_float2(0.f, 0.f);
-                    xt[u][c][q] = (t < c1 && q < rc) ? a.x[(int64_t)(r0 + q) * a.N + t] : make_float2(0.f, 0.f);
-                }
+            for (int q = 0; q < RC; ++q) {
+                acc[u][c][q] = make_float2(0.f, 0.f);
+                xt[u][c][q] = (t < ncol && q < rc) ? x[(int64_t)(r0 + q) * N + t] : make_float2(0.f, 0.f);
             }
-        for (int ec = 0; ec < E; ec += E3_ECH) {
-            const int ne = min(E3_ECH, E - ec);
-            __syncthreads();
-            for (int k = threadIdx.x; k < ne * RC; k += blockDim.x) {
-                const int el = k / RC, q = k - el * RC;
-                sh[k] = q < rc ? a.x[(int64_t)(r0 + q) * a.N + a.NT + ec + el] : make_float2(0.f, 0.f);
+        }
+    for (int ec = 0; ec < E; ec += E3_ECH) {
+        const int ne = min(E3_ECH, E - ec);
+        __syncthreads();
+        for (int k = threadIdx.x; k < ne * RC; k += blockDim.x) {
+            const int el = k / RC, q = k - el * RC;
+            sh[k] = q < rc ? x[(int64_t)(r0 + q) * N + NT + ec + el] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int el0 = warp * UNR; el0 < ne; el0 += W * UNR) {
+            float4 raw[UNR][U];
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                const float2 *brow = B + (int64_t)(ec + el0 + k) * ldb + tbase;
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    raw[k][u] = (el0 + k < ne)
+                                    ? __ldcs(reinterpret_cast<const float4 *>(brow + (int64_t)(u * 32 + lane) * CPL))
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            __syncthreads();
-            for (int el0 = warp * UNR; el0 < ne; el0 += W * UNR) {
-                float4 raw[UNR][U];
+            float2 part[UNR][RC];
 #pragma unroll
-                for (int k = 0; k < UNR; ++k) {
-                    const float2 *brow = a.B + (int64_t)(ec + el0 + k) * a.ldb + tbase;
+            for (int k = 0; k < UNR; ++k) {
+                const int el = el0 + k;
+                float2 bv[U][CPL];
 #pragma unroll
-                    for (int u = 0; u < U; ++u)  // only this CTA's columns: no byte of B is fetched twice
-                        raw[k][u] = (el0 + k < ne && tbase + (u * 32 + lane) * CPL < c1)
-                                        ? __ldcs(reinterpret_cast<const float4 *>(brow + (int64_t)(u * 32 + lane) * CPL))
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-                float2 part[UNR][RC];
-#pragma unroll
-                for (int k = 0; k < UNR; ++k) {
-                    const int el = el0 + k;
-                    float2 bv[U][CPL];
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        bv[u][0] = make_float2(raw[k][u].x, raw[k][u].y);
-                        bv[u][1] = make_float2(raw[k][u].z, raw[k][u].w);
-                    }
-#pragma unroll
-                    for (int q = 0; q < RC; ++q) {
-                        const float2 xe = el < ne ? sh[el * RC + q] : make_float2(0.f, 0.f);
-                        float2 pt = make_float2(0.f, 0.f);
-#pragma unroll
-                        for (int u = 0; u < U; ++u)
-#pragma unroll
-                            for (int c = 0; c < CPL; ++c) {
-                                acc[u][c][q] = cfma(bv[u][c], xe, acc[u][c][q]);
-                                pt = cfma(bv[u][c], xt[u][c][q], pt);
-                            }
-                        part[k][q] = pt;
-                    }
+                for (int u = 0; u < U; ++u) {
+                    bv[u][0] = make_float2(raw[k][u].x, raw[k][u].y);
+                    bv[u][1] = make_float2(raw[k][u].z, raw[k][u].w);
                 }
 #pragma unroll
                 for (int q = 0; q < RC; ++q) {
-                    float2 v4[UNR];
+                    const float2 xe = el < ne ? sh[el * RC + q] : make_float2(0.f, 0.f);
+                    float2 pt = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int k = 0; k < UNR; ++k) v4[k] = part[k][q];
-                    const float2 tot = warp_rs4<float>(v4);
-                    const int k = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
-                    if ((lane & 7) == 0 && el0 + k < ne && q < rc) {
-                        float2 *dst = a.Ep + ((int64_t)cta * a.nrhs + r0 + q) * E + ec + el0 + k;
-                        *dst = first ? tot : *dst + tot;  // the same thread owns this row in every sub-tile
-                    }
+                    for (int u = 0; u < U; ++u)
+#pragma unroll
+                        for (int c = 0; c < CPL; ++c) {
+                            acc[u][c][q] = cfma(bv[u][c], xe, acc[u][c][q]);
+                            pt = cfma(bv[u][c], xt[u][c][q], pt);
+                        }
+                    part[k][q] = pt;
                 }
             }
-        }
-        __syncthreads();
-        // B^T x_E of this sub-tile: add the W per-warp sums in warp order
 #pragma unroll
-        for (int u = 0; u < U; ++u)
+            for (int q = 0; q < RC; ++q) {
+                float2 v4[UNR];
 #pragma unroll
-            for (int c = 0; c < CPL; ++c)
-#pragma unroll
-                for (int q = 0; q < RC; ++q)
-                    sh[(warp * E3_TW + (u * 32 + lane) * CPL + c) * RC + q] = acc[u][c][q];
-        __syncthreads();
-        for (int k = threadIdx.x; k < E3_TW * RC; k += blockDim.x) {
-            const int col = k / RC, q = k - col * RC;
-            const int64_t t = tbase + col;
-            if (t < c1 && t < a.NT && q < rc) {
-                float2 sum = sh[col * RC + q];
-#pragma unroll
-                for (int w = 1; w < W; ++w) sum = sum + sh[(w * E3_TW + col) * RC + q];
-                a.ET[(int64_t)(r0 + q) * a.NT + t] = sum;
+                for (int k = 0; k < UNR; ++k) v4[k] = part[k][q];
+                const float2 tot = warp_rs4<float>(v4);
+                const int k = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
+                if ((lane & 7) == 0 && el0 + k < ne && q < rc)
+                    Ep[((int64_t)(r0 + q) * E + ec + el0 + k) * ntile + tile] = tot;
             }
         }
     }
-
-    // level 1: the last CTA of the group adds the group's row partials
-    const int g = cta / E3_GROUP;
-    const int gfirst = g * E3_GROUP;
-    const int gsize = min(E3_GROUP, a.G - gfirst);
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_ticket = atomicAdd(a.cnt + g, 1u);
+    // B^T x_E: add the W per-warp sums in warp order
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int q = 0; q < RC; ++q) sh[(warp * E3_TW + (u * 32 + lane) * CPL + c) * RC + q] = acc[u][c][q];
     __syncthreads();
-    if (s_ticket != (unsigned)gsize - 1) return;
-    __threadfence();
-    if (threadIdx.x == 0) a.cnt[g] = 0u;
-    const int64_t pstride = (int64_t)a.nrhs * E;  // between CTAs (and between groups)
-    for (int k = threadIdx.x; k < E * rc; k += blockDim.x) {
-        const int q = k / E, e = k - q * E;
-        const int64_t off = (int64_t)(r0 + q) * E + e;
-        a.Eg[(int64_t)g * pstride + off] = ordered_sum(a.Ep + (int64_t)gfirst * pstride + off, gsize, pstride);
+    for (int k = threadIdx.x; k < E3_TW * RC; k += blockDim.x) {
+        const int col = k / RC, q = k - col * RC;
+        const int64_t t = tbase + col;
+        if (t < NT && q < rc) {
+            float2 sum = sh[col * RC + q];
+#pragma unroll
+            for (int w = 1; w < W; ++w) sum = sum + sh[(w * E3_TW + col) * RC + q];
+            ET[(int64_t)(r0 + q) * NT + t] = sum;
+        }
     }
-    // level 2: the last group adds the group sums into y_E
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_ticket = atomicAdd(a.cnt + a.ngroups, 1u);
-    __syncthreads();
-    if (s_ticket != (unsigned)a.ngroups - 1) return;
-    __threadfence();
-    if (threadIdx.x == 0) a.cnt[a.ngroups] = 0u;
-    for (int k = threadIdx.x; k < E * rc; k += blockDim.x) {
-        const int q = k / E, e = k - q * E;
-        const int64_t off = (int64_t)(r0 + q) * E + e;
-        a.y[(int64_t)(r0 + q) * a.N + a.NT + e] = ordered_sum(a.Eg + off, a.ngroups, pstride);
+}
+
+// y[r][N_T + e] = sum_tile Ep[r][e][tile]: one warp per (r, e); lane l adds
+// tiles l, l+32, ... in order (loads eight at a time), then a fixed
+// butterfly over the lanes.
+__global__ void __launch_bounds__(256) k_edge3_finish(const float2 *__restrict__ Ep, float2 *__restrict__ y,
+                                                      int64_t NT, int E, int64_t N, int nrhs, int ntile) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  // r * E + e
+    if (row >= (int64_t)nrhs * E) return;
+    const float2 *src = Ep + row * ntile;
+    float2 s = make_float2(0.f, 0.f);
+    int t = lane;
+    for (; t + 7 * 32 < ntile; t += 8 * 32) {
+        float2 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = __ldcg(src + t + i * 32);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) s = s + v[i];
+    }
+    for (; t < ntile; t += 32) s = s + __ldcg(src + t);
+    s = warp_sum<float>(s);
+    if (lane == 0) {
+        const int64_t r = row / E, e = row - r * E;
+        y[r * N + NT + e] = s;
     }
 }
 
@@ -615,19 +569,8 @@ static int edge_ntile(ztoep_plan_t p, size_t csize) {
     int tile = (csize == 8) ? EdgeGeom<float>::TILE : EdgeGeom<double>::TILE;
     return (int)((p->NT + tile - 1) / tile);
 }
-// Column split of k_edge3: about 4 CTAs per SM over the N_T + E columns of
-// [B | C], each range a multiple of 4 columns (16-byte loads) and at least 32.
-struct Edge3Geom {
-    int G, range, ngroups;
-};
-static Edge3Geom edge3_geom(ztoep_plan_t p) {
-    const int64_t ncol = p->NT + p->E;
-    const int want = 4 * p->nsm;
-    int64_t range = (ncol + want - 1) / want;
-    range = std::max<int64_t>(32, (range + 3) / 4 * 4);
-    const int G = (int)((ncol + range - 1) / range);
-    return {G, (int)range, (G + E3_GROUP - 1) / E3_GROUP};
-}
+// Tiles of k_edge3 over the N_T + E columns of [B | C].
+static int edge3_ntile(ztoep_plan_t p) { return (int)((p->NT + p->E + E3_TW - 1) / E3_TW); }
 static int edge_nsplit(ztoep_plan_t p, int ntile, size_t csize) {
     if (p->E == 0) return 0;
     // enough CTAs for several resident per SM (FP32: 4 per SM, FP64: 2)
@@ -649,9 +592,10 @@ static int tc_edge_kchunk(ztoep_plan_t p) {
 }
 static int tc_edge_splits(ztoep_plan_t p) { return cgemm_splits((int)p->NT, tc_edge_kchunk(p)); }
 
+
 static void free_ws(MatvecWs &w) {
     cudaFree(w.xin); cudaFree(w.yout); cudaFree(w.X1); cudaFree(w.Xh); cudaFree(w.ET); cudaFree(w.Ep); cudaFree(w.Yh);
-    cudaFree(w.Fs); cudaFree(w.Us); cudaFree(w.Eg); cudaFree(w.cnt);
+    cudaFree(w.Fs); cudaFree(w.Us);
     w = MatvecWs{};
 }
 
@@ -675,14 +619,8 @@ template <typename R> ztoep_status_t ensure_ws(ztoep_plan_t p, int nrhs) {
         ZT_TRY(dalloc(&w.Us, side, &acc));
     } else if (p->E > 0) {
         ZT_TRY(dalloc(&w.ET, cs * (size_t)std::max(nsplit, 1) * nrhs * p->NT, &acc));
-        const int parts = std::max(cs == 8 ? edge3_geom(p).G : ntile, tc ? tc_edge_splits(p) : 0);
+        const int parts = std::max(cs == 8 ? edge3_ntile(p) : ntile, tc ? tc_edge_splits(p) : 0);
         ZT_TRY(dalloc(&w.Ep, cs * (size_t)parts * nrhs * p->E, &acc));
-        if (cs == 8) {
-            const Edge3Geom eg = edge3_geom(p);
-            ZT_TRY(dalloc(&w.Eg, cs * (size_t)eg.ngroups * nrhs * p->E, &acc));
-            ZT_TRY(dalloc((void **)&w.cnt, sizeof(unsigned) * (eg.ngroups + 1), &acc));
-            ZT_CUDA(cudaMemset(w.cnt, 0, sizeof(unsigned) * (eg.ngroups + 1)));
-        }
     }
     if (tc || p->side_k > 0) ZT_TRY(dalloc(&w.Yh, cs * nrhs * (size_t)p->F * p->b, &acc));
     w.cap = nrhs;
@@ -870,29 +808,31 @@ static ztoep_status_t launch_edge(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, 
     return ZTOEP_OK;
 }
 
-// FP32 edge coupling (k_edge3): ET holds B^T x_E and y_E = B x_T + C x_E is
-// written by the kernel's last CTA, so the whole branch is one launch per
-// group of up to 4 RHS.
+// FP32 edge coupling (k_edge3, then k_edge3_finish): ET holds B^T x_E and
+// y_E = B x_T + C x_E.  et_ready is recorded once ET is final (the finish
+// only writes y_E).
 static ztoep_status_t launch_edge3(ztoep_plan_t p, int nrhs, const float2 *x, float2 *y, MatvecWs &w,
-                                   cudaStream_t s) {
-    const Edge3Geom eg = edge3_geom(p);
-    Edge3Args a{};
-    a.x = x; a.B = p->B32; a.ET = reinterpret_cast<float2 *>(w.ET); a.Ep = reinterpret_cast<float2 *>(w.Ep);
-    a.Eg = reinterpret_cast<float2 *>(w.Eg); a.y = y; a.cnt = w.cnt;
-    a.NT = p->NT; a.ncol = p->NT + p->E; a.ldb = edge_ldb32(p->NT, p->E); a.N = p->N;
-    a.E = p->E; a.nrhs = nrhs; a.range = eg.range; a.G = eg.G; a.ngroups = eg.ngroups;
+                                   cudaStream_t s, cudaEvent_t et_ready) {
+    float2 *ET = reinterpret_cast<float2 *>(w.ET);
+    float2 *Ep = reinterpret_cast<float2 *>(w.Ep);
+    const int ntile = edge3_ntile(p);
+    const int64_t ldb = edge_ldb32(p->NT, p->E), ncol = p->NT + p->E;
     for (int r0 = 0; r0 < nrhs; r0 += 4) {
-        a.r0 = r0;
-        a.rc = std::min(4, nrhs - r0);
+        const int rc = std::min(4, nrhs - r0);
         KScope ks(K_EDGE, s);
-        if (a.rc == 1)
-            k_edge3<1><<<eg.G, 256, 0, s>>>(a);
-        else if (a.rc == 2)
-            k_edge3<2><<<eg.G, 256, 0, s>>>(a);
+        if (rc == 1)
+            k_edge3<1><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ncol, ldb, p->E, p->N, nrhs, r0, rc);
+        else if (rc == 2)
+            k_edge3<2><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ncol, ldb, p->E, p->N, nrhs, r0, rc);
         else
-            k_edge3<4><<<eg.G, 256, 0, s>>>(a);
+            k_edge3<4><<<ntile, 256, 0, s>>>(x, p->B32, ET, Ep, p->NT, ncol, ldb, p->E, p->N, nrhs, r0, rc);
         ZT_CUDA(cudaGetLastError());
     }
+    if (et_ready) ZT_CUDA(cudaEventRecord(et_ready, s));
+    KScope ks(K_MISC, s);
+    const int64_t rows = (int64_t)nrhs * p->E;
+    k_edge3_finish<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(Ep, y, p->NT, p->E, p->N, nrhs, ntile);
+    ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
 }
 
@@ -970,8 +910,8 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
             ZT_TRY(tc_edge(p, nrhs, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), w, br,
                            p->ev_et));
         } else if (sizeof(R) == sizeof(float)) {
-            ZT_TRY(launch_edge3(p, nrhs, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), w, br));
-            ZT_CUDA(cudaEventRecord(p->ev_et, br));
+            ZT_TRY(launch_edge3(p, nrhs, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), w, br,
+                                p->ev_et));
         } else {
             ZT_TRY(launch_edge<R>(p, nrhs, x, y, w, br, true));
             ZT_CUDA(cudaEventRecord(p->ev_et, br));
