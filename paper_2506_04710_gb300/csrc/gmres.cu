@@ -1281,9 +1281,10 @@ static ztoep_status_t member_products(const Member *mem, int n, bool fp32, bool 
 // The Arnoldi step is k_dots + k_upd, whose last CTA runs the iteration
 // control; a RHS that asks for a second Gram-Schmidt pass makes it set the IF
 // node that runs k_dots<2>, k_upd<2> and the iteration control instead.  The
-// Givens rotations of a step's column run in the next iteration on a branch
-// beside its products (k_givens), and after the loop for the last column, so
-// the end of a cycle is seen one step late: that step's work is discarded.  In a
+// Givens rotations of a step's column run in the next iteration (k_givens; for
+// one system on a branch beside its product, for a group after the members'
+// products) and after the loop for the last column, so the end of a cycle is
+// seen one step late: that step's work is discarded.  In a
 // group of several members, each member's iteration product sits in its own
 // IF node (members with no RHS in a cycle skip it) and the members' products
 // run concurrently; every other kernel is one launch for all members.
@@ -1366,21 +1367,27 @@ static ztoep_status_t build_graph(const Member *mem, int n, SolveGraph &sg, int 
         for (int i = 0; i < n; ++i)
             ZT_CUDA(cudaGraphConditionalHandleCreate(&g.h_prod[i], body_iter, 1, cudaGraphCondAssignDefault));
     ZT_TRY(capture_begin(s, body_iter, &sg.k_iter));
-    // the previous column's rotations on a branch beside the products
-    cudaEvent_t ev_g0 = nullptr, ev_g1 = nullptr;
-    ZT_TRY(ce.make(&ev_g0));
-    ZT_TRY(ce.make(&ev_g1));
-    ZT_CUDA(cudaEventRecord(ev_g0, s));
-    ZT_CUDA(cudaStreamWaitEvent(p0->aux, ev_g0, 0));
-    ZT_TRY(launch_givens(g, false, p0->aux));
-    ZT_CUDA(cudaEventRecord(ev_g1, p0->aux));
-    if (g.prod_if)
+    if (g.prod_if) {
+        // members' products in IF nodes (all roots of the body), then the
+        // previous column's rotations: a kernel root beside several IF roots
+        // stalled the graph on GB300 (5 members), this order did not
         ZT_TRY(add_conditionals(s, g.h_prod, n, cudaGraphCondTypeIf, body_prod));
-    else if (mixed)
-        ZT_TRY(run_matvec<float>(p0, mem[0].nrhs, (const float2 *)p0->ws32.xin, (float2 *)p0->ws32.yout, s));
-    else
-        ZT_TRY(run_matvec<double>(p0, mem[0].nrhs, p0->sws.xin64, p0->sws.w, s));
-    ZT_CUDA(cudaStreamWaitEvent(s, ev_g1, 0));
+        ZT_TRY(launch_givens(g, false, s));
+    } else {
+        // the previous column's rotations on a branch beside the product
+        cudaEvent_t ev_g0 = nullptr, ev_g1 = nullptr;
+        ZT_TRY(ce.make(&ev_g0));
+        ZT_TRY(ce.make(&ev_g1));
+        ZT_CUDA(cudaEventRecord(ev_g0, s));
+        ZT_CUDA(cudaStreamWaitEvent(p0->aux, ev_g0, 0));
+        ZT_TRY(launch_givens(g, false, p0->aux));
+        ZT_CUDA(cudaEventRecord(ev_g1, p0->aux));
+        if (mixed)
+            ZT_TRY(run_matvec<float>(p0, mem[0].nrhs, (const float2 *)p0->ws32.xin, (float2 *)p0->ws32.yout, s));
+        else
+            ZT_TRY(run_matvec<double>(p0, mem[0].nrhs, p0->sws.xin64, p0->sws.w, s));
+        ZT_CUDA(cudaStreamWaitEvent(s, ev_g1, 0));
+    }
     ZT_TRY(ops.arnoldi(g, 1, s));
     ZT_TRY(add_conditional(s, g.h_reorth, cudaGraphCondTypeIf, &body_reorth));
     ZT_TRY(capture_end(s));
