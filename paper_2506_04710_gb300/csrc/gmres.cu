@@ -92,6 +92,7 @@ struct GArgs {
     double2 *H, *cs, *sn, *g, *h1, *h2;
     double2 *part;     // [cap][nchunk + ngroups][pstride] chunk and group partial sums
     double *beta;      // [cap][m+1] ||u_k||
+    double *ibeta;     // [cap][m+1] 1 / ||u_k||, stored with beta (no division on the step kernels)
     double2 *xin64;    // [cap][N] FP64 copy of the next product input (FP64)
     double2 *rbuf;     // [cap][N] FP64 residual r of the sweep
     double2 *dbuf;     // [cap][N] correction d of the sweep
@@ -345,6 +346,7 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_residual(const __gr
         st[ST_INNER] = 1;
         nm[NM_RIN] = rn;
         a.beta[(int64_t)rr * (a.m + 1)] = rn;
+        a.ibeta[(int64_t)rr * (a.m + 1)] = 1.0 / rn;
         const double floor_abs = 0.5 * a.ctl->tol * vn;
         nm[NM_TARGET] = a.mixed ? fmax(a.ctl->inner_tol * rn, floor_abs) : floor_abs;
         double2 *gg = a.g + (int64_t)rr * (a.m + 1);
@@ -437,7 +439,9 @@ __device__ void column_decision(const GArgs &a, int rr, int j, const double2 *hs
         const int again = !(wn2 > kReorthEta * kReorthEta * w2);
         st[ST_REORTH] = again;
         if (!again) {
-            a.beta[(int64_t)rr * (m + 1) + j + 1] = sqrt(wn2);
+            const double bn = sqrt(wn2);
+            a.beta[(int64_t)rr * (m + 1) + j + 1] = bn;
+            a.ibeta[(int64_t)rr * (m + 1) + j + 1] = 1.0 / bn;
             st[ST_COLUMN] = 1;
         }
     }
@@ -521,11 +525,10 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(cons
     if (PASS == 2 && !st[ST_REORTH]) return;
     const int j = a.ctl->j;
     if (j >= a.m) return;
-    const double *beta = a.beta + (int64_t)rr * (a.m + 1);
     double2 *un = basis(a, j + 1, rr);
     double2 wv[ELEM];
     int64_t ix[ELEM];
-    const double sc = 1.0 / beta[j];
+    const double sc = a.ibeta[(int64_t)rr * (a.m + 1) + j];
 #pragma unroll
     for (int e = 0; e < ELEM; ++e) {
         ix[e] = elem_index(a, L.cx, e);
@@ -551,12 +554,9 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(cons
     for (int k0 = 0; k0 < K; k0 += 8) dots_group<ELEM>(a, rr, j, k0, K, PASS == 1, wv, ix, wred);
     __syncthreads();
     double2 *row = part_rows(a, rr) + (int64_t)L.cx * a.pstride;
-    const int nw = blockDim.x >> 5;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        double2 s = wred[0][k];
-        for (int w = 1; w < nw; ++w) s = s + wred[w][k];
-        row[k] = s;
-    }
+    for (int k = threadIdx.x; k < K; k += blockDim.x)  // the 8 warps' sums, pairwise
+        row[k] = ((wred[0][k] + wred[1][k]) + (wred[2][k] + wred[3][k])) +
+                 ((wred[4][k] + wred[5][k]) + (wred[6][k] + wred[7][k]));
     if (!reduce_rows(a, rr, L.cx, K, tot)) return;
     double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
     for (int k = threadIdx.x; k < K; k += blockDim.x) h[k] = tot[k];  // (PASS 1: ||w||^2 in slot j+1)
@@ -647,10 +647,10 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(const
         const int j = a.ctl->j;
         const bool work = st[ST_ACTIVE] && (PASS == 1 || st[ST_REORTH]) && j < a.m;
         if (work) {
-            const double *beta = a.beta + (int64_t)rr * (a.m + 1);
+            const double *ibeta = a.ibeta + (int64_t)rr * (a.m + 1);
             const double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
             for (int k = threadIdx.x; k <= j; k += blockDim.x) {
-                const double ib = 1.0 / beta[k];
+                const double ib = ibeta[k];
                 const double2 hk = cscale(__ldcg(h + k), ib);
                 hs[k] = hk;
                 cf[k] = cscale(hk, ib);
@@ -711,7 +711,9 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(const
                         for (int kk = threadIdx.x; kk <= j; kk += blockDim.x)
                             H[(int64_t)kk * m + j] = __ldcg(H + (int64_t)kk * m + j) + hs[kk];  // h1 + h2
                         if (threadIdx.x == 0) {
-                            a.beta[(int64_t)rr * (m + 1) + j + 1] = sqrt(tot[0].x);
+                            const double bn = sqrt(tot[0].x);
+                            a.beta[(int64_t)rr * (m + 1) + j + 1] = bn;
+                            a.ibeta[(int64_t)rr * (m + 1) + j + 1] = 1.0 / bn;
                             st[ST_REORTH] = 0;
                             st[ST_COLUMN] = 1;
                         }
@@ -767,20 +769,27 @@ __global__ void k_iter_ctl(const __grid_constant__ GroupArgs g) { iteration_cont
 // Least squares of a finished cycle: R y = g with R the leading jl x jl
 // upper triangle of the rotated Hessenberg matrix; ys[k] = y_k / beta_k.
 // Every CTA of the RHS solves it (the same arithmetic, so the same result):
-// R is staged in shared memory by all threads and one warp runs the
-// column-oriented back substitution (lane l keeps the running right-hand side
-// of row l).  Cycles longer than 32 fall back to one thread reading R from
-// global memory.
+// R is staged in shared memory by all threads, the reciprocals of its
+// diagonal are formed in parallel (so no division sits in the serial chain:
+// a dependent FP64 operation costs hundreds of cycles on this GPU), and one
+// warp runs the column-oriented back substitution (lane l keeps the running
+// right-hand side of row l).  Cycles longer than 32 fall back to one thread
+// reading R from global memory.
 __device__ void cycle_least_squares(const GArgs &a, int rr, int jl, double2 *ys) {
     __shared__ double2 Rs[32 * 32];
+    __shared__ double2 rinv[32];
     const int m = a.m;
     const double2 *H = a.H + (int64_t)rr * (m + 1) * m;
     const double2 *g = a.g + (int64_t)rr * (m + 1);
-    const double *beta = a.beta + (int64_t)rr * (m + 1);
+    const double *ibeta = a.ibeta + (int64_t)rr * (m + 1);
     if (jl <= 32) {
         for (int idx = threadIdx.x; idx < jl * jl; idx += blockDim.x) {
             const int i = idx / jl, l = idx - i * jl;
             if (l >= i) Rs[i * 32 + l] = __ldcg(H + i * m + l);
+        }
+        if (threadIdx.x < jl) {
+            const double2 rii = __ldcg(H + threadIdx.x * m + threadIdx.x);
+            rinv[threadIdx.x] = (rii.x != 0.0 || rii.y != 0.0) ? cdiv(make_double2(1, 0), rii) : make_double2(0, 0);
         }
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -789,9 +798,8 @@ __device__ void cycle_least_squares(const GArgs &a, int rr, int jl, double2 *ys)
             for (int i = jl - 1; i >= 0; --i) {
                 double2 yi = make_double2(0, 0);
                 if (lane == i) {
-                    const double2 rii = Rs[i * 32 + i];
-                    yi = (rii.x != 0.0 || rii.y != 0.0) ? cdiv(sl, rii) : make_double2(0, 0);
-                    ys[i] = cscale(yi, 1.0 / beta[i]);
+                    yi = cmul(sl, rinv[i]);
+                    ys[i] = cscale(yi, ibeta[i]);
                 }
                 yi = shfl_idx2(yi, i);
                 if (lane < i) sl = sl - cmul(Rs[lane * 32 + i], yi);
@@ -804,7 +812,7 @@ __device__ void cycle_least_squares(const GArgs &a, int rr, int jl, double2 *ys)
             for (int l = i + 1; l < jl; ++l) sacc = sacc - cmul(__ldcg(H + i * m + l), yv[l]);
             const double2 rii = __ldcg(H + i * m + i);
             yv[i] = (rii.x != 0.0 || rii.y != 0.0) ? cdiv(sacc, rii) : make_double2(0, 0);
-            ys[i] = cscale(yv[i], 1.0 / beta[i]);
+            ys[i] = cscale(yv[i], ibeta[i]);
         }
     }
     __syncthreads();
@@ -894,6 +902,7 @@ template <int ELEM> __global__ void __launch_bounds__(256) k_inner_residual(cons
     st[ST_COLUMN] = 0;
     st[ST_END] = 0;
     a.beta[(int64_t)rr * (a.m + 1)] = rin;
+    a.ibeta[(int64_t)rr * (a.m + 1)] = 1.0 / rin;
     double2 *gg = a.g + (int64_t)rr * (a.m + 1);
     gg[0] = make_double2(rin, 0);
     for (int i = 1; i <= a.m; ++i) gg[i] = make_double2(0, 0);
@@ -1039,7 +1048,7 @@ static ztoep_status_t ensure_solve_ws(ztoep_plan_t p, int nrhs, int m) {
     ZT_TRY(dalloc((void **)&w.h1, sizeof(double2) * (size_t)nrhs * (m + 1), &acc));
     ZT_TRY(dalloc((void **)&w.h2, sizeof(double2) * (size_t)nrhs * (m + 1), &acc));
     ZT_TRY(dalloc((void **)&w.part, sizeof(double2) * (size_t)nrhs * (gm.nchunk + ngroups) * pstride, &acc));
-    ZT_TRY(dalloc((void **)&w.nrm, sizeof(double) * (size_t)nrhs * (NM_STRIDE + m + 1), &acc));
+    ZT_TRY(dalloc((void **)&w.nrm, sizeof(double) * (size_t)nrhs * (NM_STRIDE + 2 * (m + 1)), &acc));
     ZT_TRY(dalloc((void **)&w.st, sizeof(int) * (size_t)nrhs * ST_STRIDE, &acc));
     ZT_TRY(dalloc((void **)&w.cnt, sizeof(unsigned) * (size_t)nrhs * cstride, &acc));
     ZT_TRY(dalloc((void **)&w.ctl, sizeof(SolveCtl), &acc));
@@ -1066,7 +1075,8 @@ static GArgs make_args(ztoep_plan_t p, int nrhs, int m, bool mixed, SolveCtl *ct
     a.Vb = w.Vb; a.w = w.w; a.x = w.xbuf; a.v = w.vbuf; a.xin64 = w.xin64; a.rbuf = w.rbuf; a.dbuf = w.dbuf;
     a.x32 = (float2 *)p->ws32.xin; a.y32 = (const float2 *)p->ws32.yout;
     a.H = w.H; a.cs = w.cs; a.sn = w.sn; a.g = w.g; a.h1 = w.h1; a.h2 = w.h2; a.part = w.part;
-    a.nrm = w.nrm; a.beta = w.nrm + (size_t)w.cap * NM_STRIDE; a.st = w.st; a.cnt = w.cnt;
+    a.nrm = w.nrm; a.beta = w.nrm + (size_t)w.cap * NM_STRIDE; a.ibeta = a.beta + (size_t)w.cap * (w.m + 1);
+    a.st = w.st; a.cnt = w.cnt;
     a.ctl = ctl;
     a.N = p->N; a.cap = w.cap; a.m = m; a.nchunk = gm.nchunk; a.per_cta = gm.per_cta;
     a.ngroups = (gm.nchunk + kRedGroup - 1) / kRedGroup; a.cstride = w.cstride; a.pstride = w.m + 2;
