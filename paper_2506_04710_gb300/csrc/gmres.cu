@@ -196,23 +196,32 @@ __device__ __forceinline__ double block_sum1(double v, double *red) {
     return s;
 }
 
-// out[k] = sum_{i < n} src[i * stride + k] for k < K, whole CTA: each
-// thread first adds a contiguous run of rows in order (one row when
-// n <= blockDim), then a pairwise tree over the runs through shared memory
-// `scr` (blockDim entries).  The order depends only on n, K and blockDim, and
-// the dependent FP64 chain is about log2(n) adds long.
+// out[k] = sum_{i < n} src[i * stride + k] for k < K, whole CTA: P threads
+// per column (a power of two, with P x K <= blockDim so that all columns are
+// done in one pass) each add a contiguous run of rows in order, then a
+// pairwise tree over the P runs through shared memory `scr` (blockDim
+// entries).  The order depends only on n, K and blockDim; the dependent FP64
+// chain is about n / P + log2(P) adds long.
 __device__ void tree_sum(const double2 *src, int n, int64_t stride, int K, double2 *out, double2 *scr) {
     int P = 1;
-    while (P < n && P < (int)blockDim.x) P <<= 1;
+    while (2 * P * K <= (int)blockDim.x && P < n) P <<= 1;
     const int run = (n + P - 1) / P;
-    const int per = blockDim.x / P;  // columns per pass
+    const int per = blockDim.x / P;  // columns per pass (>= K unless K > blockDim)
     const int i = threadIdx.x % P, kk = threadIdx.x / P;
     for (int kb = 0; kb < K; kb += per) {
         const int k = kb + kk;
         double2 v = make_double2(0, 0);
         if (k < K && kk < per) {
             const int r0 = i * run, r1 = min(n, r0 + run);
-            for (int r = r0; r < r1; ++r) v = v + __ldcg(src + (int64_t)r * stride + k);
+            double2 t[8];
+            int r = r0;
+            for (; r + 8 <= r1; r += 8) {  // loads in flight together, adds in row order
+#pragma unroll
+                for (int q = 0; q < 8; ++q) t[q] = __ldcg(src + (int64_t)(r + q) * stride + k);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v = v + t[q];
+            }
+            for (; r < r1; ++r) v = v + __ldcg(src + (int64_t)r * stride + k);
         }
         scr[threadIdx.x] = v;
         __syncthreads();
