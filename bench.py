@@ -770,8 +770,19 @@ def section_c4(args, dev, local):
             "ms_per_iteration": ms64 / max(1, it_64)}
     if st64 == 0:
         fp64["rhs_solves_per_s"] = nrhs / (ms64 / 1e3)
+    # FFT passes of the FP32 product at this size (kernels alone, clocks above):
+    # x pass (Nx + Lx) Ny b r, y pass (Ny + Ly) Lx b r complex64 read + written
+    lx, ly = plan.info.lx, plan.info.ly
+    fft_bytes = 2 * ((prob.nx + lx) * prob.ny + (prob.ny + ly) * lx) * prob.b * nrhs * 8
+    fft_us = classes.get("fft", {}).get("us_per_product")
+    hbm = peaks().get("hbm_gbs")
+    fft_passes = {"bytes_per_product": fft_bytes, "us_per_product": fft_us,
+                  "GB/s": fft_bytes / fft_us / 1e3 if fft_us else None,
+                  "frac_of_hbm": fft_bytes / fft_us / 1e3 / hbm if (fft_us and hbm) else None,
+                  "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     return {"workload": "64x64 array, b=96 (393,216 Toeplitz + 1,024 edge unknowns), 32 plane-wave RHS, "
                         "GMRES(30)-IR to rel. residual 1e-8",
+            "fft_passes": fft_passes,
             "n": prob.n, "nrhs": nrhs, "lx": plan.info.lx, "ly": plan.info.ly,
             "host_generation_s": gen_s, "plan_and_autotune_s": plan_s,
             "mixed": {"status": ztoep.ztoep_status_string(st), "ms_per_solve": ms,
