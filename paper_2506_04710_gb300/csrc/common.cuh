@@ -135,7 +135,6 @@ struct SolveWs {  // Krylov workspace, sized for `cap` RHS and restart `m`
     double2 *cs = nullptr;     // [cap][m]
     double2 *sn = nullptr;     // [cap][m]
     double2 *g = nullptr;      // [cap][m+1]
-    double2 *y = nullptr;      // [cap][m] least-squares solution
     double2 *h1 = nullptr;     // [cap][m+1]
     double2 *h2 = nullptr;     // [cap][m+1]
     double2 *part = nullptr;   // [cap][nchunk + ngroups][m+2] chunk and group partial sums

@@ -40,7 +40,7 @@ enum { ST_ACTIVE = 0, ST_JLEN = 1, ST_ITERS = 2, ST_STATUS = 3, ST_OUTER = 4, ST
 // beta stored) and waits for its Givens rotations, which run beside the next
 // step's product.
 enum { RS_RUNNING = 0, RS_CONVERGED = 1, RS_NONFINITE = 2, RS_MAXITER = 3 };
-enum { NM_VNORM = 0, NM_TARGET = 2, NM_RNORM = 3, NM_W0 = 5, NM_RIN = 6, NM_STRIDE = 8 };
+enum { NM_VNORM = 0, NM_TARGET = 2, NM_RNORM = 3, NM_RIN = 6, NM_STRIDE = 8 };
 // Inner (FP32-residual) restarts of one sweep: at most this many, and they stop
 // early when a restart reduces the inner residual by less than 10%.
 constexpr int kMaxRestarts = 64;
@@ -1006,7 +1006,7 @@ void free_solve_ws(ztoep_plan_t p) {
     free_solve_graphs(p);
     SolveWs &w = p->sws;
     cudaFree(w.Vb); cudaFree(w.w); cudaFree(w.xin64); cudaFree(w.vbuf); cudaFree(w.xbuf); cudaFree(w.rbuf); cudaFree(w.dbuf); cudaFree(w.H);
-    cudaFree(w.cs); cudaFree(w.sn); cudaFree(w.g); cudaFree(w.y); cudaFree(w.h1); cudaFree(w.h2);
+    cudaFree(w.cs); cudaFree(w.sn); cudaFree(w.g); cudaFree(w.h1); cudaFree(w.h2);
     cudaFree(w.part); cudaFree(w.nrm); cudaFree(w.st); cudaFree(w.cnt); cudaFree(w.ctl);
     if (w.hst) cudaFreeHost(w.hst);
     if (w.hnrm) cudaFreeHost(w.hnrm);
@@ -1053,7 +1053,6 @@ static ztoep_status_t ensure_solve_ws(ztoep_plan_t p, int nrhs, int m) {
     ZT_TRY(dalloc((void **)&w.cs, sizeof(double2) * (size_t)nrhs * m, &acc));
     ZT_TRY(dalloc((void **)&w.sn, sizeof(double2) * (size_t)nrhs * m, &acc));
     ZT_TRY(dalloc((void **)&w.g, sizeof(double2) * (size_t)nrhs * (m + 1), &acc));
-    ZT_TRY(dalloc((void **)&w.y, sizeof(double2) * (size_t)nrhs * m, &acc));
     ZT_TRY(dalloc((void **)&w.h1, sizeof(double2) * (size_t)nrhs * (m + 1), &acc));
     ZT_TRY(dalloc((void **)&w.h2, sizeof(double2) * (size_t)nrhs * (m + 1), &acc));
     ZT_TRY(dalloc((void **)&w.part, sizeof(double2) * (size_t)nrhs * (gm.nchunk + ngroups) * pstride, &acc));
