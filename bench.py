@@ -1140,7 +1140,7 @@ def run_product(args, local):
     tensor = nr >= 16
     spec = F * b * b * 8 if tensor else plan.info.n_pairs * b * b * 8
     k = prob.edge_per_cell
-    bedge = (2 * 4 * k * F * b * 8 if structured else (2 if tensor else 1) * E * NT * 8) + E * E * 8
+    bedge = (4 * k * F * b * 8 if structured else (2 if tensor else 1) * E * NT * 8) + E * E * 8
     byts = spec + bedge + 2 * NT * nr * 8 + 4 * F * b * nr * 8
     flops = 8.0 * F * b * b * nr + (16.0 * 4 * k * F * b * nr if structured else 16.0 * E * NT * nr)
     pk = peaks()

@@ -117,7 +117,7 @@ struct MatvecWs {  // per-precision matvec workspace, sized for `cap` RHS
     void *ET = nullptr;     // [nsplit][cap][NT] B^T x_E partial sums
     void *Ep = nullptr;     // B x_T partial sums: k_edge3 [cap][E][ntile], else [ntile or K split][cap][E]
     void *Yh = nullptr;     // [F][cap][b] out-of-place block-product output (tensor path, side plans)
-    void *Fs = nullptr;     // [4k][cap][Lmax] side products B x_T along each side, frequency domain
+    void *Ps = nullptr;     // [blocks][4k][cap][Lmax] partials of B x_T along each side, frequency domain
     void *Us = nullptr;     // [cap][4k][Lmax] DFTs of the side slices of x_E
     size_t bytes = 0;
 };
@@ -238,15 +238,20 @@ constexpr int kTcMaxRhs = 256;
 ztoep_status_t ensure_tensor_data(ztoep_plan_t p, int nrhs, cudaStream_t s);
 // Perimeter side-Toeplitz edge coupling (sides.cu): plan-time generator
 // spectra from B; per product: DFTs of the side slices of x_E (sides_uhat),
-// B x_T from X^ and y_E (sides_edge_rows), and the B^T x_E terms added to Y^
-// after the block product (sides_add).
+// after the block product one pass over the spectra that adds the B^T x_E
+// terms to Y^ and leaves the partials of B x_T (sides_fused), and y_E from
+// those partials and C (sides_finish).  sides_partials: partial-sum elements
+// per RHS.
 ztoep_status_t sides_build(ztoep_plan_t p, const double2 *B, cudaStream_t s, size_t *acc);
 template <typename R>
 ztoep_status_t sides_uhat(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, MatvecWs &w, cudaStream_t s);
 template <typename R>
-ztoep_status_t sides_edge_rows(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, const cplx_t<R> *Xh, cplx_t<R> *y,
-                               MatvecWs &w, cudaStream_t s);
-template <typename R> ztoep_status_t sides_add(ztoep_plan_t p, int nrhs, cplx_t<R> *Yh, MatvecWs &w, cudaStream_t s);
+ztoep_status_t sides_fused(ztoep_plan_t p, int nrhs, const cplx_t<R> *Xh, cplx_t<R> *Yh, MatvecWs &w,
+                           cudaStream_t s);
+template <typename R>
+ztoep_status_t sides_finish(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *y, MatvecWs &w,
+                            cudaStream_t s);
+int64_t sides_partials(ztoep_plan_t p);
 template <typename R> MatvecWs &ws_of(ztoep_plan_t p);
 template <typename R>
 ztoep_status_t run_forward_spectrum(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R> *Xh,

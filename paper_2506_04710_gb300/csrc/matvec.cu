@@ -24,13 +24,14 @@ namespace ztoep {
 
 // ------------------------------------------------------------ block product
 // One CTA per frequency pair {f, -f}: T^[f] (b x b, row-major) is staged in
-// shared memory once and used for both Xh[f] <- T^[f] Xh[f] (row products,
+// shared memory once and used for both Yh[f] <- T^[f] Xh[f] (row products,
 // each thread walks its row with a skew so that a warp hits distinct banks)
-// and Xh[-f] <- T^[f]^T Xh[-f] (column products, contiguous across threads).
+// and Yh[-f] <- T^[f]^T Xh[-f] (column products, contiguous across threads).
+// Yh may be Xh (in place): each RHS chunk is staged before it is written.
 template <typename R>
 __global__ void __launch_bounds__(256) k_blockprod(const int2 *__restrict__ pairs, int npairs,
                                                    const cplx_t<R> *__restrict__ That,
-                                                   cplx_t<R> *Xh, int b, int nrhs, int rch) {
+                                                   const cplx_t<R> *Xh, cplx_t<R> *Yh, int b, int nrhs, int rch) {
     using C = cplx_t<R>;
     extern __shared__ __align__(16) unsigned char zt_smem[];
     C *sT = reinterpret_cast<C *>(zt_smem);
@@ -44,8 +45,10 @@ __global__ void __launch_bounds__(256) k_blockprod(const int2 *__restrict__ pair
         for (int r0 = 0; r0 < nrhs; r0 += rch) {
             const int rc = min(rch, nrhs - r0);
             const int cb = rc * b;
-            C *xf = Xh + (size_t)f * rb + (size_t)r0 * b;
-            C *xg = Xh + (size_t)g * rb + (size_t)r0 * b;
+            const C *xf = Xh + (size_t)f * rb + (size_t)r0 * b;
+            const C *xg = Xh + (size_t)g * rb + (size_t)r0 * b;
+            C *yf = Yh + (size_t)f * rb + (size_t)r0 * b;
+            C *yg = Yh + (size_t)g * rb + (size_t)r0 * b;
             for (int t = threadIdx.x; t < cb; t += blockDim.x) {
                 sf[t] = xf[t];
                 if (g != f) sg[t] = xg[t];
@@ -63,13 +66,13 @@ __global__ void __launch_bounds__(256) k_blockprod(const int2 *__restrict__ pair
                         acc = cfma(row[j], xv[j], acc);
                         if (++j == b) j = 0;
                     }
-                    xf[o] = acc;
+                    yf[o] = acc;
                 } else {
                     const int o2 = o - cb;
                     const int rr = o2 / b, j = o2 - rr * b;
                     const C *xv = sg + (size_t)rr * b;
                     for (int i = 0; i < b; ++i) acc = cfma(sT[(size_t)i * b + j], xv[i], acc);
-                    xg[o2] = acc;
+                    yg[o2] = acc;
                 }
             }
             __syncthreads();
@@ -595,7 +598,7 @@ static int tc_edge_splits(ztoep_plan_t p) { return cgemm_splits((int)p->NT, tc_e
 
 static void free_ws(MatvecWs &w) {
     cudaFree(w.xin); cudaFree(w.yout); cudaFree(w.X1); cudaFree(w.Xh); cudaFree(w.ET); cudaFree(w.Ep); cudaFree(w.Yh);
-    cudaFree(w.Fs); cudaFree(w.Us);
+    cudaFree(w.Ps); cudaFree(w.Us);
     w = MatvecWs{};
 }
 
@@ -614,9 +617,8 @@ template <typename R> ztoep_status_t ensure_ws(ztoep_plan_t p, int nrhs) {
     ZT_TRY(dalloc(&w.Xh, cs * nrhs * (size_t)p->F * p->b, &acc));
     const bool tc = cs == 8 && nrhs >= kTcMinRhs;
     if (p->E > 0 && p->side_k > 0) {  // side products: small frequency-domain buffers only
-        const size_t side = cs * (size_t)4 * p->side_k * nrhs * std::max(p->lx, p->ly);
-        ZT_TRY(dalloc(&w.Fs, side, &acc));
-        ZT_TRY(dalloc(&w.Us, side, &acc));
+        ZT_TRY(dalloc(&w.Ps, cs * (size_t)nrhs * sides_partials(p), &acc));
+        ZT_TRY(dalloc(&w.Us, cs * (size_t)4 * p->side_k * nrhs * std::max(p->lx, p->ly), &acc));
     } else if (p->E > 0) {
         ZT_TRY(dalloc(&w.ET, cs * (size_t)std::max(nsplit, 1) * nrhs * p->NT, &acc));
         const int parts = std::max(cs == 8 ? edge3_ntile(p) : ntile, tc ? tc_edge_splits(p) : 0);
@@ -713,9 +715,8 @@ template <typename R> static bool blockprod_pipelined(ztoep_plan_t p, int nrhs) 
     return tbytes % 16 == 0 && xbytes % 16 == 0 && 2 * (tbytes + 2 * xbytes) <= 200 * 1024;
 }
 
-// Block product on the pipelined kernel when it applies (out may differ from
-// Xh there: out-of-place output), else the in-place fallback (UNSUPPORTED if an
-// out-of-place output was asked for).
+// Block product on the pipelined kernel when it applies, else the staged
+// fallback; `out` (default Xh: in place) receives Y^.
 template <typename R>
 static ztoep_status_t launch_blockprod(ztoep_plan_t p, int nrhs, cplx_t<R> *Xh, cudaStream_t s,
                                        cplx_t<R> *out = nullptr) {
@@ -760,7 +761,6 @@ static ztoep_status_t launch_blockprod(ztoep_plan_t p, int nrhs, cplx_t<R> *Xh, 
         ZT_CUDA(cudaGetLastError());
         return ZTOEP_OK;
     }
-    if (out != Xh) return ZTOEP_ERR_UNSUPPORTED;  // the fallback works in place
     if (tbytes + 2 * cs * p->b > budget) return ZTOEP_ERR_UNSUPPORTED;
     const int rch = (int)std::min<size_t>((size_t)nrhs, (budget - tbytes) / (2 * cs * p->b));
     const size_t smem = tbytes + 2 * cs * (size_t)rch * p->b;
@@ -769,7 +769,7 @@ static ztoep_status_t launch_blockprod(ztoep_plan_t p, int nrhs, cplx_t<R> *Xh, 
         ZT_CUDA(cudaFuncSetAttribute(k_blockprod<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         attr = true;
     }
-    k_blockprod<R><<<p->npairs, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, p->b, nrhs, rch);
+    k_blockprod<R><<<p->npairs, 256, smem, s>>>(p->pairs, p->npairs, that_of<R>(p), Xh, out, p->b, nrhs, rch);
     ZT_CUDA(cudaGetLastError());
     return ZTOEP_OK;
 }
@@ -917,32 +917,29 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
             ZT_CUDA(cudaEventRecord(p->ev_et, br));
         }
         ZT_CUDA(cudaEventRecord(p->ev_join, br));
+    } else if (sides) {  // side stream: the DFTs of the side slices of x_E beside the forward passes
+        ZT_CUDA(cudaEventRecord(p->ev_fork, s));
+        ZT_CUDA(cudaStreamWaitEvent(br, p->ev_fork, 0));
+        ZT_TRY(sides_uhat<R>(p, nrhs, x, w, br));
+        ZT_CUDA(cudaEventRecord(p->ev_et, br));
     }
     ZT_TRY(forward_passes<R>(p, nrhs, x, X1, Xh, s));
     cplx_t<R> *Yh = Xh;
-    bool side_branch = false;
     if (sides) {
-        // side stream: B x_T from X^ and y_E; main: U, the block product out of
-        // place (X^ stays intact for the side stream), then the B^T x_E terms
+        // block product out of place (X^ stays for B x_T), both side products
+        // in one pass over the generator spectra, then y_E on the side stream
+        // beside the inverse passes
         Yh = reinterpret_cast<cplx_t<R> *>(w.Yh);
-        ZT_TRY(sides_uhat<R>(p, nrhs, x, w, s));
-        if (tc || blockprod_pipelined<R>(p, nrhs)) {
-            ZT_CUDA(cudaEventRecord(p->ev_fork, s));  // X^ ready; the two branches only read it
-            ZT_CUDA(cudaStreamWaitEvent(br, p->ev_fork, 0));
-            ZT_TRY(sides_edge_rows<R>(p, nrhs, x, Xh, y, w, br));
-            ZT_CUDA(cudaEventRecord(p->ev_join, br));
-            if (tc)
-                ZT_TRY(tc_blockprod(p, nrhs, reinterpret_cast<const float2 *>(Xh), reinterpret_cast<float2 *>(Yh), s));
-            else
-                ZT_TRY(launch_blockprod<R>(p, nrhs, Xh, s, Yh));
-            ZT_TRY(sides_add<R>(p, nrhs, Yh, w, s));
-            side_branch = true;
-        } else {
-            ZT_TRY(sides_edge_rows<R>(p, nrhs, x, Xh, y, w, s));  // reads X^ before the in-place product
-            Yh = Xh;
-            ZT_TRY(launch_blockprod<R>(p, nrhs, Xh, s));
-            ZT_TRY(sides_add<R>(p, nrhs, Yh, w, s));
-        }
+        if (tc)
+            ZT_TRY(tc_blockprod(p, nrhs, reinterpret_cast<const float2 *>(Xh), reinterpret_cast<float2 *>(Yh), s));
+        else
+            ZT_TRY(launch_blockprod<R>(p, nrhs, Xh, s, Yh));
+        ZT_CUDA(cudaStreamWaitEvent(s, p->ev_et, 0));  // U from the side stream
+        ZT_TRY(sides_fused<R>(p, nrhs, Xh, Yh, w, s));
+        ZT_CUDA(cudaEventRecord(p->ev_fork, s));
+        ZT_CUDA(cudaStreamWaitEvent(br, p->ev_fork, 0));
+        ZT_TRY(sides_finish<R>(p, nrhs, x, y, w, br));
+        ZT_CUDA(cudaEventRecord(p->ev_join, br));
     } else if (tc) {
         Yh = reinterpret_cast<cplx_t<R> *>(w.Yh);
         ZT_TRY(tc_blockprod(p, nrhs, reinterpret_cast<const float2 *>(Xh), reinterpret_cast<float2 *>(Yh), s));
@@ -965,7 +962,7 @@ ztoep_status_t run_matvec(ztoep_plan_t p, int nrhs, const cplx_t<R> *x, cplx_t<R
             return StYOut<R>{y, x, ET, act, p->nx, p->b, ib, nrhs, ns, p->N, p->NT, scale};
         },
         s)));
-    if ((p->E > 0 && !sides) || side_branch) ZT_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
+    if (p->E > 0) ZT_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
     return ZTOEP_OK;
 }
 template ztoep_status_t run_matvec<float>(ztoep_plan_t, int, const float2 *, float2 *, cudaStream_t);

@@ -20,7 +20,8 @@ def dev(a):
 
 SHAPES = [dict(nx=4, ny=4, b=8, k=1, seed=0), dict(nx=6, ny=5, b=12, k=2, seed=3),
           dict(nx=5, ny=7, b=6, k=3, seed=5), dict(nx=9, ny=4, b=40, k=1, seed=13),
-          dict(nx=3, ny=2, b=33, k=4, seed=9), dict(nx=1, ny=1, b=4, k=2, seed=2)]
+          dict(nx=3, ny=2, b=33, k=4, seed=9), dict(nx=1, ny=1, b=4, k=2, seed=2),
+          dict(nx=3, ny=3, b=70, k=8, seed=19), dict(nx=12, ny=10, b=20, k=4, seed=17)]
 
 
 def make(sh, nrhs):
@@ -41,6 +42,25 @@ def test_structured_products_match_dense_oracle(sh, nrhs):
     y32 = plan.matvec(Xd, ztoep.ZTOEP_MIXED).cpu().numpy()
     err = np.linalg.norm(y32 - ref, axis=1) / np.linalg.norm(ref, axis=1)
     assert err.max() <= 2e-6
+    plan.close()
+
+
+@pytest.mark.parametrize("nrhs", [1, 13, 17])
+def test_structured_products_many_tiles(nrhs):
+    """32x32 cells (64x64 embedding: many CTA tiles and partial blocks of the
+    fused side kernel, ragged RHS blocks) against the oracle's direct product."""
+    prob = synth.make_problem(32, 32, 16, 2 * 4 * 64, seed=31, rhs="planewave", nrhs=nrhs)
+    ref = oracle.matvec_blocks(prob, prob.V)
+    plan = ztoep.Plan.from_problem(prob, structured=True)
+    Xd = dev(prob.V)
+    y64 = plan.matvec(Xd, ztoep.ZTOEP_FP64).cpu().numpy()
+    assert np.max(np.abs(y64 - ref)) <= 1e-12 * np.max(np.abs(ref))
+    y32 = plan.matvec(Xd, ztoep.ZTOEP_MIXED).cpu().numpy()
+    err = np.linalg.norm(y32 - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= 2e-6
+    if nrhs < 16:  # same kernels alone and in the batch (16+ RHS: tensor-core block product)
+        one = plan.matvec(Xd[nrhs - 1:], ztoep.ZTOEP_MIXED).cpu().numpy()
+        assert np.array_equal(one[0], y32[nrhs - 1])
     plan.close()
 
 
