@@ -124,6 +124,7 @@ typedef struct {
     int32_t outer;        /* true-residual evaluations (refinement sweeps) */
     int32_t inner_iters;  /* Krylov iterations (matrix products) used */
     int32_t status;       /* ztoep_status_t for this RHS */
+    int32_t second_passes;  /* Arnoldi steps that took a second Gram-Schmidt pass */
     double rel_residual;  /* final ||v - Z x|| / ||v|| in FP64 */
 } ztoep_solve_info_t;
 

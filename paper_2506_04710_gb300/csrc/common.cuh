@@ -59,7 +59,10 @@ __host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return ma
 __host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
-__host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+// |a|^2 as one explicit fused multiply-add, so that the compiler cannot
+// contract it (or a sum it is added to) differently where it is inlined: the
+// same value in every kernel.
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
 
 // a / b by Smith's algorithm (R. L. Smith, CACM 5(8), 1962).
 __host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
@@ -137,7 +140,7 @@ struct SolveWs {  // Krylov workspace, sized for `cap` RHS and restart `m`
     double2 *g = nullptr;      // [cap][m+1]
     double2 *h1 = nullptr;     // [cap][m+1]
     double2 *h2 = nullptr;     // [cap][m+1]
-    double2 *part = nullptr;   // [cap][nchunk + ngroups][m+2] chunk and group partial sums
+    double2 *part = nullptr;   // [cap][rows][m+2] chunk partial sums and inner nodes of the reduction tree
     double *nrm = nullptr;     // [cap][8] scalars, then [cap][m+1] basis norms
     int *st = nullptr;         // [cap][8] per-RHS state
     unsigned *cnt = nullptr;   // [cap][cstride] last-arriver tickets of the cross-CTA sums

@@ -32,7 +32,7 @@
 namespace ztoep {
 
 enum { ST_ACTIVE = 0, ST_JLEN = 1, ST_ITERS = 2, ST_STATUS = 3, ST_OUTER = 4, ST_PENDING = 5, ST_REORTH = 6,
-       ST_INNER = 7, ST_RESTARTS = 8, ST_END = 9, ST_COLUMN = 10, ST_STRIDE = 12 };
+       ST_INNER = 7, ST_RESTARTS = 8, ST_END = 9, ST_COLUMN = 10, ST_PASSES2 = 11, ST_STRIDE = 12 };
 // ST_END: the column just finalised ends the cycle; the iteration control
 // turns it into ACTIVE = 0, PENDING = 1 once every kernel of the step is done
 // (the Arnoldi kernels of the step test ACTIVE, so it must not change under them).
@@ -52,7 +52,6 @@ constexpr double kStagnation = 0.9;
 // for it at every step on these systems, doubling the FP64 work).
 constexpr double kReorthEta = 1.0 / 64.0;
 // Chunks per first-level group of the cross-CTA reductions.
-constexpr int kRedGroup = 16;
 // Largest Gram-Schmidt column: j + 2 <= m + 1 with m <= 128.
 constexpr int kMaxK = 130;
 // Systems solved together in one group (one launch per step for all).
@@ -90,7 +89,7 @@ struct GArgs {
     float2 *x32;       // [cap][N] FP32 copy of the next product input (MIXED)
     const float2 *y32; // [cap][N] FP32 product output (MIXED)
     double2 *H, *cs, *sn, *g, *h1, *h2;
-    double2 *part;     // [cap][nchunk + ngroups][pstride] chunk and group partial sums
+    double2 *part;     // [cap][nrows][pstride] chunk partial sums and the reduction tree's inner nodes
     double *beta;      // [cap][m+1] ||u_k||
     double *ibeta;     // [cap][m+1] 1 / ||u_k||, stored with beta (no division on the step kernels)
     double2 *xin64;    // [cap][N] FP64 copy of the next product input (FP64)
@@ -101,7 +100,7 @@ struct GArgs {
     unsigned *cnt;     // [cap][cstride] reduction tickets
     SolveCtl *ctl;     // shared by the group
     int64_t N;
-    int cap, m, nchunk, per_cta, ngroups, cstride, pstride, nrhs;
+    int cap, m, nchunk, per_cta, nrows, cstride, pstride, nrhs;
     int mixed;
 };
 
@@ -144,7 +143,7 @@ __device__ __forceinline__ int64_t elem_index(const GArgs &a, int cx, int e) {
 }
 
 __device__ __forceinline__ double2 *part_rows(const GArgs &a, int rr) {
-    return a.part + (int64_t)rr * (a.nchunk + a.ngroups) * a.pstride;
+    return a.part + (int64_t)rr * a.nrows * a.pstride;
 }
 
 __device__ __forceinline__ double2 shfl_xor2(double2 v, int o) {
@@ -196,74 +195,88 @@ __device__ __forceinline__ double block_sum1(double v, double *red) {
     return s;
 }
 
-// out[k] = sum_{i < n} src[i * stride + k] for k < K, whole CTA: P threads
-// per column (a power of two, with P x K <= blockDim so that all columns are
-// done in one pass) each add a contiguous run of rows in order, then a
-// pairwise tree over the P runs through shared memory `scr` (blockDim
-// entries).  The order depends only on n, K and blockDim; the dependent FP64
-// chain is about n / P + log2(P) adds long.
-__device__ void tree_sum(const double2 *src, int n, int64_t stride, int K, double2 *out, double2 *scr) {
-    int P = 1;
-    while (2 * P * K <= (int)blockDim.x && P < n) P <<= 1;
-    const int run = (n + P - 1) / P;
-    const int per = blockDim.x / P;  // columns per pass (>= K unless K > blockDim)
-    const int i = threadIdx.x % P, kk = threadIdx.x / P;
-    for (int kb = 0; kb < K; kb += per) {
-        const int k = kb + kk;
-        double2 v = make_double2(0, 0);
-        if (k < K && kk < per) {
-            const int r0 = i * run, r1 = min(n, r0 + run);
-            double2 t[8];
-            int r = r0;
-            for (; r + 8 <= r1; r += 8) {  // loads in flight together, adds in row order
-#pragma unroll
-                for (int q = 0; q < 8; ++q) t[q] = __ldcg(src + (int64_t)(r + q) * stride + k);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) v = v + t[q];
-            }
-            for (; r < r1; ++r) v = v + __ldcg(src + (int64_t)r * stride + k);
-        }
-        scr[threadIdx.x] = v;
-        __syncthreads();
-        for (int h = P >> 1; h > 0; h >>= 1) {
-            if (i < h) scr[threadIdx.x] = scr[threadIdx.x] + scr[threadIdx.x + h];
-            __syncthreads();
-        }
-        if (i == 0 && k < K && kk < per) out[k] = scr[threadIdx.x];
-        __syncthreads();
+// Cross-CTA sums use one fixed tree over the chunks of a RHS: nodes of 16
+// chunks at the first level and of 32 nodes above, each node the pairwise
+// sum ((v0 + v1) + (v2 + v3)) + ... of its children, zero-padded to the full
+// fan-in.  The tree depends only on the chunk count, so a RHS is summed in the
+// same order alone, in any batch and in any group.
+constexpr int kFan0 = 16, kFanUp = 32;
+__host__ __device__ inline int tree_fan(int level) { return level == 0 ? kFan0 : kFanUp; }
+// Stored rows per RHS (every level but the root) and tickets (every node above the chunks).
+__host__ __device__ inline int tree_rows(int nchunk) {
+    int n = nchunk, rows = 0, l = 0;
+    while (true) {
+        const int np = (n + tree_fan(l) - 1) / tree_fan(l);
+        rows += n;
+        if (np == 1) return rows;
+        n = np;
+        ++l;
+    }
+}
+__host__ __device__ inline int tree_tickets(int nchunk) {
+    int n = nchunk, t = 0, l = 0;
+    while (true) {
+        const int np = (n + tree_fan(l) - 1) / tree_fan(l);
+        t += np;
+        if (np == 1) return t;
+        n = np;
+        ++l;
     }
 }
 
+// One node: the pairwise tree over FAN values ld(i) (i < nch, zero beyond).
+template <int FAN, typename Ld> __device__ __forceinline__ double2 fan_sum(int nch, Ld ld) {
+    double2 v[FAN];
+#pragma unroll
+    for (int i = 0; i < FAN; ++i) v[i] = i < nch ? ld(i) : make_double2(0, 0);
+#pragma unroll
+    for (int w = 1; w < FAN; w *= 2)
+#pragma unroll
+        for (int i = 0; i < FAN; i += 2 * w) v[i] = v[i] + v[i + w];
+    return v[0];
+}
+__device__ __forceinline__ double2 node_sum(int level, const double2 *src, int nch, int64_t stride, bool global) {
+    if (global) {
+        if (level == 0) return fan_sum<kFan0>(nch, [&](int i) { return __ldcg(src + i * stride); });
+        return fan_sum<kFanUp>(nch, [&](int i) { return __ldcg(src + i * stride); });
+    }
+    if (level == 0) return fan_sum<kFan0>(nch, [&](int i) { return src[i * stride]; });
+    return fan_sum<kFanUp>(nch, [&](int i) { return src[i * stride]; });
+}
+
 // Cross-CTA sum of one RHS's partial rows (chunk cx has written row cx,
-// columns 0..K-1).  The last CTA to finish in each group of kRedGroup chunks
-// adds the group's rows into a group row; the last group to finish adds the
-// group rows into tot[0..K) (shared memory).  Returns true in that one CTA
-// (all threads).  The tickets are last-arriver counters that reset
-// themselves; nothing waits.  The order depends only on nchunk and K.
+// columns 0..K-1): the last CTA to finish among a node's children forms the
+// node (a row of the next level), and so on up; the CTA that forms the root
+// writes it to tot[0..K) (shared memory) and returns true (all threads).  The
+// tickets are last-arriver counters that reset themselves; nothing waits.
 __device__ bool reduce_rows(const GArgs &a, int rr, int cx, int K, double2 *tot) {
     __shared__ unsigned s_t;
-    __shared__ double2 scr[256];
     double2 *rows = part_rows(a, rr);
     unsigned *cnt = a.cnt + (int64_t)rr * a.cstride;
-    const int g = cx / kRedGroup, g0 = g * kRedGroup;
-    const int gs = min(kRedGroup, a.nchunk - g0);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_t = atomicAdd(cnt + g, 1u);
-    __syncthreads();
-    if (s_t != (unsigned)gs - 1) return false;
-    __threadfence();
-    if (threadIdx.x == 0) cnt[g] = 0u;  // no other CTA of this launch touches it again
-    tree_sum(rows + (int64_t)g0 * a.pstride, gs, a.pstride, K, rows + (int64_t)(a.nchunk + g) * a.pstride, scr);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_t = atomicAdd(cnt + a.ngroups, 1u);
-    __syncthreads();
-    if (s_t != (unsigned)a.ngroups - 1) return false;
-    __threadfence();
-    if (threadIdx.x == 0) cnt[a.ngroups] = 0u;
-    tree_sum(rows + (int64_t)a.nchunk * a.pstride, a.ngroups, a.pstride, K, tot, scr);
-    return true;
+    int node = cx, n = a.nchunk, roff = 0, coff = 0;
+    for (int level = 0;; ++level) {
+        const int fan = tree_fan(level);
+        const int parent = node / fan, first = parent * fan, nch = min(fan, n - first);
+        const int np = (n + fan - 1) / fan;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_t = atomicAdd(cnt + coff + parent, 1u);
+        __syncthreads();
+        if (s_t != (unsigned)nch - 1) return false;
+        __threadfence();
+        if (threadIdx.x == 0) cnt[coff + parent] = 0u;  // no other CTA of this launch touches it again
+        const double2 *src = rows + (int64_t)(roff + first) * a.pstride;
+        double2 *dst = np == 1 ? tot : rows + (int64_t)(roff + n + parent) * a.pstride;
+        for (int k = threadIdx.x; k < K; k += blockDim.x) dst[k] = node_sum(level, src + k, nch, a.pstride, true);
+        if (np == 1) {
+            __syncthreads();
+            return true;
+        }
+        roff += n;
+        coff += np;
+        node = parent;
+        n = np;
+    }
 }
 
 __device__ __forceinline__ double2 *basis(const GArgs &a, int k, int rr) {
@@ -429,12 +442,13 @@ __device__ void givens_column(const GArgs &a, int rr, int j) {
 // pass.  The column h goes to H; without a second pass beta_{j+1} = ||w'|| is
 // stored and the column waits for its rotations.  Whole CTA; the sum of
 // |h_k|^2 is a fixed-order warp tree.
-__device__ void column_decision(const GArgs &a, int rr, int j, const double2 *hs, double w2) {
+__device__ int column_decision(const GArgs &a, int rr, int j, const double2 *hs, double w2, bool store) {
     __shared__ double s_hsq;
     int *st = a.st + rr * ST_STRIDE;
     const int m = a.m;
     double2 *H = a.H + (int64_t)rr * (m + 1) * m;
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) H[(int64_t)i * m + j] = hs[i];
+    if (store)
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) H[(int64_t)i * m + j] = hs[i];
     if (threadIdx.x < 32) {
         double v = 0;
         for (int k = threadIdx.x; k <= j; k += 32) v += cabs2(hs[k]);
@@ -443,10 +457,11 @@ __device__ void column_decision(const GArgs &a, int rr, int j, const double2 *hs
         if (threadIdx.x == 0) s_hsq = v;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const double wn2 = w2 - s_hsq;
-        const int again = !(wn2 > kReorthEta * kReorthEta * w2);
+    const double wn2 = w2 - s_hsq;
+    const int again = !(wn2 > kReorthEta * kReorthEta * w2);
+    if (store && threadIdx.x == 0) {
         st[ST_REORTH] = again;
+        st[ST_PASSES2] += again;
         if (!again) {
             const double bn = sqrt(wn2);
             a.beta[(int64_t)rr * (m + 1) + j + 1] = bn;
@@ -454,6 +469,8 @@ __device__ void column_decision(const GArgs &a, int rr, int j, const double2 *hs
             st[ST_COLUMN] = 1;
         }
     }
+    __syncthreads();
+    return again;
 }
 
 // Partial dot products <u_k, w> for k in [k0, k0+8) (k <= j) plus, when
@@ -503,44 +520,33 @@ __device__ __forceinline__ void dots_group(const GArgs &a, int rr, int j, int k0
     }
 }
 
-// Gram-Schmidt dots.
-// PASS 1: w = (product of u_j) / beta_j is formed (from the FP32 or FP64
-//   product) and stored as u_{j+1}; the CTA's sums of <u_k, w> (k <= j) and
-//   ||w||^2 are reduced across the RHS's chunks; the last CTA stores them
-//   unscaled: h1_k = beta_k <v_k, w> and h1_{j+1} = ||w||^2 (the update
-//   kernel scales, so no division sits on this kernel's serial tail).
-// PASS 2 (flagged RHS only): h2_k = beta_k <v_k, u_{j+1}>.
-template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(const __grid_constant__ GroupArgs g) {
-    __shared__ double2 wred[8][kMaxK];
-    __shared__ double2 tot[kMaxK];
-    if (PASS == 1 && blockIdx.x == 0 && threadIdx.x == 0) {
-        // Guard: every iteration body advances j, so a cycle runs at most m + 1
-        // bodies (one after its end is seen); beyond that the loops are ended
-        // and the solve reports TIMEOUT rather than running on.
-        SolveCtl *c = g.m[0].ctl;
-        if (++c->cycle_bodies > g.m[0].m + 2) {
-            c->guard = 1;
-            c->timed_out = 1;
-            c->cond_iter = 0;
-            if (g.graph) cudaGraphSetConditional(g.h_iter, 0u);
-        }
+// Guard: every iteration body advances j, so a cycle runs at most m + 1
+// bodies (one after its end is seen); beyond that the loops are ended and the
+// solve reports TIMEOUT rather than running on.  Block 0, thread 0 of the
+// step's first kernel.
+__device__ __forceinline__ void iteration_guard(const GroupArgs &g) {
+    SolveCtl *c = g.m[0].ctl;
+    if (++c->cycle_bodies > g.m[0].m + 2) {
+        c->guard = 1;
+        c->timed_out = 1;
+        c->cond_iter = 0;
+        if (g.graph) cudaGraphSetConditional(g.h_iter, 0u);
     }
-    const Loc L = locate(g, false);
-    if (L.mi < 0) return;
-    const GArgs &a = g.m[L.mi];
-    const int rr = L.rr;
-    const int *st = a.st + rr * ST_STRIDE;
-    if (!st[ST_ACTIVE]) return;
-    if (PASS == 2 && !st[ST_REORTH]) return;
-    const int j = a.ctl->j;
-    if (j >= a.m) return;
+}
+
+// The chunk's partial row of the Gram-Schmidt sums (whole CTA).
+// PASS 1: w = (product of u_j) / beta_j is formed (from the FP32 or FP64
+//   product) and stored as u_{j+1}; row = <u_k, w> (k <= j) and ||w||^2.
+// PASS 2: row = <u_k, u_{j+1}> (k <= j).  Returns the row length K.
+template <int ELEM, int PASS>
+__device__ int dots_row(const GArgs &a, int rr, int cx, int j, double2 (*wred)[kMaxK]) {
     double2 *un = basis(a, j + 1, rr);
     double2 wv[ELEM];
     int64_t ix[ELEM];
     const double sc = a.ibeta[(int64_t)rr * (a.m + 1) + j];
 #pragma unroll
     for (int e = 0; e < ELEM; ++e) {
-        ix[e] = elem_index(a, L.cx, e);
+        ix[e] = elem_index(a, cx, e);
         wv[e] = make_double2(0, 0);
         if (ix[e] >= 0) {
             if (PASS == 1) {
@@ -562,10 +568,31 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(cons
     const int K = j + 1 + (PASS == 1 ? 1 : 0);
     for (int k0 = 0; k0 < K; k0 += 8) dots_group<ELEM>(a, rr, j, k0, K, PASS == 1, wv, ix, wred);
     __syncthreads();
-    double2 *row = part_rows(a, rr) + (int64_t)L.cx * a.pstride;
+    double2 *row = part_rows(a, rr) + (int64_t)cx * a.pstride;
     for (int k = threadIdx.x; k < K; k += blockDim.x)  // the 8 warps' sums, pairwise
         row[k] = ((wred[0][k] + wred[1][k]) + (wred[2][k] + wred[3][k])) +
                  ((wred[4][k] + wred[5][k]) + (wred[6][k] + wred[7][k]));
+    return K;
+}
+
+// Gram-Schmidt dots: the chunk rows, then the last CTA stores the sums
+// unscaled (PASS 1: h1_k = beta_k <v_k, w> and h1_{j+1} = ||w||^2, the update
+// kernel scales, so no division sits on this kernel's serial tail; PASS 2
+// (flagged RHS only): h2_k = beta_k <v_k, u_{j+1}>).
+template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_dots(const __grid_constant__ GroupArgs g) {
+    __shared__ double2 wred[8][kMaxK];
+    __shared__ double2 tot[kMaxK];
+    if (PASS == 1 && blockIdx.x == 0 && threadIdx.x == 0) iteration_guard(g);
+    const Loc L = locate(g, false);
+    if (L.mi < 0) return;
+    const GArgs &a = g.m[L.mi];
+    const int rr = L.rr;
+    const int *st = a.st + rr * ST_STRIDE;
+    if (!st[ST_ACTIVE]) return;
+    if (PASS == 2 && !st[ST_REORTH]) return;
+    const int j = a.ctl->j;
+    if (j >= a.m) return;
+    const int K = dots_row<ELEM, PASS>(a, rr, L.cx, j, wred);
     if (!reduce_rows(a, rr, L.cx, K, tot)) return;
     double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
     for (int k = threadIdx.x; k < K; k += blockDim.x) h[k] = tot[k];  // (PASS 1: ||w||^2 in slot j+1)
@@ -642,6 +669,86 @@ __device__ void iteration_control(const GroupArgs &g) {
 //   to that pass).
 // PASS 2 (after a second Gram-Schmidt pass): also forms ||u_{j+1}|| across
 //   the chunks, adds h2 to the stored column and stores beta_{j+1}.
+// hs_k = h_k / beta_k and the update coefficients cf_k = hs_k / beta_k
+// (k <= j) from the step's sums h (whole CTA, ends with a barrier).
+__device__ __forceinline__ void step_coefficients(const GArgs &a, int rr, int j, const double2 *h, bool global,
+                                                  double2 *hs, double2 *cf) {
+    const double *ibeta = a.ibeta + (int64_t)rr * (a.m + 1);
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) {
+        const double ib = ibeta[k];
+        const double2 hk = cscale(global ? __ldcg(h + k) : h[k], ib);
+        hs[k] = hk;
+        cf[k] = cscale(hk, ib);
+    }
+    __syncthreads();
+}
+
+// The chunk's update u_{j+1} <- u_{j+1} - sum_k cf_k u_k, with its copy for
+// the next product; returns the thread's share of ||u_{j+1}||^2.
+template <int ELEM> __device__ double update_chunk(const GArgs &a, int rr, int cx, int j, const double2 *cf) {
+    double2 *un = basis(a, j + 1, rr);
+    double2 wv[ELEM];
+    int64_t ix[ELEM];
+#pragma unroll
+    for (int e = 0; e < ELEM; ++e) {
+        ix[e] = elem_index(a, cx, e);
+        wv[e] = ix[e] >= 0 ? un[ix[e]] : make_double2(0, 0);
+    }
+    int k = 0;
+    const int64_t vstride = (int64_t)a.cap * a.N;
+    constexpr int UNR = ELEM == 1 ? 8 : 4;  // basis vectors per step, loads first
+    for (; k + UNR <= j + 1; k += UNR) {
+        const double2 *u0 = basis(a, k, rr);
+#pragma unroll
+        for (int e = 0; e < ELEM; ++e) {
+            if (ix[e] >= 0) {
+                double2 uv[UNR];
+#pragma unroll
+                for (int kk = 0; kk < UNR; ++kk) uv[kk] = u0[kk * vstride + ix[e]];
+#pragma unroll
+                for (int kk = 0; kk < UNR; ++kk) wv[e] = cfms(cf[k + kk], uv[kk], wv[e]);
+            }
+        }
+    }
+    for (; k <= j; ++k) {
+        const double2 c = cf[k];
+        const double2 *uk = basis(a, k, rr);
+#pragma unroll
+        for (int e = 0; e < ELEM; ++e)
+            if (ix[e] >= 0) wv[e] = cfms(c, uk[ix[e]], wv[e]);
+    }
+    double acc = 0;
+#pragma unroll
+    for (int e = 0; e < ELEM; ++e) {
+        if (ix[e] >= 0) {
+            un[ix[e]] = wv[e];
+            if (a.mixed)
+                a.x32[(int64_t)rr * a.N + ix[e]] = make_float2((float)wv[e].x, (float)wv[e].y);
+            else
+                a.xin64[(int64_t)rr * a.N + ix[e]] = wv[e];
+            acc += cabs2(wv[e]);
+        }
+    }
+    return acc;
+}
+
+// After the second pass (the CTA that formed ||u_{j+1}||^2 = n2): H gets
+// h1 + h2 and beta_{j+1} is stored; the column waits for its rotations.
+__device__ void second_pass_close(const GArgs &a, int rr, int j, const double2 *hs2, double n2) {
+    int *st = a.st + rr * ST_STRIDE;
+    const int m = a.m;
+    double2 *H = a.H + (int64_t)rr * (m + 1) * m;
+    for (int kk = threadIdx.x; kk <= j; kk += blockDim.x)
+        H[(int64_t)kk * m + j] = __ldcg(H + (int64_t)kk * m + j) + hs2[kk];  // h1 + h2
+    if (threadIdx.x == 0) {
+        const double bn = sqrt(n2);
+        a.beta[(int64_t)rr * (m + 1) + j + 1] = bn;
+        a.ibeta[(int64_t)rr * (m + 1) + j + 1] = 1.0 / bn;
+        st[ST_REORTH] = 0;
+        st[ST_COLUMN] = 1;
+    }
+}
+
 template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(const __grid_constant__ GroupArgs g) {
     __shared__ double red[8];
     __shared__ double2 cf[kMaxK];
@@ -656,77 +763,16 @@ template <int ELEM, int PASS> __global__ void __launch_bounds__(256) k_upd(const
         const int j = a.ctl->j;
         const bool work = st[ST_ACTIVE] && (PASS == 1 || st[ST_REORTH]) && j < a.m;
         if (work) {
-            const double *ibeta = a.ibeta + (int64_t)rr * (a.m + 1);
             const double2 *h = (PASS == 1 ? a.h1 : a.h2) + (int64_t)rr * (a.m + 1);
-            for (int k = threadIdx.x; k <= j; k += blockDim.x) {
-                const double ib = ibeta[k];
-                const double2 hk = cscale(__ldcg(h + k), ib);
-                hs[k] = hk;
-                cf[k] = cscale(hk, ib);
-            }
-            __syncthreads();
+            step_coefficients(a, rr, j, h, true, hs, cf);
             if (PASS == 1 && L.cx == a.nchunk) {
-                column_decision(a, rr, j, hs, __ldcg(h + j + 1).x);
+                column_decision(a, rr, j, hs, __ldcg(h + j + 1).x, true);
             } else {
-                double2 *un = basis(a, j + 1, rr);
-                double2 wv[ELEM];
-                int64_t ix[ELEM];
-#pragma unroll
-                for (int e = 0; e < ELEM; ++e) {
-                    ix[e] = elem_index(a, L.cx, e);
-                    wv[e] = ix[e] >= 0 ? un[ix[e]] : make_double2(0, 0);
-                }
-                int k = 0;
-                const int64_t vstride = (int64_t)a.cap * a.N;
-                constexpr int UNR = ELEM == 1 ? 8 : 4;  // basis vectors per step, loads first
-                for (; k + UNR <= j + 1; k += UNR) {
-                    const double2 *u0 = basis(a, k, rr);
-#pragma unroll
-                    for (int e = 0; e < ELEM; ++e) {
-                        if (ix[e] >= 0) {
-                            double2 uv[UNR];
-#pragma unroll
-                            for (int kk = 0; kk < UNR; ++kk) uv[kk] = u0[kk * vstride + ix[e]];
-#pragma unroll
-                            for (int kk = 0; kk < UNR; ++kk) wv[e] = cfms(cf[k + kk], uv[kk], wv[e]);
-                        }
-                    }
-                }
-                for (; k <= j; ++k) {
-                    const double2 c = cf[k];
-                    const double2 *uk = basis(a, k, rr);
-#pragma unroll
-                    for (int e = 0; e < ELEM; ++e)
-                        if (ix[e] >= 0) wv[e] = cfms(c, uk[ix[e]], wv[e]);
-                }
-                double acc = 0;
-#pragma unroll
-                for (int e = 0; e < ELEM; ++e) {
-                    if (ix[e] >= 0) {
-                        un[ix[e]] = wv[e];
-                        if (a.mixed)
-                            a.x32[(int64_t)rr * a.N + ix[e]] = make_float2((float)wv[e].x, (float)wv[e].y);
-                        else
-                            a.xin64[(int64_t)rr * a.N + ix[e]] = wv[e];
-                        acc += cabs2(wv[e]);
-                    }
-                }
+                double acc = update_chunk<ELEM>(a, rr, L.cx, j, cf);
                 if (PASS == 2) {
                     acc = block_sum1(acc, red);
                     if (threadIdx.x == 0) part_rows(a, rr)[(int64_t)L.cx * a.pstride] = make_double2(acc, 0);
-                    if (reduce_rows(a, rr, L.cx, 1, tot)) {
-                        const int m = a.m;
-                        double2 *H = a.H + (int64_t)rr * (m + 1) * m;
-                        for (int kk = threadIdx.x; kk <= j; kk += blockDim.x)
-                            H[(int64_t)kk * m + j] = __ldcg(H + (int64_t)kk * m + j) + hs[kk];  // h1 + h2
-                        if (threadIdx.x == 0) {
-                            const double bn = sqrt(tot[0].x);
-                            a.beta[(int64_t)rr * (m + 1) + j + 1] = bn;
-                            a.ibeta[(int64_t)rr * (m + 1) + j + 1] = 1.0 / bn;
-                            st[ST_REORTH] = 0;
-                            st[ST_COLUMN] = 1;
-                        }
-                    }
+                    if (reduce_rows(a, rr, L.cx, 1, tot)) second_pass_close(a, rr, j, hs, tot[0].x);
                 }
             }
         }
@@ -1037,8 +1083,8 @@ static ztoep_status_t ensure_solve_ws(ztoep_plan_t p, int nrhs, int m) {
     free_solve_ws(p);
     const int64_t N = p->N;
     const Geom gm = geom_for(N, p->nsm);
-    const int ngroups = (gm.nchunk + kRedGroup - 1) / kRedGroup;
-    const int cstride = ngroups + 1;
+    const int nrows = tree_rows(gm.nchunk);
+    const int cstride = tree_tickets(gm.nchunk);
     const int pstride = m + 2;
     const size_t vec = sizeof(double2) * (size_t)nrhs * N;
     size_t acc = 0;
@@ -1055,7 +1101,7 @@ static ztoep_status_t ensure_solve_ws(ztoep_plan_t p, int nrhs, int m) {
     ZT_TRY(dalloc((void **)&w.g, sizeof(double2) * (size_t)nrhs * (m + 1), &acc));
     ZT_TRY(dalloc((void **)&w.h1, sizeof(double2) * (size_t)nrhs * (m + 1), &acc));
     ZT_TRY(dalloc((void **)&w.h2, sizeof(double2) * (size_t)nrhs * (m + 1), &acc));
-    ZT_TRY(dalloc((void **)&w.part, sizeof(double2) * (size_t)nrhs * (gm.nchunk + ngroups) * pstride, &acc));
+    ZT_TRY(dalloc((void **)&w.part, sizeof(double2) * (size_t)nrhs * nrows * pstride, &acc));
     ZT_TRY(dalloc((void **)&w.nrm, sizeof(double) * (size_t)nrhs * (NM_STRIDE + 2 * (m + 1)), &acc));
     ZT_TRY(dalloc((void **)&w.st, sizeof(int) * (size_t)nrhs * ST_STRIDE, &acc));
     ZT_TRY(dalloc((void **)&w.cnt, sizeof(unsigned) * (size_t)nrhs * cstride, &acc));
@@ -1087,11 +1133,12 @@ static GArgs make_args(ztoep_plan_t p, int nrhs, int m, bool mixed, SolveCtl *ct
     a.st = w.st; a.cnt = w.cnt;
     a.ctl = ctl;
     a.N = p->N; a.cap = w.cap; a.m = m; a.nchunk = gm.nchunk; a.per_cta = gm.per_cta;
-    a.ngroups = (gm.nchunk + kRedGroup - 1) / kRedGroup; a.cstride = w.cstride; a.pstride = w.m + 2;
+    a.nrows = tree_rows(gm.nchunk); a.cstride = w.cstride; a.pstride = w.m + 2;
     a.nrhs = nrhs;
     a.mixed = mixed ? 1 : 0;
     return a;
 }
+
 
 // The work list of a solve of `n` members (the first member's control block
 // is the group's).
@@ -1593,6 +1640,7 @@ static ztoep_status_t solve_core(const Member *mem, int n, const ztoep_solve_opt
                 info[i][rr].inner_iters = st[ST_ITERS];
                 info[i][rr].status = rs;
                 info[i][rr].rel_residual = nm[NM_VNORM] > 0 ? nm[NM_RNORM] / nm[NM_VNORM] : nm[NM_RNORM];
+                info[i][rr].second_passes = st[ST_PASSES2];
             }
         }
     }

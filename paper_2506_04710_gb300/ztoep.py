@@ -52,7 +52,7 @@ class SolveOpts(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("outer", ctypes.c_int32), ("inner_iters", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("rel_residual", ctypes.c_double)]
+                ("second_passes", ctypes.c_int32), ("rel_residual", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -559,7 +559,7 @@ class Plan:
         if check and st not in (ZTOEP_OK,):
             raise ZtoepError(st, "ztoep_solve")
         return X, [dict(outer=i.outer, inner_iters=i.inner_iters, status=i.status,
-                        rel_residual=i.rel_residual) for i in info], st
+                        second_passes=i.second_passes, rel_residual=i.rel_residual) for i in info], st
 
     def far_field(self, I, Fh, k: float, eta: float, stream=None):
         """Far field on the array-factor grid (ztoep_far_field_grid): I
