@@ -93,6 +93,13 @@ class Clocks:
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+        # the sampler's start-up (NVML initialisation) stays out of the timed
+        # region: wait for its first sample (at most 5 s)
+        t0 = time.perf_counter()
+        while self.p is not None and self.p.poll() is None and time.perf_counter() - t0 < 5.0:
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.05)
 
     def stop(self):
         if self.p is None:
