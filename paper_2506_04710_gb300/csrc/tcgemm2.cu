@@ -16,20 +16,27 @@
 //
 // CTA = 14 warps, one CTA per SM, persistent over work items (problem, RHS
 // chunk of rp <= 64, K split, 128-row tile):
-//   warp 0     TMA producer: A tile (128 rows x 32 floats, 128B swizzle) and
-//              the raw X tile (rp rows x 32 floats) of each k-block into a raw
-//              ring of NR stages (mbarrier full[r], transaction bytes); a raw
-//              stage is refilled as soon as it has been converted (rfree[r]),
-//              so up to NR loads are in flight whatever the MMAs are doing;
-//   warps 2-9  split A into hi and lo tiles, expand and split X into
-//              [Xhi; Xlo] (swizzled) in one of NO = 2-3 operand stages (once
-//              the MMAs that last read it are done, ofree[o]), then arrive on
-//              rfree[r] and ready[o];
-//   warp 1     one thread issues the MMAs of a k-block and commits them to
-//              ofree[o] and, at the end of an item, to accf[b];
+//   warp 0     TMA producer: the A tile (128 rows x 32 floats per k-block,
+//              128B-swizzled boxes) and the raw X tile (rp rows) of two
+//              k-blocks into a raw ring of NR stages (mbarrier full[r],
+//              transaction bytes); a raw stage is refilled as soon as it has
+//              been converted (rfree[r]), so up to NR loads are in flight
+//              whatever the MMAs are doing;
+//   warps 2-9  split A into hi and lo and write them to tensor memory (warp w
+//              owns TMEM lanes 32 (w mod 4) .. +31, i.e. its rows, and half of
+//              the k-block's columns; the swizzled raw box lets its 32 rows be
+//              read without bank conflicts), expand and split X into [Xhi;
+//              Xlo] (swizzled, shared memory), in one of NO = 2-3 operand
+//              stages (once the MMAs that last read it are done, ofree[o]),
+//              then arrive on rfree[r] and ready[o];
+//   warp 1     one thread issues the MMAs of a k-block (A from tensor memory,
+//              X from shared memory) and commits them to ofree[o] and, at the
+//              end of an item, to accf[b];
 //   warps 10-13 epilogue: tensor memory -> registers -> C, then acce[b]; the
-//              accumulator is double-buffered, so an item's epilogue overlaps
-//              the next item's MMAs.
+//              accumulator is double-buffered when two buffers fit beside the
+//              A stages (so an item's epilogue overlaps the next item's MMAs).
+// Tensor memory: accumulator buffers of 4 rp columns, then 64 columns (A hi,
+// A lo) per operand stage.
 // Every wait is bounded: a wait that gives up records an error bit, raises an
 // abort flag the other roles poll, and the producer waits (bounded) for its
 // copies in flight before the CTA frees its tensor memory and leaves.
@@ -66,6 +73,7 @@ struct G2Args {
     int nchunk, ksplit, mtiles, nprob, kchunk;
     int nraw;            // stages of the raw ring
     int nop;             // stages of the operand ring (2 or 3)
+    int nacc;            // accumulator buffers in tensor memory (2, or 1 when they would not fit beside A)
     uint32_t tmem_cols;
     int *err;
 };
@@ -122,17 +130,18 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
     unsigned char *smem = g2_smem_raw + (base - raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int NR = g.nraw, NO = g.nop, rp = g.rp;
-    // operand ring (NO stages, one k-block each): A hi (16 KB) | A lo (16 KB) |
-    //   X expanded [4 rp][128 B], all 128B-swizzled K-major tiles
-    // raw ring (NR stages, G2_KPR k-blocks each, as loaded, row-major):
-    //   A [128][G2_KPR x 128 B] | X [rp][G2_KPR x 128 B]
-    constexpr uint32_t RW = 128u * G2_KPR;  // bytes of a raw row
-    const uint32_t op_bytes = 32768u + 512u * (uint32_t)rp, raw_bytes = (128u + (uint32_t)rp) * RW;
-    auto a_hi = [&](int o) { return base + (uint32_t)o * op_bytes; };
-    auto a_lo = [&](int o) { return a_hi(o) + 16384u; };
-    auto x_exp = [&](int o) { return a_hi(o) + 32768u; };
+    // operand ring (NO stages, one k-block each): X expanded [4 rp][128 B]
+    //   (128B-swizzled K-major) in shared memory; A hi and A lo [128 lanes][32
+    //   columns] each in tensor memory after the accumulators
+    // raw ring (NR stages, G2_KPR k-blocks each, as loaded): A as G2_KPR
+    //   128B-swizzled [128][128 B] boxes | X [rp][G2_KPR x 128 B] row-major
+    constexpr uint32_t RW = 128u * G2_KPR;  // bytes of a raw X row
+    const uint32_t op_bytes = 512u * (uint32_t)rp, raw_bytes = (128u + (uint32_t)rp) * RW;
+    auto x_exp = [&](int o) { return base + (uint32_t)o * op_bytes; };
     auto a_raw = [&](int r) { return base + (uint32_t)NO * op_bytes + (uint32_t)r * raw_bytes; };
     auto x_raw = [&](int r) { return a_raw(r) + 128u * RW; };
+    const uint32_t acol0 = (uint32_t)(g.nacc * 4 * rp);                   // first A column in tensor memory
+    auto a_col = [&](int o) { return acol0 + (uint32_t)o * 64u; };  // hi: +0..31, lo: +32..63
 
     if (threadIdx.x == 0) {
         for (int r = 0; r < NR; ++r) {
@@ -187,7 +196,8 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
                     }
                     mbar_arrive_expect_tx(&full[r], tx);
                     const int kx = 2 * (w.k0 + kb * 16);
-                    tma_load_3d(a_raw(r), &tmA, kx, w.mt * 128, w.p, &full[r]);
+                    for (int sb = 0; sb < G2_KPR; ++sb)
+                        tma_load_3d(a_raw(r) + (uint32_t)sb * 16384u, &tmA, kx + 32 * sb, w.mt * 128, w.p, &full[r]);
                     tma_load_3d(x_raw(r), &tmX, kx, w.c * rp, w.p, &full[r]);
                     ++kbg;
                 }
@@ -207,8 +217,8 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
             bool ok = true;
             for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
                 const Item w = decode(g, it);
-                const int b = (int)(tc & 1);
-                const uint32_t u = tc >> 1;
+                const int b = (int)(tc % (uint32_t)g.nacc);
+                const uint32_t u = tc / (uint32_t)g.nacc;
                 if (u > 0 && !mbar_wait_bounded(&acce[b], (u - 1) & 1, G2_WAIT)) {
                     ok = false;
                     break;
@@ -223,11 +233,11 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
                     }
                     fence_after();
 #pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {  // 4 x (K = 8 real = 32 bytes)
-                        const uint32_t off = ks * 32;
-                        const uint64_t xb = sdesc(x_exp(o) + off);
-                        mma_tf32(d, sdesc(a_hi(o) + off), xb, id_wide, (kb > 0 || ks > 0) ? 1 : 0);
-                        mma_tf32(d, sdesc(a_lo(o) + off), xb, id_half, 1);
+                    for (int ks = 0; ks < 4; ++ks) {  // 4 x (K = 8 real = 32 bytes, 8 columns)
+                        const uint64_t xb = sdesc(x_exp(o) + ks * 32);
+                        const uint32_t ac = tmem + a_col(o) + 8u * ks;
+                        mma_tf32_ta(d, ac, xb, id_wide, (kb > 0 || ks > 0) ? 1 : 0);
+                        mma_tf32_ta(d, ac + 32u, xb, id_half, 1);
                     }
                     mma_commit(&ofree[o]);
                     ++kbg;
@@ -241,18 +251,17 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
     } else if (warp < 2 + G2_TW) {  // ---------------- raw -> operands (G2_TW warps)
         constexpr int NT = 32 * G2_TW;
         const int t = threadIdx.x - 64;
-        // this thread's (row, 16-byte chunk) pieces of an A and an X k-block:
-        // offsets in the raw row-major tile and in the swizzled operand tile,
-        // fixed for the whole kernel
-        constexpr int AP = 1024 / NT;
+        // A: this warp's lane quarter (its tensor-memory lanes) and half of the
+        // k-block's 32 reals; the thread's row is read from the swizzled raw box
+        // (16-byte chunk c of row a at chunk c ^ (a mod 8): a warp's 32 rows hit
+        // distinct banks)
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        const int arow = 32 * quarter + lane;
+        const uint32_t tlane = (uint32_t)(32 * quarter) << 16;
+        // X: this thread's (row, 16-byte chunk) pieces: offsets in the raw
+        // row-major tile and in the swizzled operand tile, fixed for the kernel
         constexpr int XP = (G2_MAXRP * 8 + NT - 1) / NT;
-        uint32_t ai[AP], ao[AP], xi[XP], xo[XP][4];
-#pragma unroll
-        for (int k = 0; k < AP; ++k) {
-            const int i = t + k * NT, row = i >> 3, ch = i & 7;
-            ai[k] = (uint32_t)row * RW + (uint32_t)ch * 16u;
-            ao[k] = sw128(row, ch);
-        }
+        uint32_t xi[XP], xo[XP][4];
 #pragma unroll
         for (int k = 0; k < XP; ++k) {
             const int i = t + k * NT, q = i >> 3, ch = i & 7;
@@ -281,15 +290,28 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
                         ok = false;
                         break;
                     }
-                    unsigned char *ah = smem + (a_hi(o) - base);
-                    unsigned char *al = smem + (a_lo(o) - base);
+                    fence_after();  // the MMAs that read stage o are complete before it is rewritten
                     const uint32_t so = (uint32_t)sub * 128u;
+                    {
+                        const unsigned char *arow_p = ar + sub * 16384 + arow * 128;
+                        uint32_t hi[16], lo[16];
 #pragma unroll
-                    for (int k = 0; k < AP; ++k) {
-                        const float4 v = *reinterpret_cast<const float4 *>(ar + ai[k] + so);
-                        const float4 h = tf32n4(v);
-                        *reinterpret_cast<float4 *>(ah + ao[k]) = h;
-                        *reinterpret_cast<float4 *>(al + ao[k]) = tf32n4(sub4(v, h));
+                        for (int c = 0; c < 4; ++c) {
+                            const int ch = 4 * half + c;
+                            const float4 v = *reinterpret_cast<const float4 *>(arow_p + ((ch ^ (arow & 7)) << 4));
+                            const float4 h = tf32n4(v), l = tf32n4(sub4(v, h));
+                            hi[4 * c] = __float_as_uint(h.x);
+                            hi[4 * c + 1] = __float_as_uint(h.y);
+                            hi[4 * c + 2] = __float_as_uint(h.z);
+                            hi[4 * c + 3] = __float_as_uint(h.w);
+                            lo[4 * c] = __float_as_uint(l.x);
+                            lo[4 * c + 1] = __float_as_uint(l.y);
+                            lo[4 * c + 2] = __float_as_uint(l.z);
+                            lo[4 * c + 3] = __float_as_uint(l.w);
+                        }
+                        const uint32_t ta = tmem + tlane + a_col(o) + 16u * half;
+                        tmem_st16(ta, hi);
+                        tmem_st16(ta + 32u, lo);
                     }
                     unsigned char *xe = smem + (x_exp(o) - base);
 #pragma unroll
@@ -306,6 +328,8 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
                         }
                     }
                     fence_proxy_async();  // generic-proxy stores -> visible to the tensor core
+                    tmem_st_wait();       // the warp's tensor-memory stores have landed
+                    fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&ready[o]);
                     ++kbg;
@@ -324,8 +348,8 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
         bool ok = true;
         for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
             const Item w = decode(g, it);
-            const int b = (int)(tc & 1);
-            const uint32_t u = tc >> 1;
+            const int b = (int)(tc % (uint32_t)g.nacc);
+            const uint32_t u = tc / (uint32_t)g.nacc;
             if (*abort_v || !mbar_wait_bounded(&accf[b], u & 1, G2_WAIT)) {
                 ok = false;
                 break;
@@ -384,14 +408,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 3-D FP32 view {2K floats, rows, problems} of a complex operand; box
-// {32 floats, box_rows, 1}.
+// {box_inner floats, box_rows, 1}, 128B-swizzled or not.
 bool make_map(CUtensorMap *m, const float2 *base, int K, int rows, int64_t ld, int nprob, int64_t stride,
-              int box_rows, bool swizzle) {
+              int box_inner, int box_rows, bool swizzle) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)(2 * (int64_t)K), (cuuint64_t)rows, (cuuint64_t)nprob};
     const cuuint64_t strides[2] = {(cuuint64_t)(ld * 8), (cuuint64_t)((nprob > 1 ? stride : ld * rows) * 8)};
-    const cuuint32_t box[3] = {(cuuint32_t)(32 * G2_KPR), (cuuint32_t)box_rows, 1u};
+    const cuuint32_t box[3] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows, 1u};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2 *>(base), dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -428,17 +452,23 @@ ztoep_status_t launch_cgemm_tc2(const CgemmArgs &a, int nprob, int nsm, cudaStre
     g.ksplit = (a.K + kc - 1) / kc;
     g.mtiles = (a.M + 127) / 128;
     g.nprob = nprob;
-    const size_t op_bytes = 32768 + 512 * (size_t)g.rp, raw_bytes = (128 + (size_t)g.rp) * 128 * G2_KPR;
+    const size_t op_bytes = 512 * (size_t)g.rp, raw_bytes = (128 + (size_t)g.rp) * 128 * G2_KPR;
     if (G2_SMEM_CAP < 1024 + 2 * op_bytes + 2 * raw_bytes) return ZTOEP_ERR_UNSUPPORTED;
     // three operand stages when four raw stages still fit beside them
     g.nop = G2_SMEM_CAP >= 1024 + 3 * op_bytes + 4 * raw_bytes ? 3 : 2;
     g.nraw = (int)std::min<size_t>(G2_MAXRAW, (G2_SMEM_CAP - 1024 - g.nop * op_bytes) / raw_bytes);
+    // tensor memory: the accumulators (two buffers when A's stages still fit
+    // beside them, so an item's epilogue overlaps the next item's MMAs), then
+    // 64 columns (A hi, A lo) per operand stage
+    g.nacc = 2 * 4 * g.rp + 64 * g.nop <= 512 ? 2 : 1;
     uint32_t cols = 32;
-    while (cols < (uint32_t)(8 * g.rp)) cols <<= 1;
+    while (cols < (uint32_t)(g.nacc * 4 * g.rp + 64 * g.nop)) cols <<= 1;
+    if (cols > 512) return ZTOEP_ERR_UNSUPPORTED;
     g.tmem_cols = cols;
     CUtensorMap ma, mx;
-    if (!make_map(&ma, a.A, a.K, a.M, a.lda, nprob, a.strideA, 128, false)) return ZTOEP_ERR_UNSUPPORTED;
-    if (!make_map(&mx, a.X, a.K, a.N, a.ldx, nprob, a.strideX, g.rp, false)) return ZTOEP_ERR_UNSUPPORTED;
+    if (!make_map(&ma, a.A, a.K, a.M, a.lda, nprob, a.strideA, 32, 128, true)) return ZTOEP_ERR_UNSUPPORTED;
+    if (!make_map(&mx, a.X, a.K, a.N, a.ldx, nprob, a.strideX, 32 * G2_KPR, g.rp, false))
+        return ZTOEP_ERR_UNSUPPORTED;
     const size_t smem = (size_t)g.nop * op_bytes + (size_t)g.nraw * raw_bytes + 1024;
     static bool attr = false;
     if (!attr) {
